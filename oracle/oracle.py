@@ -1,0 +1,278 @@
+"""FP64 CPU oracle: plain, slow, obviously correct.
+
+TEST INFRASTRUCTURE ONLY: only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA library (``paper_2404_10928_gb300``) and imports nothing from it;
+the two meet only in the seeded input generators (``phantoms``), which hold
+none of the method's arithmetic.
+
+What is computed, and where it comes from:
+
+* ``forward`` / ``adjoint`` / ``forward_dense`` / ``dc``: the time-domain
+  measurement matrix of Eq. 6 (Sec. 3.4) discretised with a linear-interpolation
+  hat and a 1/distance weight (the spreading factor of Eq. 7); C loops in
+  ``pa_oracle.c``.
+* ``landweber``: projected gradient descent on the data term of Eq. 8,
+  ``x <- max(0, x + omega * A^T (y - A x))``.  This is the gradient line the
+  paper profiles (Table 3: ``t1 = 2*kn'*(kn*mk1r - y)``) with step omega/2,
+  plus a non-negativity projection.
+* ``cgls``: conjugate gradients on the normal equations of the same data term
+  (Hestenes-Stiefel recursion for least squares), then a final clamp x >= 0.
+* ``power_iteration``: largest eigenvalue of A^T A (step size for Landweber).
+* ``tv`` / ``tv_grad``: smoothed isotropic total variation (the TV term of
+  Eq. 8 with Psi' = identity).
+
+Readings where the paper is silent are listed in the design doc; each function
+names the one it uses.  Parity status: every function here is pinned by a
+``-m "not gpu"`` test in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pa_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile pa_oracle.c into liboracle.so with gcc (FP64, OpenMP, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            geo = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                   ctypes.c_double, ctypes.c_int]
+            for name in ("oracle_forward", "oracle_forward_dense", "oracle_adjoint"):
+                fn = getattr(lib, name)
+                fn.argtypes = geo + [dp, dp]
+                fn.restype = None
+            lib.oracle_dc.argtypes = geo + [dp, dp, dp]
+            lib.oracle_dc.restype = ctypes.c_double
+            lib.oracle_min_distance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, dp, dp, dp, ctypes.c_int]
+            lib.oracle_min_distance.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Geometry:
+    """The oracle's own copy of a problem's geometry (plain FP64 numbers)."""
+
+    def __init__(self, dim, shape, spacing, origin, sensors, c, fs, n_samples, t0=0.0,
+                 amp_scale=1.0):
+        self.dim = int(dim)
+        self.shape = tuple(int(v) for v in shape)
+        self.spacing = _f64(spacing)
+        self.origin = _f64(origin)
+        self.sensors = _f64(sensors).reshape(-1, self.dim)
+        self.c = float(c)
+        self.fs = float(fs)
+        self.n_samples = int(n_samples)
+        self.t0 = float(t0)
+        self.amp = float(amp_scale)
+
+    @classmethod
+    def of(cls, prob, c=None):
+        return cls(prob.dim, prob.shape, prob.spacing, prob.origin, prob.sensors,
+                   prob.c if c is None else c, prob.fs, prob.n_samples, prob.t0, prob.amp_scale)
+
+    @property
+    def n_pixels(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    @property
+    def n_sensors(self):
+        return self.sensors.shape[0]
+
+    def _args(self, c=None):
+        nx, ny, nz = self.shape
+        return (self.dim, nx, ny, nz, _ptr(self.spacing), _ptr(self.origin), _ptr(self.sensors),
+                self.n_sensors, self.c if c is None else float(c), self.fs, self.t0, self.amp,
+                self.n_samples)
+
+
+def forward(geo: Geometry, x, c=None) -> np.ndarray:
+    """p = A x (Eq. 6 discretised), two-tap form.  Returns [S][K] float64."""
+    x = _f64(x).ravel()
+    assert x.size == geo.n_pixels
+    p = np.empty((geo.n_sensors, geo.n_samples))
+    _load().oracle_forward(*geo._args(c), _ptr(x), _ptr(p))
+    return p
+
+
+def forward_dense(geo: Geometry, x) -> np.ndarray:
+    """p = A x evaluating the hat at every sample (no floor).  Tiny grids only."""
+    x = _f64(x).ravel()
+    p = np.empty((geo.n_sensors, geo.n_samples))
+    _load().oracle_forward_dense(*geo._args(), _ptr(x), _ptr(p))
+    return p
+
+
+def adjoint(geo: Geometry, p, c=None) -> np.ndarray:
+    """g = A^T p (delay-and-sum back-projection with the same hat and weight)."""
+    p = _f64(p).reshape(geo.n_sensors, geo.n_samples)
+    g = np.empty(geo.n_pixels)
+    _load().oracle_adjoint(*geo._args(c), _ptr(p), _ptr(g))
+    return g
+
+
+def dc(geo: Geometry, x, g, c=None) -> float:
+    """d/dc <g, A(x; c)>: the speed-of-sound derivative of the forward model."""
+    x = _f64(x).ravel()
+    g = _f64(g).reshape(geo.n_sensors, geo.n_samples)
+    per = np.empty(geo.n_sensors)
+    return float(_load().oracle_dc(*geo._args(c), _ptr(x), _ptr(g), _ptr(per)))
+
+
+def min_distance(geo: Geometry) -> float:
+    nx, ny, nz = geo.shape
+    return float(_load().oracle_min_distance(geo.dim, nx, ny, nz, _ptr(geo.spacing),
+                                             _ptr(geo.origin), _ptr(geo.sensors), geo.n_sensors))
+
+
+def matrix(geo: Geometry) -> np.ndarray:
+    """Explicit [S*K][N] matrix assembled column by column with forward_dense."""
+    n = geo.n_pixels
+    cols = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        cols.append(forward_dense(geo, e).ravel())
+    return np.stack(cols, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# iterations (numpy, FP64)
+# ----------------------------------------------------------------------------
+
+def landweber(geo: Geometry, y, n_iter: int, omega: float, x0=None, nonneg: bool = True):
+    """Projected Landweber: x_{n+1} = max(0, x_n + omega * A^T (y - A x_n)).
+
+    Reading: Table 3 gives only the gradient 2 K^T (K x - y); the update is a
+    plain gradient step of size omega/2 followed by the projection onto x >= 0.
+    Returns (x_n, history) with history[n] = ||y - A x_n||^2, n = 0..n_iter.
+    """
+    y = _f64(y).reshape(geo.n_sensors, geo.n_samples)
+    x = np.zeros(geo.n_pixels) if x0 is None else _f64(x0).ravel().copy()
+    hist = []
+    for _ in range(n_iter):
+        r = y - forward(geo, x)
+        hist.append(float(np.sum(r * r)))
+        x = x + omega * adjoint(geo, r)
+        if nonneg:
+            x = np.maximum(x, 0.0)
+    r = y - forward(geo, x)
+    hist.append(float(np.sum(r * r)))
+    return x, np.array(hist)
+
+
+def cgls(geo: Geometry, y, n_iter: int, x0=None, nonneg: bool = True):
+    """CGLS (conjugate gradients on A^T A x = A^T y, Hestenes-Stiefel form).
+
+    r = y - A x0; s = A^T r; p = s; gamma = ||s||^2; then per iteration
+      q = A p; alpha = gamma / ||q||^2; x += alpha p; r -= alpha q;
+      s = A^T r; gamma' = ||s||^2; beta = gamma'/gamma; p = s + beta p.
+    A zero ||q||^2 or gamma stops the recursion (alpha = 0 / beta = 0).
+    Reading: non-negativity is applied once after the last iteration.
+    Returns (x, history) with history[n] = ||r_n||^2, n = 0..n_iter.
+    """
+    y = _f64(y).reshape(geo.n_sensors, geo.n_samples)
+    x = np.zeros(geo.n_pixels) if x0 is None else _f64(x0).ravel().copy()
+    r = y - forward(geo, x)
+    s = adjoint(geo, r)
+    p = s.copy()
+    gamma = float(np.sum(s * s))
+    hist = [float(np.sum(r * r))]
+    for _ in range(n_iter):
+        q = forward(geo, p)
+        delta = float(np.sum(q * q))
+        alpha = gamma / delta if delta > 0.0 else 0.0
+        x = x + alpha * p
+        r = r - alpha * q
+        hist.append(float(np.sum(r * r)))
+        s = adjoint(geo, r)
+        gamma_new = float(np.sum(s * s))
+        beta = gamma_new / gamma if gamma > 0.0 else 0.0
+        gamma = gamma_new
+        p = s + beta * p
+    if nonneg:
+        x = np.maximum(x, 0.0)
+    return x, np.array(hist)
+
+
+def power_iteration(geo: Geometry, v0, n_iter: int = 50) -> float:
+    """sigma_max(A)^2 by power iteration on A^T A from the given start vector.
+
+    v <- A^T A v / ||A^T A v||; the estimate is ||A^T A v|| at the last step
+    with v of unit norm.
+    """
+    v = _f64(v0).ravel()
+    v = v / np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(n_iter):
+        w = adjoint(geo, forward(geo, v))
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return lam
+
+
+# ----------------------------------------------------------------------------
+# smoothed total variation (2D), the TV term of Eq. 8 with Psi' = I
+# ----------------------------------------------------------------------------
+
+def tv(img2d, eps: float = 1e-4) -> float:
+    """sum_ij sqrt((x[i,j+1]-x[i,j])^2 + (x[i+1,j]-x[i,j])^2 + eps^2), forward
+    differences, zero difference past the last row/column (Neumann)."""
+    x = _f64(img2d)
+    gx = np.zeros_like(x)
+    gy = np.zeros_like(x)
+    gx[:, :-1] = x[:, 1:] - x[:, :-1]
+    gy[:-1, :] = x[1:, :] - x[:-1, :]
+    return float(np.sum(np.sqrt(gx * gx + gy * gy + eps * eps)))
+
+
+def tv_grad(img2d, eps: float = 1e-4) -> np.ndarray:
+    """Analytic gradient of ``tv``."""
+    x = _f64(img2d)
+    gx = np.zeros_like(x)
+    gy = np.zeros_like(x)
+    gx[:, :-1] = x[:, 1:] - x[:, :-1]
+    gy[:-1, :] = x[1:, :] - x[:-1, :]
+    m = np.sqrt(gx * gx + gy * gy + eps * eps)
+    ax = gx / m
+    ay = gy / m
+    g = -(ax + ay)
+    g[:, 1:] += ax[:, :-1]
+    g[1:, :] += ay[:-1, :]
+    return g

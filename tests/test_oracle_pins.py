@@ -1,0 +1,229 @@
+"""Pins of the FP64 oracle to facts fixed outside the oracle itself.
+
+Each test checks the oracle against something it cannot agree with by
+construction: hand-worked closed forms (``tests/golden``), partition-of-unity
+sums of the hat, an independently written adjoint loop, a brute-force matrix
+that evaluates the hat at every sample, library solvers (lstsq, NNLS, SVD) and
+finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2404_10928_gb300 import phantoms as ph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _single_pixel_geo(case):
+    dim = case["dim"]
+    shape = (1, 1, 1)
+    spacing = (1e-4, 1e-4, 1e-4)
+    origin = (0.0, 0.0, 0.0)
+    sensors = np.array([case["sensor"]], dtype=np.float64)
+    return orc.Geometry(dim, shape, spacing, origin, sensors, case["c"], case["fs"], case["K"],
+                        case["t0"], case["amp"])
+
+
+def _load_cases():
+    with open(os.path.join(GOLDEN, "single_pixel.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _load_cases(), ids=lambda c: c["name"])
+def test_single_pixel_closed_form(case):
+    geo = _single_pixel_geo(case)
+    p = orc.forward(geo, np.ones(1))[0]
+    expect = np.zeros(case["K"])
+    for k, v in case["taps"].items():
+        expect[int(k)] = v
+    # FP64 rounding of d*fs/c can put u a hair below an integer: that moves
+    # at most ~1e-12 of the weight to the neighbouring tap.
+    np.testing.assert_allclose(p, expect, rtol=1e-10, atol=1e-9)
+    # the brute-force form and the adjoint see the same two taps
+    np.testing.assert_allclose(orc.forward_dense(geo, np.ones(1))[0], expect, rtol=1e-10, atol=1e-9)
+    y = np.arange(case["K"], dtype=np.float64)[None, :] + 1.0
+    np.testing.assert_allclose(orc.adjoint(geo, y)[0], float(expect @ y[0]), rtol=1e-12)
+
+
+def _random_geo(dim, shape, n_sensors, K, seed, radius=None, spacing=1e-4, t0=0.0, amp=1.0):
+    rng = np.random.default_rng(seed)
+    shape3 = tuple(shape) + (1,) * (3 - len(shape))
+    sp = (spacing, spacing, spacing)
+    origin = ph.centred_origin(shape3, sp)
+    ext = max(shape) * spacing
+    if radius is None:
+        radius = ext + 1e-3
+    dirs = rng.normal(size=(n_sensors, dim))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    sensors = dirs * radius * rng.uniform(1.0, 1.5, size=(n_sensors, 1))
+    return orc.Geometry(dim, shape3, sp, origin, sensors, 1500.0, 40e6, K, t0, amp)
+
+
+def _distances(geo):
+    """Pixel-sensor distances computed here with numpy broadcasting, [S][N]."""
+    nx, ny, nz = geo.shape
+    xs = geo.origin[0] + geo.spacing[0] * np.arange(nx)
+    ys = geo.origin[1] + geo.spacing[1] * np.arange(ny)
+    zs = geo.origin[2] + geo.spacing[2] * np.arange(nz)
+    gz, gy, gx = np.meshgrid(zs, ys, xs, indexing="ij")
+    pts = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)[:, :geo.dim]
+    return np.linalg.norm(pts[None, :, :] - geo.sensors[:, None, :], axis=2)
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (7, 5)), (3, (4, 3, 5))])
+def test_sum_rule_partition_of_unity(dim, shape):
+    """sum_k p[s,k] = sum_i x_i / d_is when every tap lies inside [0, K)."""
+    geo = _random_geo(dim, shape, 6, 4096, seed=11)
+    x = np.random.default_rng(3).uniform(0, 1, geo.n_pixels)
+    p = orc.forward(geo, x)
+    d = _distances(geo)
+    np.testing.assert_allclose(p.sum(axis=1), (x[None, :] / d).sum(axis=1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (6, 4)), (3, (3, 4, 2))])
+def test_adjoint_of_ones(dim, shape):
+    """(A^T 1)_i = sum_s 1/d_is when both taps of every pair lie inside [0, K)."""
+    geo = _random_geo(dim, shape, 5, 4096, seed=5)
+    g = orc.adjoint(geo, np.ones((geo.n_sensors, geo.n_samples)))
+    np.testing.assert_allclose(g, (1.0 / _distances(geo)).sum(axis=0), rtol=1e-12)
+
+
+@pytest.mark.parametrize("dim,shape,K,t0", [(2, (4, 4), 64, 0.0), (3, (3, 3, 3), 64, 0.0),
+                                            (2, (5, 3), 40, 3e-7)])
+def test_bruteforce_matrix(dim, shape, K, t0):
+    """A equals the explicitly assembled matrix (hat evaluated at every sample,
+    no floor) and A^T equals its transpose, including truncated taps."""
+    geo = _random_geo(dim, shape, 4, K, seed=21, radius=1.2e-3, t0=t0)
+    M = orc.matrix(geo)
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=geo.n_pixels)
+    y = rng.normal(size=(geo.n_sensors, K))
+    np.testing.assert_allclose(orc.forward(geo, x).ravel(), M @ x, rtol=1e-11, atol=1e-9)
+    np.testing.assert_allclose(orc.adjoint(geo, y), M.T @ y.ravel(), rtol=1e-11, atol=1e-9)
+    assert np.count_nonzero(M) > 0
+
+
+@pytest.mark.parametrize("dim,shape,S,K", [(2, (33, 21), 17, 300), (3, (9, 7, 6), 11, 200),
+                                           (2, (20, 20), 8, 90)])
+def test_adjoint_identity(dim, shape, S, K):
+    """<A x, y> = <x, A^T y> with independently written forward and adjoint loops
+    (the last case truncates most arrivals)."""
+    geo = _random_geo(dim, shape, S, K, seed=99)
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=geo.n_pixels)
+    y = rng.normal(size=(S, K))
+    lhs = float(np.sum(orc.forward(geo, x) * y))
+    rhs = float(x @ orc.adjoint(geo, y))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0) * 10
+
+
+def test_linearity():
+    geo = _random_geo(2, (12, 9), 5, 256, seed=2)
+    rng = np.random.default_rng(4)
+    a, b = rng.normal(size=(2, geo.n_pixels))
+    np.testing.assert_allclose(orc.forward(geo, 2.5 * a - 0.5 * b),
+                               2.5 * orc.forward(geo, a) - 0.5 * orc.forward(geo, b),
+                               rtol=1e-11, atol=1e-9)
+
+
+def _tiny_system(seed=8):
+    geo = _random_geo(2, (3, 3), 4, 64, seed=seed, radius=1.0e-3)
+    M = orc.matrix(geo)
+    return geo, M
+
+
+def test_cgls_matches_lstsq():
+    """CGLS on a tiny full-rank system reaches numpy.linalg.lstsq."""
+    geo, M = _tiny_system()
+    assert np.linalg.matrix_rank(M) == geo.n_pixels
+    y = np.random.default_rng(6).normal(size=M.shape[0])
+    x_ls = np.linalg.lstsq(M, y, rcond=None)[0]
+    x, hist = orc.cgls(geo, y, n_iter=3 * geo.n_pixels, nonneg=False)
+    np.testing.assert_allclose(x, x_ls, rtol=1e-8, atol=1e-10 * np.abs(x_ls).max())
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+
+
+def test_landweber_matches_nnls():
+    """Projected Landweber with omega = 1/sigma_max^2 converges to the NNLS
+    solution (Lawson-Hanson, scipy.optimize.nnls) with active constraints."""
+    from scipy.optimize import nnls
+
+    geo, M = _tiny_system(seed=12)
+    x_star = np.array([1.0, -0.5, 0.8, 0.3, -0.2, 1.2, 0.0, 0.5, 0.9])
+    y = M @ x_star
+    x_nn, _ = nnls(M, y, maxiter=10000)
+    assert np.any(x_nn == 0.0)
+    sig = np.linalg.svd(M, compute_uv=False)
+    omega = 1.0 / sig[0] ** 2
+    x, hist = orc.landweber(geo, y, n_iter=20000, omega=omega, nonneg=True)
+    np.testing.assert_allclose(x, x_nn, atol=1e-8 * np.abs(x_nn).max())
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+
+
+def test_power_iteration_matches_svd():
+    geo, M = _tiny_system(seed=14)
+    lam = orc.power_iteration(geo, ph.power_start(geo.n_pixels), n_iter=200)
+    sig = np.linalg.svd(M, compute_uv=False)
+    assert abs(lam - sig[0] ** 2) <= 1e-6 * sig[0] ** 2
+
+
+def test_dc_matches_finite_differences():
+    """d/dc <g, A(x;c)> against central differences, on a geometry where no
+    arrival crosses a sample boundary within +-delta_c."""
+    for seed in range(50):
+        geo = _random_geo(2, (6, 5), 4, 128, seed=100 + seed)
+        d = _distances(geo)
+        c, dc_step = geo.c, 1e-2
+        u_lo = d * geo.fs / (c + dc_step)
+        u_hi = d * geo.fs / (c - dc_step)
+        if np.all(np.floor(u_lo) == np.floor(u_hi)):
+            break
+    else:
+        pytest.fail("no seed without sample-boundary crossings")
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0, 1, geo.n_pixels)
+    g = rng.normal(size=(geo.n_sensors, geo.n_samples))
+    f = lambda cc: float(np.sum(g * orc.forward(geo, x, c=cc)))
+    fd = (f(c + dc_step) - f(c - dc_step)) / (2 * dc_step)
+    an = orc.dc(geo, x, g)
+    assert abs(an - fd) <= 1e-6 * abs(fd)
+
+
+def test_tv_constant_and_fd():
+    eps = 1e-4
+    img = np.full((5, 7), 0.3)
+    assert abs(orc.tv(img, eps) - img.size * eps) <= 1e-15
+    assert np.all(orc.tv_grad(img, eps) == 0.0)
+    rng = np.random.default_rng(9)
+    img = rng.uniform(0, 1, (6, 5))
+    g = orc.tv_grad(img, eps)
+    h = 1e-6
+    fd = np.zeros_like(img)
+    for idx in np.ndindex(img.shape):
+        e = np.zeros_like(img)
+        e[idx] = h
+        fd[idx] = (orc.tv(img + e, eps) - orc.tv(img - e, eps)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-7)
+
+
+def test_tv_hand_value():
+    """2x2 image [[0,1],[0,0]]: four terms worked out by hand."""
+    eps = 1e-4
+    img = np.array([[0.0, 1.0], [0.0, 0.0]])
+    # (0,0): dx=1, dy=0; (0,1): dx=0, dy=-1; (1,0): dx=0, dy=0; (1,1): 0, 0
+    expect = 2 * np.sqrt(1 + eps * eps) + 2 * eps
+    assert abs(orc.tv(img, eps) - expect) <= 1e-15
+
+
+def test_monotone_residual_landweber():
+    prob = ph.custom(2, (16, 16), (1e-4, 1e-4), ph.ring_sensors(12, 2.5e-3), 160, seed=4)
+    geo = orc.Geometry.of(prob)
+    y = orc.forward(geo, prob.x_true)
+    lam = orc.power_iteration(geo, ph.power_start(geo.n_pixels), 50)
+    _, hist = orc.landweber(geo, y, 25, omega=1.0 / lam)
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+    assert hist[-1] < 0.5 * hist[0]
