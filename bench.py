@@ -1,0 +1,350 @@
+"""Benchmark: iterative photoacoustic reconstruction on one or more GB300s.
+
+A step is one full reconstruction of one frame of the 2D ring workload
+(256x256 pixels at 0.1 mm, 256-sensor ring of radius 20 mm, 2048 samples at
+40 MHz, Bezier vessel phantom, 1% noise, 50 CGLS iterations with FP64
+reductions), with the measured traces already resident in device memory.
+``value`` is pixel-sensor updates per second (one update = one (pixel, sensor)
+pair evaluated by A or A^T) summed over all ranks; every rank reconstructs its
+own frame (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+reference arm), on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel·sensor updates/s for A and Aᵀ; recon frames/s batched vs plain, % FP32 peak"
+UNIT = "pixel·sensor updates/s"
+WORKLOAD = "2D 256x256 0.1mm, 256-sensor ring R=20mm, 2048 samples @40MHz, c=1500, vessel phantom + 1% noise, 50 CGLS (FP64 reductions)"
+N_ITER = 50
+FLOPS_PER_PAIR = 18  # 9 FP32 instructions per pair (FFMA-equivalent, 2 flop each)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cgls_launches(n_iter: int) -> int:
+    """Kernels of one CGLS reconstruction: setup (A, reduce, pack, A^T, reduce),
+    7 per iteration (A, reduce, update, reduce, A^T, reduce, p-update), final clamp."""
+    return 5 + 7 * n_iter + 1
+
+
+def cgls_applications(n_iter: int) -> int:
+    return 2 + 2 * n_iter
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: the cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, y, target_s: float = 15.0):
+    """Time the FP64 oracle's CGLS on the workload: as many iterations as fit in
+    about target_s seconds of host time.  Returns (pairs/s, seconds, iterations)."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores()))
+    from oracle import oracle as orc
+    geo = orc.Geometry.of(prob)
+    t = time.perf_counter()
+    orc.cgls(geo, y, 1)  # 4 applications
+    per_app = (time.perf_counter() - t) / 4.0
+    n_it = max(1, int((target_s / per_app - 2) / 2))
+    t = time.perf_counter()
+    orc.cgls(geo, y, n_it)
+    dt = time.perf_counter() - t
+    apps = cgls_applications(n_it)
+    return prob.pairs * apps / dt, dt, n_it
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from paper_2404_10928_gb300 import phantoms as ph
+    from oracle import oracle as orc
+    prob = ph.ring_vessels()
+    geo = orc.Geometry.of(prob)
+    y = ph.add_noise(orc.forward(geo, prob.x_true), prob.noise_unit, prob.noise_level)
+    y = y.astype(np.float32).astype(np.float64)
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores()))
+    n_it = 2  # bounded sample per step: 2 CGLS iterations = 6 operator applications
+    for _ in range(args.warmup):
+        orc.cgls(geo, y, 0)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        orc.cgls(geo, y, n_it)
+        times.append(time.perf_counter() - t)
+    apps = cgls_applications(n_it)
+    total = sum(times)
+    value = prob.pairs * apps * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n_it} CGLS iterations per step "
+                   f"({apps} operator applications of {prob.pairs} pairs)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle", "sample": f"{n_it} CGLS iterations per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def read_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == kernel and not line.startswith("#"):
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2404_10928_gb300 import build, phantoms as ph
+    build.build()
+    from paper_2404_10928_gb300.api import Plan
+
+    prob = ph.ring_vessels(seed=1002)
+    # each rank reconstructs its own frame (same geometry, its own noise draw)
+    noise = np.random.default_rng(2003 + rank).standard_normal(prob.noise_unit.shape)
+    plan = Plan.from_problem(prob)
+    x_true = torch.tensor(prob.x_true, dtype=torch.float32, device=dev)
+    clean = plan.forward(x_true).cpu().numpy().astype(np.float64)
+    y_host = ph.add_noise(clean, noise, prob.noise_level).astype(np.float32)
+    y = torch.tensor(y_host, device=dev)
+    x = torch.zeros(prob.n_pixels, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timing: bool):
+        x.zero_()
+        plan.reconstruct(y, "cgls", N_ITER, out=x, kernel_timing=timing)
+
+    for _ in range(max(args.warmup, 0)):
+        step(True)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    fwd_ms = adj_ms = 0.0
+    n_fwd = n_adj = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict L2 between timed steps
+            starts[i].record(stream)
+            step(True)
+            ends[i].record(stream)
+            ends[i].synchronize()
+            kt = plan.kernel_times()
+            fwd_ms += kt["fwd_ms"]
+            adj_ms += kt["adj_ms"]
+            n_fwd += kt["n_fwd"]
+            n_adj += kt["n_adj"]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    apps = cgls_applications(N_ITER)
+    pairs_all = prob.pairs * apps * args.steps * world
+    value = pairs_all / (total_ms * 1e-3)
+
+    # end to end through the host-buffer entry point (pinned buffers, copies inside)
+    y_pin = torch.empty(y_host.shape, dtype=torch.float32).pin_memory()
+    y_pin.copy_(torch.from_numpy(y_host))
+    x_pin = torch.zeros(prob.n_pixels, dtype=torch.float32).pin_memory()
+    y_np, x_np = y_pin.numpy(), x_pin.numpy()
+    for _ in range(2):
+        x_np[:] = 0
+        plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter()
+    for _ in range(args.steps):
+        x_np[:] = 0
+        plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)
+    e2e_t = time.perf_counter() - e2e_t
+    if dist:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = pairs_all / e2e_t
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, n_it = oracle_sample(prob, y_host.astype(np.float64))
+        cpu = {"value": rate, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores())),
+               "kind": "oracle",
+               "sample": f"FP64 oracle CGLS, {n_it} iterations ({cgls_applications(n_it)} operator "
+                         f"applications) of the same frame, {secs:.1f} s"}
+
+    if rank == 0:
+        import json as _json
+        peaks = {}
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk):
+            peaks = _json.load(open(pk))
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        dom_is_adj = adj_ms >= fwd_ms
+        launch_ms = (adj_ms / max(n_adj, 1)) if dom_is_adj else (fwd_ms / max(n_fwd, 1))
+        achieved = prob.pairs * FLOPS_PER_PAIR / (launch_ms * 1e-3) / 1e12
+        kname = "k_adjoint<2>" if dom_is_adj else "k_forward<2>"
+        clk = clocks.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_rank_per_step": 1,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "pairs_per_application": prob.pairs,
+                       "applications_per_step": apps, "parallelism": f"frame-parallel x{world}"},
+            "frames_per_s": world * args.steps / (total_ms * 1e-3),
+            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": read_traffic(kname),
+                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                         "flops_per_launch": prob.pairs * FLOPS_PER_PAIR},
+            "kernels": {"adjoint_ms_per_launch": adj_ms / max(n_adj, 1),
+                        "forward_ms_per_launch": fwd_ms / max(n_fwd, 1),
+                        "adjoint_pairs_per_s": prob.pairs / (adj_ms / max(n_adj, 1) * 1e-3),
+                        "forward_pairs_per_s": prob.pairs / (fwd_ms / max(n_fwd, 1) * 1e-3),
+                        "share_of_step": (adj_ms + fwd_ms) / total_ms if world == 1 else None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(y_host.nbytes + prob.n_pixels * 4),
+                    "d2h_bytes_per_step": int(prob.n_pixels * 4)},
+            "gpu_launches": cgls_launches(N_ITER) * args.steps,
+            "clocks": clk,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

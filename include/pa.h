@@ -1,0 +1,183 @@
+/*
+ * pa.h -- C ABI of the GB300 (sm_103a) library for iterative photoacoustic
+ * reconstruction with a matrix-free time-of-flight system operator.
+ *
+ * What the library computes (model of Sec. 3.4, Eq. 6, discretised):
+ *   A pixel at r_i and a sensor at r_s, distance d = |r_i - r_s|, exchange the
+ *   sample time u = d*fs/c - t0*fs (in samples).  The forward operator A maps an
+ *   initial-pressure image x (the p_0 of Eq. 1-2) to sensor traces
+ *       p[s,k] = amp * sum_i x_i * h(u_is - k) / d_is,   h(t) = max(0, 1-|t|),
+ *   i.e. the delta of Eq. 6 spread over the two neighbouring samples by linear
+ *   interpolation and weighted by the 1/distance spreading of Eq. 7.  Taps
+ *   outside 0..K-1 are dropped.  The adjoint A^T is delay-and-sum
+ *   back-projection with the same hat and weight.  The reconstruction minimises
+ *   the data term ||A x - y||^2 of Eq. 8 (whose gradient 2 A^T (A x - y) is the
+ *   line the paper profiles, Table 3) by projected Landweber or by CGLS.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: pixel (i,j,l) sits at origin + (i*dx, j*dy, l*dz) metres; images are
+ *     row-major [nz][ny][nx] float32 (x fastest).  2D grids use dim = 2, nz = 1.
+ *   - Sensors: host array [n_sensors][dim] of float64 metres.
+ *   - Traces: row-major [n_sensors][n_samples] (sample fastest); sample k is at
+ *     time t0 + k/fs.
+ *   - Every *_dev pointer is CUDA device memory owned by the caller (e.g. a
+ *     torch tensor).  The library never frees it and keeps no reference to it
+ *     after the call returns, except that pa_reconstruct caches a CUDA graph
+ *     keyed on (y_dev, x_dev) -- the graph is rebuilt when they change.
+ *   - Streams: pa_stream is the same type as cudaStream_t (NULL = legacy default
+ *     stream).  Calls only enqueue work on that stream unless stated otherwise;
+ *     results are valid once the stream has synchronised.
+ *   - Plans are not re-entrant: one plan owns one workspace, so calls on the
+ *     same plan must not overlap (use one plan per stream or thread).  Distinct
+ *     plans are independent.
+ *   - Errors: every call returns pa_status; pa_last_error() gives a message for
+ *     the calling thread.  Errors detected on the device (a bounded wait that
+ *     gave up, a failed internal check) are latched in the plan and reported by
+ *     pa_plan_sync_status() or by the next call that synchronises.
+ */
+#ifndef PA_H_
+#define PA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_VERSION 1
+
+typedef struct pa_plan pa_plan;
+typedef struct CUstream_st *pa_stream; /* == cudaStream_t */
+
+typedef enum {
+  PA_OK = 0,
+  PA_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, a bad enum */
+  PA_ERR_GEOMETRY = 2,      /* a sensor closer than half a pixel, NaN, dims */
+  PA_ERR_CUDA = 3,          /* a CUDA runtime call failed; see pa_last_error() */
+  PA_ERR_OOM = 4,           /* device allocation failed */
+  PA_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  PA_ERR_DEVICE_CHECK = 6,  /* an internal device-side consistency check failed */
+  PA_ERR_UNSUPPORTED = 7    /* valid request this build does not handle */
+} pa_status;
+
+typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1 } pa_method;
+typedef enum { PA_F32 = 0, PA_F16 = 1 } pa_dtype;
+
+/* Regular grid of pixel centres (Sec. 3.4: r_ij, the Cartesian pixel
+ * coordinates of Eq. 6-7).  dim is 2 or 3; nx, ny, nz >= 1 (nz == 1 for 2D);
+ * spacings > 0 metres; origin = centre of pixel (0,0,0). */
+typedef struct {
+  int dim;
+  int nx, ny, nz;
+  double dx, dy, dz;
+  double origin[3];
+} pa_grid;
+
+/* Optional plan settings.  t0: time of sample 0 in seconds (default 0; t0 = 1/fs
+ * reproduces the 1-based t = s*dt of Eq. 6).  amp_scale: global amplitude of the
+ * model (default 1; 1/(2*pi*c) gives Eq. 6's prefactor).  y_dtype: storage type
+ * of the measured traces y passed to pa_reconstruct (PA_F32 or PA_F16; the
+ * arithmetic stays FP32). */
+typedef struct {
+  double t0;
+  double amp_scale;
+  int y_dtype;
+} pa_plan_opts;
+
+/* Reconstruction settings (fill with pa_recon_opts_default first).
+ *   omega        Landweber step.  <= 0: 1/sigma^2 with sigma^2 = largest
+ *                eigenvalue of A^T A from power_iters power-iteration steps.
+ *   nonneg       1: x >= 0 (Landweber: projection every step; CGLS: once at the
+ *                end, after the unconstrained iterations).
+ *   power_iters  steps of the power iteration when omega <= 0 (default 50).
+ *   power_v0_dev start vector [N] float32 on the device, or NULL for all ones.
+ *   residual_history_host  NULL, or n_iter+1 doubles receiving ||y - A x_n||^2
+ *                for n = 0..n_iter; when given, the call waits for the stream.
+ *   use_graph    1: the iteration is captured once as a CUDA graph and replayed.
+ *   kernel_timing 1: CUDA events bracket every A and A^T gather launch; read the
+ *                totals with pa_plan_kernel_times after the stream finished. */
+typedef struct {
+  double omega;
+  int nonneg;
+  int power_iters;
+  const float *power_v0_dev;
+  double *residual_history_host;
+  int use_graph;
+  int kernel_timing;
+} pa_recon_opts;
+
+/* Facts about a plan (sizes, tiling, memory), for logging and benchmarks. */
+typedef struct {
+  int64_t n_pixels;
+  int64_t n_sensors;
+  int64_t n_samples;
+  int64_t pairs;            /* n_pixels * n_sensors: one application of A or A^T */
+  int tile[3];              /* pixel tile of the gather kernels */
+  int window;               /* trace samples staged per (tile, sensor) */
+  int cluster;              /* CTAs per tile in the adjoint (sensor split) */
+  int fwd_bins;             /* samples per forward-gather CTA */
+  int64_t device_bytes;     /* device memory owned by the plan */
+} pa_plan_info;
+
+void pa_recon_opts_default(pa_recon_opts *opts);
+
+/* Create a plan for one geometry.  Validates the geometry (PA_ERR_GEOMETRY if
+ * any sensor lies closer than half the smallest pixel spacing to a pixel
+ * centre), uploads it and builds the per-(pixel tile, sensor) reference table on
+ * the current CUDA device.  Blocks until the table is built.  c > 0 (m/s),
+ * fs > 0 (Hz), n_samples >= 2, n_sensors >= 1.  *out receives the plan. */
+pa_status pa_plan_create(pa_plan **out, const double *sensors_xyz, int n_sensors,
+                         const pa_grid *grid, double c, double fs, int n_samples,
+                         const pa_plan_opts *opts);
+
+/* Free the plan and its device memory.  NULL-safe.  Waits for the device. */
+pa_status pa_plan_destroy(pa_plan *plan);
+
+/* Change the speed of sound (rebuilds the reference table; blocks). */
+pa_status pa_plan_set_sound_speed(pa_plan *plan, double c);
+
+/* Wait for the device and report (then clear) device-side error flags. */
+pa_status pa_plan_sync_status(pa_plan *plan);
+
+pa_status pa_plan_query(const pa_plan *plan, pa_plan_info *info);
+
+/* p = A x (Eq. 6 discretised, see top).  x_dev: [N] float32; p_dev: [S][K]
+ * float32, fully overwritten. */
+pa_status pa_forward(pa_plan *plan, const float *x_dev, float *p_dev, pa_stream stream);
+
+/* x = A^T p (delay-and-sum back-projection; the adjoint of pa_forward).
+ * p_dev: [S][K] float32; x_dev: [N] float32, fully overwritten. */
+pa_status pa_adjoint(pa_plan *plan, const float *p_dev, float *x_dev, pa_stream stream);
+
+/* Largest eigenvalue of A^T A by n_iter power-iteration steps from v0_dev ([N]
+ * float32, NULL = ones).  Blocks; *sigma2 receives the estimate. */
+pa_status pa_power_iteration(pa_plan *plan, int n_iter, const float *v0_dev, double *sigma2,
+                             pa_stream stream);
+
+/* Iterative reconstruction minimising ||A x - y||^2 (Eq. 8 data term).
+ * y_dev: [S][K] measured traces in the plan's y_dtype; x_dev: [N] float32, in:
+ * start image x_0, out: result.  n_iter >= 0.  opts may be NULL (defaults). */
+pa_status pa_reconstruct(pa_plan *plan, pa_method method, int n_iter, const void *y_dev,
+                         float *x_dev, const pa_recon_opts *opts, pa_stream stream);
+
+/* Same as pa_reconstruct with HOST buffers (pinned memory recommended): copies
+ * y_host to the device, runs, copies the result to x_host and waits. */
+pa_status pa_reconstruct_host(pa_plan *plan, pa_method method, int n_iter, const void *y_host,
+                              float *x_host, const pa_recon_opts *opts, pa_stream stream);
+
+/* Sum of the device durations (ms) and counts of the A and A^T gather launches
+ * of the last reconstruction run with kernel_timing = 1.  Call after the stream
+ * finished.  Any pointer may be NULL. */
+pa_status pa_plan_kernel_times(pa_plan *plan, double *fwd_ms, int *n_fwd, double *adj_ms,
+                               int *n_adj);
+
+const char *pa_status_string(pa_status status);
+const char *pa_last_error(void);
+int pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H_ */

@@ -1,0 +1,204 @@
+"""Python face of the library: a ``Plan`` around the C ABI of ``include/pa.h``.
+
+Device memory and streams come from PyTorch; every step of the computation
+runs in the library's own CUDA kernels.  Methods check tensor shapes, dtypes
+and devices, then pass raw pointers and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PA_CGLS, PA_F16, PA_F32, PA_LANDWEBER, check
+
+METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS}
+
+
+def _stream_handle(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Plan:
+    """One imaging geometry on one GPU (see ``pa_plan_create``)."""
+
+    def __init__(self, sensors, shape, spacing, origin, c: float, fs: float, n_samples: int,
+                 t0: float = 0.0, amp_scale: float = 1.0, y_dtype: str = "f32",
+                 dim: Optional[int] = None, device=None):
+        self._lib = _lib.load()
+        sensors = np.ascontiguousarray(sensors, dtype=np.float64)
+        dim = int(dim if dim is not None else sensors.shape[1])
+        shape = tuple(int(v) for v in shape) + (1,) * (3 - len(shape))
+        spacing = tuple(float(v) for v in spacing) + (float(spacing[-1]),) * (3 - len(spacing))
+        origin = tuple(float(v) for v in origin) + (0.0,) * (3 - len(origin))
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.dim, self.shape, self.spacing, self.origin = dim, shape, spacing, origin
+        self.n_sensors = int(sensors.shape[0])
+        self.n_samples = int(n_samples)
+        self.n_pixels = shape[0] * shape[1] * shape[2]
+        self.c, self.fs, self.t0, self.amp_scale = float(c), float(fs), float(t0), float(amp_scale)
+        self.y_dtype = y_dtype
+        self._sensors = sensors  # keep alive for the call
+        grid = _lib.pa_grid(dim, shape[0], shape[1], shape[2], spacing[0], spacing[1], spacing[2],
+                            (ctypes.c_double * 3)(*origin))
+        opts = _lib.pa_plan_opts(self.t0, self.amp_scale, PA_F16 if y_dtype == "f16" else PA_F32)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self._lib.pa_plan_create(ctypes.byref(handle),
+                                          sensors.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          self.n_sensors, ctypes.byref(grid), self.c, self.fs,
+                                          self.n_samples, ctypes.byref(opts))
+        check(st, "pa_plan_create")
+        self._h = handle
+
+    @classmethod
+    def from_problem(cls, prob, c: Optional[float] = None, y_dtype: Optional[str] = None, **kw):
+        return cls(prob.sensors, prob.shape, prob.spacing, prob.origin,
+                   prob.c if c is None else c, prob.fs, prob.n_samples, t0=prob.t0,
+                   amp_scale=prob.amp_scale,
+                   y_dtype=y_dtype or prob.extra.get("y_dtype", "f32"), dim=prob.dim, **kw)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pa_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- helpers ----------------------------------------------------------
+    def _check_tensor(self, t: torch.Tensor, numel: int, name: str, dtype=torch.float32):
+        if not isinstance(t, torch.Tensor) or t.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{name} must be contiguous with {numel} elements")
+
+    def info(self) -> dict:
+        inf = _lib.pa_plan_info()
+        check(self._lib.pa_plan_query(self._h, ctypes.byref(inf)), "pa_plan_query")
+        return {"n_pixels": inf.n_pixels, "n_sensors": inf.n_sensors, "n_samples": inf.n_samples,
+                "pairs": inf.pairs, "tile": tuple(inf.tile), "window": inf.window,
+                "cluster": inf.cluster, "fwd_bins": inf.fwd_bins,
+                "device_bytes": inf.device_bytes}
+
+    def set_sound_speed(self, c: float):
+        check(self._lib.pa_plan_set_sound_speed(self._h, float(c)), "pa_plan_set_sound_speed")
+        self.c = float(c)
+
+    def sync_status(self):
+        check(self._lib.pa_plan_sync_status(self._h), "pa_plan_sync_status")
+
+    # -- operators --------------------------------------------------------
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """p = A x: [N] image -> [S][K] traces."""
+        self._check_tensor(x, self.n_pixels, "x")
+        if out is None:
+            out = torch.empty((self.n_sensors, self.n_samples), device=self.device,
+                              dtype=torch.float32)
+        self._check_tensor(out, self.n_sensors * self.n_samples, "out")
+        check(self._lib.pa_forward(self._h, x.data_ptr(), out.data_ptr(),
+                                   _stream_handle(self.device)), "pa_forward")
+        return out
+
+    def adjoint(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """x = A^T p: [S][K] traces -> [N] image."""
+        self._check_tensor(p, self.n_sensors * self.n_samples, "p")
+        if out is None:
+            out = torch.empty(self.n_pixels, device=self.device, dtype=torch.float32)
+        self._check_tensor(out, self.n_pixels, "out")
+        check(self._lib.pa_adjoint(self._h, p.data_ptr(), out.data_ptr(),
+                                   _stream_handle(self.device)), "pa_adjoint")
+        return out
+
+    def power_iteration(self, n_iter: int = 50, v0: Optional[torch.Tensor] = None) -> float:
+        if v0 is not None:
+            self._check_tensor(v0, self.n_pixels, "v0")
+        out = ctypes.c_double()
+        check(self._lib.pa_power_iteration(self._h, int(n_iter),
+                                           v0.data_ptr() if v0 is not None else None,
+                                           ctypes.byref(out), _stream_handle(self.device)),
+              "pa_power_iteration")
+        return out.value
+
+    def _opts(self, omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing):
+        o = _lib.pa_recon_opts()
+        self._lib.pa_recon_opts_default(ctypes.byref(o))
+        o.omega = float(omega)
+        o.nonneg = int(bool(nonneg))
+        o.power_iters = int(power_iters)
+        o.power_v0_dev = power_v0.data_ptr() if power_v0 is not None else None
+        o.residual_history_host = (hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                   if hist is not None else None)
+        o.use_graph = int(bool(use_graph))
+        o.kernel_timing = int(bool(kernel_timing))
+        return o
+
+    def reconstruct(self, y: torch.Tensor, method: str = "cgls", n_iter: int = 50,
+                    x0: Optional[torch.Tensor] = None, omega: float = 0.0, nonneg: bool = True,
+                    power_iters: int = 50, power_v0: Optional[torch.Tensor] = None,
+                    history: bool = False, use_graph: bool = True, kernel_timing: bool = False,
+                    out: Optional[torch.Tensor] = None):
+        """Minimise ||A x - y||^2 (Landweber with projection, or CGLS + final clamp).
+
+        Returns x (and the residual history ||y - A x_n||^2, n = 0..n_iter, when
+        ``history`` is set).  ``out`` (if given) is used in place: its contents
+        are the start image unless ``x0`` is given."""
+        ydt = torch.float16 if self.y_dtype == "f16" else torch.float32
+        self._check_tensor(y, self.n_sensors * self.n_samples, "y", ydt)
+        if out is None:
+            out = (x0.clone() if x0 is not None else
+                   torch.zeros(self.n_pixels, device=self.device, dtype=torch.float32))
+        elif x0 is not None:
+            out.copy_(x0)
+        self._check_tensor(out, self.n_pixels, "x")
+        if power_v0 is not None:
+            self._check_tensor(power_v0, self.n_pixels, "power_v0")
+        hist = np.zeros(n_iter + 1) if history else None
+        o = self._opts(omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing)
+        check(self._lib.pa_reconstruct(self._h, METHODS[method], int(n_iter), y.data_ptr(),
+                                       out.data_ptr(), ctypes.byref(o),
+                                       _stream_handle(self.device)), "pa_reconstruct")
+        return (out, hist) if history else out
+
+    def reconstruct_host(self, y: np.ndarray, method: str = "cgls", n_iter: int = 50,
+                         x0: Optional[np.ndarray] = None, omega: float = 0.0, nonneg: bool = True,
+                         power_iters: int = 50, use_graph: bool = True,
+                         x_out: Optional[np.ndarray] = None) -> np.ndarray:
+        """Same as ``reconstruct`` with host (numpy, ideally pinned) buffers."""
+        ydt = np.float16 if self.y_dtype == "f16" else np.float32
+        if y.dtype != ydt or not y.flags.c_contiguous or y.size != self.n_sensors * self.n_samples:
+            raise ValueError(f"y must be a contiguous {ydt} array of {self.n_sensors}x{self.n_samples}")
+        if x_out is None:
+            x_out = (np.array(x0, dtype=np.float32) if x0 is not None
+                     else np.zeros(self.n_pixels, dtype=np.float32))
+        if x_out.dtype != np.float32 or not x_out.flags.c_contiguous or x_out.size != self.n_pixels:
+            raise ValueError("x_out must be a contiguous float32 array of n_pixels")
+        o = self._opts(omega, nonneg, power_iters, None, None, use_graph, False)
+        check(self._lib.pa_reconstruct_host(self._h, METHODS[method], int(n_iter), y.ctypes.data,
+                                            x_out.ctypes.data, ctypes.byref(o),
+                                            _stream_handle(self.device)), "pa_reconstruct_host")
+        return x_out
+
+    def kernel_times(self) -> dict:
+        fm, am = ctypes.c_double(), ctypes.c_double()
+        fn, an = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.pa_plan_kernel_times(self._h, ctypes.byref(fm), ctypes.byref(fn),
+                                             ctypes.byref(am), ctypes.byref(an)),
+              "pa_plan_kernel_times")
+        return {"fwd_ms": fm.value, "n_fwd": fn.value, "adj_ms": am.value, "n_adj": an.value}

@@ -1,0 +1,220 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+pa_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define PA_CUDA(call)                                                         \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::pa::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define PA_TRY(call)                  \
+  do {                                \
+    pa_status s_ = (call);            \
+    if (s_ != PA_OK) return s_;       \
+  } while (0)
+
+// device error bits (latched in plan->d_err)
+enum : int {
+  ERR_WAIT_TIMEOUT = 1,   // a bounded mbarrier / flag wait gave up
+  ERR_WINDOW = 2,         // a tile's arrival span does not fit the staged window
+  ERR_INDEX = 4           // an index check of a checked build failed
+};
+
+// sentinel for (tile, sensor) pairs whose taps all fall outside [0, K)
+constexpr int kSkip = INT_MIN;
+
+// ---------------------------------------------------------------------------
+// per (pixel tile, sensor) time-of-flight reference, 32 bytes.
+//
+// For a pixel at tile centre + delta, with e = centre - sensor and
+// d_ref = |e|, the exact identity
+//      u - u_ref = kappa * (d - d_ref) = kappa * (2 e.delta + |delta|^2) / (d + d_ref)
+// lets FP32 evaluate the sample position with the error of the small
+// difference instead of the error of d itself (u reaches ~1300 samples, where
+// an FP32 ulp is ~1e-4 samples).  u_ref is formed in FP64 when the table is
+// built and stored relative to the start of the staged trace window.
+// ---------------------------------------------------------------------------
+struct __align__(16) TileRef {
+  int klo;      // first sample of the staged window (even), or kSkip
+  float fref;   // u_ref - klo - 0.5
+  float dref;   // |centre - sensor|
+  float dref2;  // d_ref^2
+  float ex2k;   // 2*kappa*(centre - sensor).x
+  float ey2k;   // 2*kappa*(centre - sensor).y
+  float ez2k;   // 2*kappa*(centre - sensor).z (0 in 2D)
+  int flags;    // kNear: the sensor is much closer to some pixel than to the centre
+};
+// d^2 = d_ref^2 + q/kappa cancels when d << d_ref; such pairs form d^2 from the
+// explicit offset vector instead (sensors inside or next to the grid).
+constexpr int kNear = 1;
+static_assert(sizeof(TileRef) == 32, "TileRef must be 32 bytes");
+
+struct GridF {
+  int nx, ny, nz;
+  int ntx, nty, ntz;  // tiles per axis
+  float hdx, hdy, hdz;  // half spacings (FP32)
+};
+
+// kernel modes
+enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2 };
+enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
+
+struct AdjParams {
+  const TileRef* table;   // [ntiles][S]
+  const float2* packed;   // [S][Kp] (pmid, dp) with PAD zero samples on each side
+  int S, Kp, pad, L;
+  GridF g;
+  float kappa, inv_kappa, half_inv_kappa, amp;
+  int mode;
+  int nonneg;
+  float* out;             // [N] image (ADJ_STORE / ADJ_NORM) or x updated in place
+  const double* omega;    // device scalar (ADJ_LANDWEBER)
+  double* partials;       // one FP64 partial of ||out||^2 per CTA (ADJ_NORM)
+  int* err;
+  int sensors_per_rank;
+};
+
+struct FwdParams {
+  const TileRef* table;   // [ntiles][S]
+  const int2* krange;     // [S][ntiles]: (first tap, last tap) or (kSkip, .)
+  const int* order;       // [S * nwin] CTA -> work item s * nwin + window, heaviest first
+  const float* x;         // [N]
+  int S, K, W, ntiles, nwin;
+  GridF g;
+  float kappa, inv_kappa, half_inv_kappa, amp;
+  int mode;
+  float* out;             // [S][K]
+  const void* y;          // [S][K] measured traces (FWD_RESID), f32 or f16
+  int y_f16;
+  double* partials;       // one FP64 partial per CTA (FWD_RESID / FWD_NORM)
+  int* err;
+};
+
+// tile shapes
+template <int DIM> struct Tile;
+template <> struct Tile<2> { static constexpr int X = 32, Y = 32, Z = 1; };
+template <> struct Tile<3> { static constexpr int X = 16, Y = 8, Z = 8; };
+constexpr int kTilePixels = 1024;
+static_assert(Tile<2>::X * Tile<2>::Y * Tile<2>::Z == kTilePixels, "tile");
+static_assert(Tile<3>::X * Tile<3>::Y * Tile<3>::Z == kTilePixels, "tile");
+
+// adjoint kernel shape
+constexpr int kAdjWarps = 8;                 // compute warps (+1 producer warp)
+constexpr int kAdjThreads = 32 * (kAdjWarps + 1);
+constexpr int kAdjPPT = kTilePixels / (32 * kAdjWarps);  // pixels per compute thread
+constexpr int kAdjSB = 8;                    // sensors per pipeline stage
+constexpr int kAdjStages = 4;
+
+// forward kernel shape
+constexpr int kFwdWarps = 8;
+constexpr int kFwdThreads = 32 * kFwdWarps;
+constexpr int kFwdBins = 256;                // samples per CTA
+
+// ---------------------------------------------------------------------------
+// launchers (pa_ops.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const double* sensors_dev,
+                               int S, const pa_grid& grid, const GridF& g, double kappa,
+                               double t0fs, int K, int L, double hmin, int* err, cudaStream_t st);
+cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
+                        cudaStream_t st);
+cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st);
+cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
+int adjoint_smem_bytes(int L);
+cudaError_t configure_kernels(int smem_adj, int smem_fwd);
+int forward_smem_bytes(int ntiles);
+pa_status validate_grid(const pa_grid* g);
+
+// reductions and vector updates
+enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3, OP_SIGMA = 4 };
+cudaError_t launch_reduce(const double* partials, int n, double* out_sum, int op,
+                          const double* other, double* out2, cudaStream_t st);
+cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
+                           const float* q, float2* packed, const double* alpha, int N, int S,
+                           int K, int Kp, int pad, double* partials, int nblk_x, int nblk_r,
+                           cudaStream_t st);
+cudaError_t launch_axpby(float* p, const float* s, const double* beta, int N, cudaStream_t st);
+cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
+                         cudaStream_t st);
+cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
+cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
+cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
+cudaError_t launch_norm_partials(const float* v, int64_t n, double* partials, int nblk,
+                                 cudaStream_t st);
+
+}  // namespace pa
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct pa_plan {
+  int device = 0;
+  int dim = 2;
+  pa_grid grid{};
+  int S = 0, K = 0;
+  double c = 0, fs = 0, t0 = 0, amp = 1;
+  int y_f16 = 0;
+  std::vector<double> sensors;  // host copy [S][dim]
+
+  // tiling
+  pa::GridF g{};
+  int ntiles = 0;
+  int L = 0;        // staged window (samples)
+  int pad = 0;      // zero samples on each side of a packed trace
+  int Kp = 0;       // packed row length (even)
+  int cluster = 1;  // adjoint CTAs per tile
+  int fwd_windows = 0;
+
+  // device memory owned by the plan
+  double* d_sensors = nullptr;
+  pa::TileRef* d_table = nullptr;
+  int2* d_krange = nullptr;
+  int* d_order = nullptr;
+  float2* d_packed = nullptr;
+  int* d_err = nullptr;
+  double* d_partials = nullptr;
+  int n_partials = 0;
+  // reconstruction workspace (allocated on first use)
+  float* d_ra = nullptr;
+  float* d_rb = nullptr;
+  float* d_q = nullptr;
+  float* d_pv = nullptr;
+  float* d_sv = nullptr;
+  double* d_scal = nullptr;   // scalar records, see pa_recon.cu
+  int scal_cap = 0;
+  void* d_yhost = nullptr;    // device copies for pa_reconstruct_host
+  float* d_xhost = nullptr;
+  int64_t bytes = 0;
+
+  // graphs
+  cudaStream_t cap_stream = nullptr;
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> fwd_ev, adj_ev;  // pairs (start, stop)
+  };
+  std::map<std::tuple<int, int, const void*, float*, double, int, int, const float*, int>,
+           GraphEntry>
+      graphs;
+  GraphEntry direct;                 // timing events of runs without a graph
+  const GraphEntry* last_timed = nullptr;
+};

@@ -1,0 +1,982 @@
+// Device kernels of the time-of-flight operator A, its adjoint A^T, and the
+// vector steps of the Landweber / CGLS iterations.
+//
+// Model (Sec. 3.4, Eq. 6 discretised with a linear-interpolation hat and the
+// 1/distance weight of Eq. 7):
+//     p[s,k] = amp * sum_i x_i h(u_is - k) / d_is,   u = d fs / c - t0 fs.
+// Both operators are gathers: every output element is produced by exactly one
+// CTA, no global atomics, and all floating-point sums run in a fixed order, so
+// results are bitwise reproducible.
+#include <cooperative_groups.h>
+
+#include "pa_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pa {
+
+// ---------------------------------------------------------------------------
+// PTX helpers (sm_90+ mbarrier / bulk-copy / approximate SFU forms)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// MUFU reciprocal square root and reciprocal: relative error about 2^-22.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A wait that gives up after ~2 s (or 2^30 polls) instead of spinning forever.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity);
+}
+
+// 1D bulk copy global -> shared, completion counted in bytes on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Deterministic FP64 block sum: xor-tree within warps, warps in index order.
+template <int NW>
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NW; ++w) t += s_red[w];
+  return t;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// per-pixel geometry shared by A and A^T (identical FP32 arithmetic, so the two
+// kernels apply exactly the same matrix entries)
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void pixel_local(int p, int& lx, int& ly, int& lz) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y;
+  lx = p % TX;
+  ly = (p / TX) % TY;
+  lz = p / (TX * TY);
+}
+
+// offset of a pixel from the centre of its tile's in-grid pixels (an exact
+// small integer times half the spacing) and kappa |delta|^2.  nvx/nvy/nvz are
+// the tile's in-grid pixel counts along each axis.
+template <int DIM>
+__device__ __forceinline__ void pixel_offset(int lx, int ly, int lz, int nvx, int nvy, int nvz,
+                                             const GridF& g, float kappa, float& ddx, float& ddy,
+                                             float& ddz, float& cm) {
+  ddx = (float)(2 * lx - (nvx - 1)) * g.hdx;
+  ddy = (float)(2 * ly - (nvy - 1)) * g.hdy;
+  ddz = (DIM == 3) ? (float)(2 * lz - (nvz - 1)) * g.hdz : 0.0f;
+  cm = kappa * fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+}
+
+// in-grid pixel counts of tile (tx, ty, tz) along each axis
+template <int DIM>
+__device__ __forceinline__ void tile_valid(int tx, int ty, int tz, const GridF& g, int& nvx,
+                                           int& nvy, int& nvz) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  nvx = min(TX, g.nx - tx * TX);
+  nvy = min(TY, g.ny - ty * TY);
+  nvz = min(TZ, g.nz - tz * TZ);
+}
+
+// Pixels of a ragged edge tile that fall outside the grid are evaluated as a
+// copy of the nearest in-grid pixel of the same tile (their results are never
+// stored), so every evaluated pair has d >= half a pixel and its arrival stays
+// inside the (tile, sensor) window built from the clipped tile.
+template <int DIM>
+__device__ __forceinline__ void clamp_local(int tx, int ty, int tz, const GridF& g, int& lx, int& ly,
+                                            int& lz) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  lx = min(lx, g.nx - 1 - tx * TX);
+  ly = min(ly, g.ny - 1 - ty * TY);
+  lz = min(lz, g.nz - 1 - tz * TZ);
+}
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+constexpr int kMagicBits = 0x4B400000;
+
+// Sample position of one (pixel, sensor) pair relative to the staged window:
+// returns the window index n = floor(u_loc) through `idx`, e = u_loc - n - 0.5
+// in [-0.5, 0.5] and rinv = 1/d.  NEAR pairs (kNear) form d^2 from the offset
+// vector (centre - sensor) + delta instead of d_ref^2 + q/kappa.
+template <int DIM, bool NEAR>
+__device__ __forceinline__ void time_of_flight(const TileRef& r, float ddx, float ddy, float ddz,
+                                               float cm, float inv_kappa, float half_inv_kappa,
+                                               float& rinv, float& e, int& idx) {
+  float q;
+  if (DIM == 3)
+    q = fmaf(r.ex2k, ddx, fmaf(r.ey2k, ddy, fmaf(r.ez2k, ddz, cm)));
+  else
+    q = fmaf(r.ex2k, ddx, fmaf(r.ey2k, ddy, cm));
+  float d2;
+  if (NEAR) {
+    const float ax = fmaf(r.ex2k, half_inv_kappa, ddx);
+    const float ay = fmaf(r.ey2k, half_inv_kappa, ddy);
+    const float az = (DIM == 3) ? fmaf(r.ez2k, half_inv_kappa, ddz) : 0.0f;
+    d2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+  } else {
+    d2 = fmaf(q, inv_kappa, r.dref2);   // |r_i - r_s|^2
+  }
+  rinv = rsqrt_approx(d2);
+  const float d = d2 * rinv;
+  const float rden = rcp_approx(d + r.dref);
+  const float w = fmaf(q, rden, r.fref);         // u_loc - 0.5
+  const float t = __fadd_rn(w, kMagic);
+  const float n = __fsub_rn(t, kMagic);
+  e = __fsub_rn(w, n);
+  idx = __float_as_int(t) - kMagicBits;
+}
+
+// ---------------------------------------------------------------------------
+// setup: per (tile, sensor) reference table, FP64
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_build_table(TileRef* __restrict__ table, int2* __restrict__ krange,
+                              const double* __restrict__ sensors, int S, int nx, int ny, int nz,
+                              double dx, double dy, double dz, double ox, double oy, double oz,
+                              int ntx, int nty, int ntz, double kappa, double t0fs, int K, int L,
+                              double hmin, int* err) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  const int64_t ntiles = (int64_t)ntx * nty * ntz;
+  const int64_t total = ntiles * S;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx / S), s = (int)(idx % S);
+    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
+    const double sx = sensors[(int64_t)s * DIM], sy = sensors[(int64_t)s * DIM + 1];
+    const double sz = (DIM == 3) ? sensors[(int64_t)s * DIM + 2] : 0.0;
+    // centre of the tile's in-grid pixels
+    const int nvx = min(TX, nx - tx * TX), nvy = min(TY, ny - ty * TY), nvz = min(TZ, nz - tz * TZ);
+    const double cx = ox + (tx * TX + 0.5 * (nvx - 1)) * dx;
+    const double cy = oy + (ty * TY + 0.5 * (nvy - 1)) * dy;
+    const double cz = (DIM == 3) ? oz + (tz * TZ + 0.5 * (nvz - 1)) * dz : 0.0;
+    const double ex = cx - sx, ey = cy - sy, ez = (DIM == 3) ? cz - sz : 0.0;
+    const double dref = sqrt(ex * ex + ey * ey + ez * ez);
+    // box of the tile's pixel centres, clipped to the grid
+    const int i0 = tx * TX, i1 = min(nx, i0 + TX) - 1;
+    const int j0 = ty * TY, j1 = min(ny, j0 + TY) - 1;
+    const int l0 = tz * TZ, l1 = min(nz, l0 + TZ) - 1;
+    const double bx0 = ox + i0 * dx, bx1 = ox + i1 * dx;
+    const double by0 = oy + j0 * dy, by1 = oy + j1 * dy;
+    const double bz0 = (DIM == 3) ? oz + l0 * dz : 0.0, bz1 = (DIM == 3) ? oz + l1 * dz : 0.0;
+    const double nxq = fmin(fmax(sx, bx0), bx1) - sx;
+    const double nyq = fmin(fmax(sy, by0), by1) - sy;
+    const double nzq = (DIM == 3) ? fmin(fmax(sz, bz0), bz1) - sz : 0.0;
+    const double fxq = fmax(fabs(bx0 - sx), fabs(bx1 - sx));
+    const double fyq = fmax(fabs(by0 - sy), fabs(by1 - sy));
+    const double fzq = (DIM == 3) ? fmax(fabs(bz0 - sz), fabs(bz1 - sz)) : 0.0;
+    const double dmin = sqrt(nxq * nxq + nyq * nyq + nzq * nzq);
+    const double dmax = sqrt(fxq * fxq + fyq * fyq + fzq * fzq);
+    const double umin = kappa * dmin - t0fs, umax = kappa * dmax - t0fs;
+    const double uref = kappa * dref - t0fs;
+    const double k0min = floor(umin), k0max = floor(umax);
+    TileRef r;
+    r.dref = (float)dref;
+    r.dref2 = (float)(dref * dref);
+    r.ex2k = (float)(2.0 * kappa * ex);
+    r.ey2k = (float)(2.0 * kappa * ey);
+    r.ez2k = (float)(2.0 * kappa * ez);
+    const bool skip = (k0max + 1.0 < 0.0) || (k0min > (double)(K - 1));
+    // every pixel is >= hmin/2 from every sensor (checked at plan creation)
+    r.flags = (dref > 4.0 * fmax(dmin, 0.5 * hmin)) ? kNear : 0;
+    int2 kr;
+    if (skip) {
+      r.klo = kSkip;
+      r.fref = 0.0f;
+      kr = make_int2(kSkip, kSkip);
+    } else {
+      long long kl = (long long)k0min - 2;
+      kl = kl & ~1LL;  // round down to even (16-byte aligned float2 window)
+      if ((long long)k0max - kl + 1 > (long long)L - 2) atomicOr(err, ERR_WINDOW);
+      r.klo = (int)kl;
+      r.fref = (float)(uref - (double)kl - 0.5);
+      kr = make_int2((int)k0min - 1, (int)k0max + 2);
+    }
+    table[idx] = r;
+    krange[(int64_t)s * ntiles + t] = kr;
+  }
+}
+
+cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const double* sensors_dev,
+                               int S, const pa_grid& grid, const GridF& g, double kappa,
+                               double t0fs, int K, int L, double hmin, int* err, cudaStream_t st) {
+  const int64_t total = (int64_t)g.ntx * g.nty * g.ntz * S;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 65535);
+  if (dim == 2)
+    k_build_table<2><<<blocks, threads, 0, st>>>(
+        table, krange, sensors_dev, S, grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz,
+        grid.origin[0], grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, kappa, t0fs, K, L,
+        hmin, err);
+  else
+    k_build_table<3><<<blocks, threads, 0, st>>>(
+        table, krange, sensors_dev, S, grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz,
+        grid.origin[0], grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, kappa, t0fs, K, L,
+        hmin, err);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// trace packing: r[s][k] -> packed[s][pad + k] = (mid, slope) for k in [-1, K),
+// mid = (r_k + r_{k+1})/2, slope = r_{k+1} - r_k, with r_{-1} = r_K = 0.
+// Linear interpolation at r_k + f (f in [0,1]) is then mid + (f - 1/2) slope.
+// ---------------------------------------------------------------------------
+__global__ void k_pack(const float* __restrict__ r, float2* __restrict__ packed, int S, int K,
+                       int Kp, int pad) {
+  const int64_t row = K + 1;
+  const int64_t total = (int64_t)S * row;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(idx / row);
+    const int k = (int)(idx % row) - 1;
+    const float* rs = r + (int64_t)s * K;
+    const float a = (k >= 0) ? rs[k] : 0.0f;
+    const float b = (k + 1 < K) ? rs[k + 1] : 0.0f;
+    packed[(int64_t)s * Kp + pad + k] = make_float2(0.5f * (a + b), b - a);
+  }
+}
+
+cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
+                        cudaStream_t st) {
+  const int64_t total = (int64_t)S * (K + 1);
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 152 * 16);
+  k_pack<<<blocks, threads, 0, st>>>(r, packed, S, K, Kp, pad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A^T: pixel-tile gather.
+//
+// One cluster of C CTAs per 1024-pixel tile; CTA rank r loops over its share of
+// the sensors.  A producer warp stages, per pipeline stage, the reference
+// entries of kAdjSB sensors and each sensor's window of L packed trace samples
+// (one cp.async.bulk per sensor, completion tracked by an mbarrier); eight
+// compute warps evaluate four pixels per thread per sensor from shared memory.
+// The C partial images are summed through distributed shared memory in rank
+// order, then the epilogue (store / Landweber update / norm) runs once.
+// ---------------------------------------------------------------------------
+int adjoint_smem_bytes(int L) {
+  return kAdjStages * kAdjSB * L * (int)sizeof(float2) +
+         kAdjStages * kAdjSB * (int)sizeof(TileRef) + kTilePixels * (int)sizeof(float) +
+         2 * kAdjStages * (int)sizeof(uint64_t);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int L = P.L;
+  float2* s_trace = reinterpret_cast<float2*>(smem);
+  TileRef* s_ref = reinterpret_cast<TileRef*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
+  float* s_acc = reinterpret_cast<float*>(s_ref + kAdjStages * kAdjSB);
+  uint64_t* s_full = reinterpret_cast<uint64_t*>(s_acc + kTilePixels);
+  uint64_t* s_empty = s_full + kAdjStages;
+  __shared__ int s_abort;
+  __shared__ int s_issued;
+  __shared__ double s_red[kAdjWarps + 1];
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const int tile = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s_begin = rank * P.sensors_per_rank;
+  const int s_end = min(P.S, s_begin + P.sensors_per_rank);
+  const int n_stages = s_end > s_begin ? (s_end - s_begin + kAdjSB - 1) / kAdjSB : 0;
+
+  if (tid == 0) {
+    for (int i = 0; i < kAdjStages; ++i) {
+      mbar_init(&s_full[i], 1);
+      mbar_init(&s_empty[i], kAdjWarps);
+    }
+    s_abort = 0;
+    s_issued = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kAdjWarps) {
+    // ----------------------------- producer warp -----------------------------
+    int j = 0;
+    for (; j < n_stages; ++j) {
+      const int slot = j % kAdjStages;
+      if (j >= kAdjStages) {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&s_empty[slot], ((j / kAdjStages) - 1) & 1);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(P.err, ERR_WAIT_TIMEOUT);
+            s_abort = 1;
+          }
+          break;
+        }
+      }
+      const int s = s_begin + j * kAdjSB + lane;
+      uint32_t bytes = 0;
+      const float2* src = nullptr;
+      if (lane < kAdjSB) {
+        TileRef r;
+        if (s < s_end) {
+          r = P.table[(int64_t)tile * P.S + s];
+          if (r.klo != kSkip) {
+            bytes = (uint32_t)L * (uint32_t)sizeof(float2);
+            src = P.packed + (int64_t)s * P.Kp + P.pad + r.klo;
+          }
+        } else {
+          r.klo = kSkip;
+        }
+        s_ref[slot * kAdjSB + lane] = r;
+      }
+      const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(&s_full[slot], total);
+      __syncwarp();
+      if (bytes) bulk_g2s(s_trace + (slot * kAdjSB + lane) * L, src, bytes, &s_full[slot]);
+    }
+    if (lane == 0) s_issued = j;
+  } else {
+    // ----------------------------- compute warps -----------------------------
+    float ddx[kAdjPPT], ddy[kAdjPPT], ddz[kAdjPPT], cm[kAdjPPT], acc[kAdjPPT];
+    const int ttx = tile % P.g.ntx, tty = (tile / P.g.ntx) % P.g.nty;
+    const int ttz = tile / (P.g.ntx * P.g.nty);
+    int nvx, nvy, nvz;
+    tile_valid<DIM>(ttx, tty, ttz, P.g, nvx, nvy, nvz);
+#pragma unroll
+    for (int m = 0; m < kAdjPPT; ++m) {
+      int lx, ly, lz;
+      pixel_local<DIM>(tid + m * 32 * kAdjWarps, lx, ly, lz);
+      clamp_local<DIM>(ttx, tty, ttz, P.g, lx, ly, lz);
+      pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ddx[m], ddy[m], ddz[m], cm[m]);
+      acc[m] = 0.0f;
+    }
+    const float inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
+    for (int j = 0; j < n_stages; ++j) {
+      const int slot = j % kAdjStages;
+      const bool ok = mbar_wait_bounded(&s_full[slot], (j / kAdjStages) & 1);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          atomicOr(P.err, ERR_WAIT_TIMEOUT);
+          s_abort = 1;
+        }
+        break;
+      }
+      if (*(volatile int*)&s_abort) break;
+      const TileRef* refs = s_ref + slot * kAdjSB;
+      const float2* trs = s_trace + slot * kAdjSB * L;
+#pragma unroll 1
+      for (int sb = 0; sb < kAdjSB; ++sb) {
+        const TileRef r = refs[sb];
+        if (r.klo == kSkip) continue;
+        const float2* win = trs + sb * L;
+        if (r.flags & kNear) {
+#pragma unroll
+          for (int m = 0; m < kAdjPPT; ++m) {
+            float rinv, e;
+            int idx;
+            time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
+                                      idx);
+            const float2 v = win[idx];
+            acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < kAdjPPT; ++m) {
+            float rinv, e;
+            int idx;
+            time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
+                                       idx);
+            const float2 v = win[idx];
+            acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_empty[slot]);
+    }
+#pragma unroll
+    for (int m = 0; m < kAdjPPT; ++m) s_acc[tid + m * 32 * kAdjWarps] = acc[m];
+  }
+  __syncthreads();
+  if (tid == 0 && s_abort) {
+    // drain copies that may still be in flight before the CTA's shared memory
+    // is released (bounded)
+    const int issued = s_issued;
+    for (int jj = max(0, issued - kAdjStages); jj < issued; ++jj)
+      mbar_wait_bounded(&s_full[jj % kAdjStages], (jj / kAdjStages) & 1);
+  }
+
+  cluster.sync();
+  // --------------- cluster reduction in rank order + epilogue ---------------
+  const int per = (kTilePixels + C - 1) / C;
+  const int p0 = rank * per, p1 = min(kTilePixels, p0 + per);
+  const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
+  double part = 0.0;
+  for (int p = p0 + tid; p < p1; p += kAdjThreads) {
+    float v = 0.0f;
+    for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(s_acc, q)[p];
+    int lx, ly, lz;
+    pixel_local<DIM>(p, lx, ly, lz);
+    const int gx = tx * TX + lx, gy = ty * TY + ly, gz = tz * TZ + lz;
+    if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
+      const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
+      const float gval = P.amp * v;
+      if (P.mode == ADJ_LANDWEBER) {
+        float xv = fmaf((float)(*P.omega), gval, P.out[i]);
+        if (P.nonneg) xv = fmaxf(xv, 0.0f);
+        P.out[i] = xv;
+      } else {
+        P.out[i] = gval;
+        part += (double)gval * (double)gval;
+      }
+    }
+  }
+  if (P.mode == ADJ_NORM) {
+    const double t = block_sum<kAdjWarps + 1>(part, s_red);
+    if (tid == 0) P.partials[(int64_t)tile * C + rank] = t;
+  }
+  cluster.sync();
+  (void)TZ;
+}
+
+cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st) {
+  const int smem = adjoint_smem_bytes(p.L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, ntiles, 1);
+  cfg.blockDim = dim3(kAdjThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (dim == 2)
+    e = cudaLaunchKernelEx(&cfg, k_adjoint<2>, p);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_adjoint<3>, p);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A: (sensor, window of W samples) gather.
+//
+// A CTA owns the W output samples [kb, kb + W) of one sensor.  It lists, in
+// tile order, the pixel tiles whose arrival span meets the window, then, a
+// batch of tiles at a time, keeps the 32-pixel chunks (a tile row in 2D, two
+// rows in 3D) whose conservative arrival range meets the window.  Warps take
+// the surviving chunks round robin; every pixel adds (x (1-f)/d, x f/d) to the
+// sample pair (k0, k0 + 1).  Along a row on one side of the sensor the arrival
+// grows monotonically with distance from the sensor, so equal k0 sit in
+// adjacent lanes: a segmented shuffle scan sums them (fixed tree order) and
+// the last lane of each segment adds the sum to the warp's private histogram,
+// one run (row, side) per round.  If FP32 rounding ever broke the monotone
+// order, the chunk falls back to adding its segments one lane at a time.  The
+// warp histograms are summed in warp order: no atomics, bitwise reproducible.
+// ---------------------------------------------------------------------------
+constexpr int kFwdBatchTiles = kFwdThreads / 32;  // 32 candidate chunks per tile
+
+int forward_smem_bytes(int ntiles) {
+  return kFwdWarps * (kFwdBins + 1) * (int)sizeof(float2) +   // warp histograms
+         ((ntiles + 3) / 4 * 4) * (int)sizeof(int) +          // hit tiles
+         kFwdThreads * (int)sizeof(int) +                     // surviving chunks
+         kFwdBatchTiles * (int)sizeof(TileRef) +              // references of a batch
+         kFwdBatchTiles * (int)sizeof(int4);                  // tile coordinates
+}
+
+// Block-wide ordered compaction: returns the number of `keep` threads with a
+// lower thread index (their output slot) and writes the total to *total.
+__device__ __forceinline__ int block_compact(bool keep, int* s_wcount, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) s_wcount[warp] = __popc(bal);
+  __syncthreads();
+  int off = 0, tot = 0;
+  for (int w = 0; w < kFwdWarps; ++w) {
+    if (w < warp) off += s_wcount[w];
+    tot += s_wcount[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return off + __popc(bal & ((1u << lane) - 1u));
+}
+
+// Conservative arrival range of chunk c of a tile (FP32; error ~1e-4 samples,
+// callers add a margin of one sample).
+template <int DIM>
+__device__ __forceinline__ void chunk_range(const TileRef& r, int c, int nvx, int nvy, int nvz,
+                                            const GridF& g, float kappa, float hik, float& umin,
+                                            float& umax) {
+  constexpr int TY = Tile<DIM>::Y;
+  const float ex = r.ex2k * hik, ey = r.ey2k * hik, ez = r.ez2k * hik;
+  const float ax0 = ex - (float)(nvx - 1) * g.hdx;
+  const float ax1 = ex + (float)(nvx - 1) * g.hdx;
+  const float mx = (ax0 > 0.f) ? ax0 : ((ax1 < 0.f) ? -ax1 : 0.f);
+  const float Mx = fmaxf(fabsf(ax0), fabsf(ax1));
+  float yz_min, yz_max;
+  if (DIM == 2) {
+    const float ay = ey + (float)(2 * c - (nvy - 1)) * g.hdy;
+    yz_min = yz_max = ay * ay;
+  } else {
+    const int ly0 = 2 * (c % (TY / 2)), lz = c / (TY / 2);
+    const int ly1 = min(ly0 + 1, nvy - 1);
+    const float ay0 = ey + (float)(2 * ly0 - (nvy - 1)) * g.hdy;
+    const float ay1 = ey + (float)(2 * ly1 - (nvy - 1)) * g.hdy;
+    const float az = ez + (float)(2 * lz - (nvz - 1)) * g.hdz;
+    yz_min = fminf(ay0 * ay0, ay1 * ay1) + az * az;
+    yz_max = fmaxf(ay0 * ay0, ay1 * ay1) + az * az;
+  }
+  const float dmin = sqrtf(mx * mx + yz_min), dmax = sqrtf(Mx * Mx + yz_max);
+  const float base = (float)r.klo + r.fref + 0.5f;
+  umin = base + kappa * (dmin - r.dref);
+  umax = base + kappa * (dmax - r.dref);
+}
+
+// lane -> tile-local pixel of chunk c (a row in 2D; two half-warp rows in 3D)
+template <int DIM>
+__device__ __forceinline__ void chunk_pixel(int c, int lane, int& lx, int& ly, int& lz) {
+  if (DIM == 2) {
+    lx = lane;
+    ly = c;
+    lz = 0;
+  } else {
+    lx = lane & 15;
+    ly = 2 * (c & 3) + (lane >> 4);
+    lz = c >> 2;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdParams P) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  static_assert(TX * TY * TZ == 32 * 32, "32 chunks of 32 pixels per tile");
+  static_assert(DIM == 2 ? TX == 32 : (TX == 16 && TY == 8 && TZ == 8), "chunk layout");
+  constexpr int W = kFwdBins;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* hist = reinterpret_cast<float2*>(smem);
+  int* tiles = reinterpret_cast<int*>(hist + kFwdWarps * (W + 1));
+  int* chunks = tiles + (P.ntiles + 3) / 4 * 4;
+  TileRef* refs = reinterpret_cast<TileRef*>(chunks + kFwdThreads);
+  int4* tcoord = reinterpret_cast<int4*>(refs + kFwdBatchTiles);
+  __shared__ int s_wcount[kFwdWarps];
+  __shared__ double s_red[kFwdWarps];
+
+  const int item = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
+  const int s = item / P.nwin, win = item - s * P.nwin, kb = win * W;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float kappa = P.kappa, inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
+
+  for (int i = tid; i < kFwdWarps * (W + 1); i += kFwdThreads) hist[i] = make_float2(0.f, 0.f);
+
+  // ordered list of tiles whose taps can land in [kb, kb + W)
+  int n_hit = 0;
+  for (int t0 = 0; t0 < P.ntiles; t0 += kFwdThreads) {
+    const int t = t0 + tid;
+    bool hit = false;
+    if (t < P.ntiles) {
+      const int2 kr = P.krange[(int64_t)s * P.ntiles + t];
+      hit = kr.x != kSkip && kr.x <= kb + W - 1 && kr.y >= kb;
+    }
+    int tot;
+    const int slot = block_compact(hit, s_wcount, &tot);
+    if (hit) tiles[n_hit + slot] = t;
+    n_hit += tot;
+  }
+  __syncthreads();  // the tile list is complete before any thread reads it
+
+  float2* myhist = hist + warp * (W + 1);
+  for (int tb = 0; tb < n_hit; tb += kFwdBatchTiles) {
+    // ---- cull the batch's chunks by their conservative arrival range ----
+    const int hs = tid >> 5, c = lane;
+    bool keep = false;
+    if (tb + hs < n_hit) {
+      const int t = tiles[tb + hs];
+      const TileRef r = P.table[(int64_t)t * P.S + s];
+      const int tx = t % P.g.ntx, ty = (t / P.g.ntx) % P.g.nty, tz = t / (P.g.ntx * P.g.nty);
+      int nvx, nvy, nvz;
+      tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
+      if (c == 0) {
+        refs[hs] = r;
+        tcoord[hs] = make_int4(tx * TX, ty * TY, tz * TZ, nvx | (nvy << 8) | (nvz << 16));
+      }
+      int ly, lz;
+      if (DIM == 2) {
+        ly = c;
+        lz = 0;
+      } else {
+        ly = 2 * (c & 3);
+        lz = c >> 2;
+      }
+      if (ly < nvy && lz < nvz) {
+        float umin, umax;
+        chunk_range<DIM>(r, c, nvx, nvy, nvz, P.g, kappa, hik, umin, umax);
+        keep = (umin - 1.0f <= (float)(kb + W - 1)) && (umax + 2.0f >= (float)kb);
+      }
+    }
+    int nch;
+    const int slot = block_compact(keep, s_wcount, &nch);
+    if (keep) chunks[slot] = (hs << 5) | c;
+    __syncthreads();
+
+    // ---- evaluate the surviving chunks ----
+    for (int qi = warp; qi < nch; qi += kFwdWarps) {
+      const int code = chunks[qi];
+      const int hb = code >> 5, cc = code & 31;
+      const TileRef r = refs[hb];
+      const int4 tc = tcoord[hb];
+      int lx, ly, lz;
+      chunk_pixel<DIM>(cc, lane, lx, ly, lz);
+      const int gx = tc.x + lx, gy = tc.y + ly, gz = tc.z + lz;
+      float xv = 0.0f;
+      if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz)
+        xv = P.x[((int64_t)gz * P.g.ny + gy) * P.g.nx + gx];
+      if (!__any_sync(0xffffffffu, xv != 0.0f)) continue;
+      const int nvx = tc.w & 0xff, nvy = (tc.w >> 8) & 0xff, nvz = tc.w >> 16;
+      lx = min(lx, nvx - 1);
+      ly = min(ly, nvy - 1);
+      lz = min(lz, nvz - 1);
+      float ddx, ddy, ddz, cm, rinv, e;
+      int idx;
+      pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, kappa, ddx, ddy, ddz, cm);
+      if (r.flags & kNear)
+        time_of_flight<DIM, true>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv, e, idx);
+      else
+        time_of_flight<DIM, false>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv, e, idx);
+      const int j = r.klo + idx - (kb - 1);  // slot of the tap pair (k0, k0 + 1)
+      const bool inwin = (unsigned)j <= (unsigned)W;
+      const int side = (ddx >= -(r.ex2k * hik)) ? 1 : 0;  // pixel right of the sensor
+      const int run = (DIM == 3 ? ((lane >> 4) << 1) : 0) | side;
+      const float wgt = xv * rinv;
+      const float hw = 0.5f * wgt;
+      float a = inwin ? fmaf(-wgt, e, hw) : 0.0f;  // x (1 - f) / d  -> sample k0
+      float b = inwin ? fmaf(wgt, e, hw) : 0.0f;   // x f / d        -> sample k0 + 1
+      // slot clamped to [-1, W + 1] keeps the order of out-of-window lanes
+      const int jc = min(max(j, -1), W + 1);
+      const int key = (run << 16) | (jc + 1);
+      const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool same_run = lane > 0 && (pkey >> 16) == run;
+      const int pjc = (pkey & 0xffff) - 1;
+      const bool viol = same_run && (side ? (pjc > jc) : (pjc < jc));
+      const bool head = inwin && !(same_run && pjc == jc);
+      const unsigned heads = __ballot_sync(0xffffffffu, head);
+      const unsigned inw = __ballot_sync(0xffffffffu, inwin);
+      if (inw == 0u) continue;
+      const bool bad = __any_sync(0xffffffffu, viol);
+      const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+      const int seg = inwin ? 31 - __clz(heads & le) : lane;
+      const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - seg + 1));
+      for (unsigned off = 1; off < maxlen; off <<= 1) {
+        const float a2 = __shfl_up_sync(0xffffffffu, a, off);
+        const float b2 = __shfl_up_sync(0xffffffffu, b, off);
+        if (inwin && lane - (int)off >= seg) {
+          a += a2;
+          b += b2;
+        }
+      }
+      const unsigned above = (lane == 31) ? 0u : (heads | ~inw) >> (lane + 1);
+      const bool tail = inwin && (lane == 31 || (above & 1u));
+      if (!bad) {
+        unsigned rmask = __reduce_or_sync(0xffffffffu, tail ? (1u << run) : 0u);
+        while (rmask) {
+          const int rr = __ffs(rmask) - 1;
+          rmask &= rmask - 1u;
+          if (tail && run == rr) {
+            float2 h = myhist[j];
+            h.x += a;
+            h.y += b;
+            myhist[j] = h;
+          }
+          __syncwarp();
+        }
+      } else {
+        for (unsigned m = __ballot_sync(0xffffffffu, tail); m; m &= m - 1u) {
+          if (lane == __ffs(m) - 1) {
+            float2 h = myhist[j];
+            h.x += a;
+            h.y += b;
+            myhist[j] = h;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  double part = 0.0;
+  for (int m = tid; m < W; m += kFwdThreads) {
+    const int k = kb + m;
+    if (k >= P.K) continue;
+    float v = 0.0f;
+    for (int w = 0; w < kFwdWarps; ++w) {
+      const float2* h = hist + w * (W + 1);
+      v += h[m + 1].x + h[m].y;
+    }
+    v *= P.amp;
+    const int64_t o = (int64_t)s * P.K + k;
+    if (P.mode == FWD_RESID) {
+      const float y = P.y_f16 ? __half2float(reinterpret_cast<const __half*>(P.y)[o])
+                              : reinterpret_cast<const float*>(P.y)[o];
+      const float rr = y - v;
+      P.out[o] = rr;
+      part += (double)rr * (double)rr;
+    } else {
+      P.out[o] = v;
+      part += (double)v * (double)v;
+    }
+  }
+  if (P.mode != FWD_STORE) {
+    const double t = block_sum<kFwdWarps>(part, s_red);
+    if (tid == 0) P.partials[item] = t;
+  }
+}
+
+cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
+  const int smem = forward_smem_bytes(p.ntiles);
+  const int grid = p.S * p.nwin;
+  if (dim == 2)
+    k_forward<2><<<grid, kFwdThreads, smem, st>>>(p);
+  else
+    k_forward<3><<<grid, kFwdThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limit of the gather kernels (called when a
+// plan is created, outside any stream capture).
+cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_adjoint<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_adj)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_adjoint<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_adj)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_forward<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_fwd)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_forward<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions of per-CTA partials (one CTA, fixed order) and the scalar
+// steps of the iterations.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 1024;
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const double* __restrict__ partials, int n,
+                                                        double* out_sum, int op,
+                                                        const double* other, double* out2) {
+  __shared__ double s_red[kRedThreads / 32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += kRedThreads) v += partials[i];
+  const double t = block_sum<kRedThreads / 32>(v, s_red);
+  if (threadIdx.x == 0) {
+    if (out_sum) *out_sum = t;
+    switch (op) {
+      case OP_ALPHA: {  // alpha = gamma / ||q||^2
+        *out2 = t > 0.0 ? *other / t : 0.0;
+        break;
+      }
+      case OP_BETA: {  // beta = gamma_new / gamma_old
+        *out2 = *other > 0.0 ? t / *other : 0.0;
+        break;
+      }
+      case OP_INVSQRT: {  // 1/||w||
+        *out2 = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        break;
+      }
+      default:
+        break;
+    }
+  }
+}
+
+cudaError_t launch_reduce(const double* partials, int n, double* out_sum, int op,
+                          const double* other, double* out2, cudaStream_t st) {
+  k_reduce<<<1, kRedThreads, 0, st>>>(partials, n, out_sum, op, other, out2);
+  return cudaGetLastError();
+}
+
+constexpr int kVecThreads = 256;
+
+// CGLS: x += alpha p (first nblk_x blocks); r_out = r_in - alpha q, packed
+// residual and FP64 partials of ||r_out||^2 (remaining blocks, one partial each).
+__global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
+    float* __restrict__ x, const float* __restrict__ pv, const float* __restrict__ r_in,
+    float* __restrict__ r_out, const float* __restrict__ q, float2* __restrict__ packed,
+    const double* __restrict__ alpha_p, int N, int S, int K, int Kp, int pad,
+    double* __restrict__ partials, int nblk_x) {
+  __shared__ double s_red[kVecThreads / 32];
+  const float alpha = (float)(*alpha_p);
+  if ((int)blockIdx.x < nblk_x) {
+    for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < N;
+         i += (int64_t)nblk_x * kVecThreads)
+      x[i] = fmaf(alpha, pv[i], x[i]);
+    return;
+  }
+  const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
+  const int64_t total = (int64_t)S * K;
+  double part = 0.0;
+  for (int64_t o = b * (int64_t)kVecThreads + threadIdx.x; o < total;
+       o += (int64_t)nb * kVecThreads) {
+    const int s = (int)(o / K), k = (int)(o % K);
+    const float rk = fmaf(-alpha, q[o], r_in[o]);
+    const float rn = (k + 1 < K) ? fmaf(-alpha, q[o + 1], r_in[o + 1]) : 0.0f;
+    r_out[o] = rk;
+    float2* row = packed + (int64_t)s * Kp + pad;
+    row[k] = make_float2(0.5f * (rk + rn), rn - rk);
+    if (k == 0) row[-1] = make_float2(0.5f * rk, rk);
+    part += (double)rk * (double)rk;
+  }
+  const double t = block_sum<kVecThreads / 32>(part, s_red);
+  if (threadIdx.x == 0) partials[b] = t;
+}
+
+cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
+                           const float* q, float2* packed, const double* alpha, int N, int S,
+                           int K, int Kp, int pad, double* partials, int nblk_x, int nblk_r,
+                           cudaStream_t st) {
+  k_cgls_xr<<<nblk_x + nblk_r, kVecThreads, 0, st>>>(x, pvec, r_in, r_out, q, packed, alpha, N, S,
+                                                     K, Kp, pad, partials, nblk_x);
+  return cudaGetLastError();
+}
+
+__global__ void k_axpby(float* __restrict__ p, const float* __restrict__ s,
+                        const double* __restrict__ beta_p, int N) {
+  const float beta = (float)(*beta_p);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], s[i]);
+}
+
+__global__ void k_scale(float* __restrict__ v, const float* __restrict__ w,
+                        const double* __restrict__ f_p, int N) {
+  const float f = (float)(*f_p);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * f;
+}
+
+__global__ void k_clamp(float* __restrict__ x, int N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fmaxf(x[i], 0.0f);
+}
+
+__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+
+__global__ void k_fill(float* __restrict__ dst, float v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = v;
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_norm_partials(const float* __restrict__ v,
+                                                               int64_t n, double* partials) {
+  __shared__ double s_red[kVecThreads / 32];
+  double part = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kVecThreads)
+    part += (double)v[i] * (double)v[i];
+  const double t = block_sum<kVecThreads / 32>(part, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+static int vec_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecThreads - 1) / kVecThreads, 152 * 8));
+}
+
+cudaError_t launch_axpby(float* p, const float* s, const double* beta, int N, cudaStream_t st) {
+  k_axpby<<<vec_blocks(N), kVecThreads, 0, st>>>(p, s, beta, N);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
+                         cudaStream_t st) {
+  k_scale<<<vec_blocks(N), kVecThreads, 0, st>>>(v, w, factor, N);
+  return cudaGetLastError();
+}
+cudaError_t launch_clamp(float* x, int N, cudaStream_t st) {
+  k_clamp<<<vec_blocks(N), kVecThreads, 0, st>>>(x, N);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st) {
+  k_set_scalar<<<1, 1, 0, st>>>(dst, value);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
+  k_fill<<<vec_blocks(n), kVecThreads, 0, st>>>(dst, value, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_norm_partials(const float* v, int64_t n, double* partials, int nblk,
+                                 cudaStream_t st) {
+  k_norm_partials<<<nblk, kVecThreads, 0, st>>>(v, n, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace pa

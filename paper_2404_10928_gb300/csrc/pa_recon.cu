@@ -1,0 +1,367 @@
+// Iteration drivers: power iteration, projected Landweber and CGLS, each an
+// all-device sequence of kernels (scalars stay in device memory, no host
+// synchronisation inside the loop) that is captured once as a CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <utility>
+
+#include "pa_internal.cuh"
+
+namespace pa {
+
+FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode, const void* y);
+AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* omega, int nonneg);
+int forward_partials(const pa_plan* p);
+int adjoint_partials(const pa_plan* p);
+
+namespace {
+
+// Scalar records in device memory (FP64).
+struct Scalars {
+  double* omega;    // Landweber step given by the caller
+  double* inv_lam;  // 1/||A^T A v|| of the latest power step (= step when omega <= 0)
+  double* lam2;     // ||A^T A v||^2 of the latest power step
+  double* hist;     // [n+1] ||r_n||^2
+  double* gamma;    // [n+1] ||A^T r_n||^2 (CGLS)
+  double* delta;    // [n+1] ||A p_n||^2
+  double* alpha;    // [n+1]
+  double* beta;     // [n+1]
+};
+
+int scalar_count(int n) { return 3 + 5 * (n + 1); }
+
+Scalars scalars(pa_plan* p, int n) {
+  Scalars s;
+  double* b = p->d_scal;
+  s.omega = b;
+  s.inv_lam = b + 1;
+  s.lam2 = b + 2;
+  s.hist = b + 3;
+  s.gamma = s.hist + (n + 1);
+  s.delta = s.gamma + (n + 1);
+  s.alpha = s.delta + (n + 1);
+  s.beta = s.alpha + (n + 1);
+  return s;
+}
+
+void drop_graphs(pa_plan* p) {
+  for (auto& kv : p->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto ev : kv.second.fwd_ev) cudaEventDestroy(ev);
+    for (auto ev : kv.second.adj_ev) cudaEventDestroy(ev);
+  }
+  p->graphs.clear();
+  p->last_timed = nullptr;
+}
+
+template <typename T>
+pa_status alloc_once(pa_plan* p, T** ptr, size_t count) {
+  if (*ptr) return PA_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PA_ERR_OOM : PA_ERR_CUDA;
+  }
+  p->bytes += (int64_t)(count * sizeof(T));
+  return PA_OK;
+}
+
+pa_status ensure_workspace(pa_plan* p, int n_iter) {
+  const size_t N = (size_t)p->grid.nx * p->grid.ny * p->grid.nz;
+  const size_t SK = (size_t)p->S * p->K;
+  PA_TRY(alloc_once(p, &p->d_ra, SK));
+  PA_TRY(alloc_once(p, &p->d_rb, SK));
+  PA_TRY(alloc_once(p, &p->d_q, SK));
+  PA_TRY(alloc_once(p, &p->d_pv, N));
+  PA_TRY(alloc_once(p, &p->d_sv, N));
+  const int need = scalar_count(n_iter);
+  if (p->scal_cap < need) {
+    drop_graphs(p);  // graphs hold pointers into the old records
+    if (p->d_scal) {
+      PA_CUDA(cudaDeviceSynchronize());
+      cudaFree(p->d_scal);
+      p->bytes -= (int64_t)p->scal_cap * (int64_t)sizeof(double);
+      p->d_scal = nullptr;
+    }
+    const int cap = std::max(need, scalar_count(64));
+    PA_TRY(alloc_once(p, &p->d_scal, (size_t)cap));
+    p->scal_cap = cap;
+  }
+  return PA_OK;
+}
+
+// Event pairs around the gather launches (only when timing is requested).
+struct Timing {
+  pa_plan::GraphEntry* entry = nullptr;
+  bool on = false;
+};
+
+pa_status mark(Timing& t, bool fwd, cudaStream_t st) {
+  if (!t.on) return PA_OK;
+  cudaEvent_t ev;
+  PA_CUDA(cudaEventCreate(&ev));
+  (fwd ? t.entry->fwd_ev : t.entry->adj_ev).push_back(ev);
+  PA_CUDA(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  return PA_OK;
+}
+
+pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, Timing& t,
+              cudaStream_t st) {
+  PA_TRY(mark(t, true, st));
+  FwdParams f = forward_params(p, x, out, mode, y);
+  PA_CUDA(launch_forward(p->dim, f, st));
+  PA_TRY(mark(t, true, st));
+  return PA_OK;
+}
+
+pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg, Timing& t,
+              cudaStream_t st) {
+  PA_TRY(mark(t, false, st));
+  AdjParams a = adjoint_params(p, out, mode, omega, nonneg);
+  PA_CUDA(launch_adjoint(p->dim, a, p->cluster, p->ntiles, st));
+  PA_TRY(mark(t, false, st));
+  return PA_OK;
+}
+
+int vec_blocks_x(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 4)); }
+int vec_blocks_r(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+// v <- A^T A v / ||A^T A v||, n_pow times, from v0 (NULL = ones).  Afterwards
+// *inv_lam = 1/||A^T A v|| and *lam2 = ||A^T A v||^2 for the last unit v.
+pa_status enqueue_power(pa_plan* p, int n_pow, const float* v0, const Scalars& sc, Timing& t,
+                        cudaStream_t st) {
+  const int64_t N = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
+  if (v0)
+    PA_CUDA(cudaMemcpyAsync(p->d_pv, v0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  else
+    PA_CUDA(launch_fill(p->d_pv, 1.0f, N, st));
+  const int nb = vec_blocks_r(N);
+  PA_CUDA(launch_norm_partials(p->d_pv, N, p->d_partials, nb, st));
+  PA_CUDA(launch_reduce(p->d_partials, nb, nullptr, OP_INVSQRT, nullptr, sc.inv_lam, st));
+  PA_CUDA(launch_scale(p->d_pv, p->d_pv, sc.inv_lam, (int)N, st));
+  for (int it = 0; it < n_pow; ++it) {
+    PA_TRY(fwd(p, p->d_pv, p->d_q, FWD_STORE, nullptr, t, st));
+    PA_CUDA(launch_pack(p->d_q, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, t, st));
+    PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.lam2, OP_INVSQRT, nullptr,
+                          sc.inv_lam, st));
+    PA_CUDA(launch_scale(p->d_pv, p->d_sv, sc.inv_lam, (int)N, st));
+  }
+  return PA_OK;
+}
+
+pa_status enqueue_landweber(pa_plan* p, int n_iter, const void* y, float* x,
+                            const pa_recon_opts& o, const Scalars& sc, Timing& t,
+                            cudaStream_t st) {
+  const double* omega = sc.omega;
+  if (o.omega > 0.0) {
+    PA_CUDA(launch_set_scalar(sc.omega, o.omega, st));
+  } else {
+    PA_TRY(enqueue_power(p, o.power_iters > 0 ? o.power_iters : 50, o.power_v0_dev, sc, t, st));
+    omega = sc.inv_lam;
+  }
+  for (int it = 0; it <= n_iter; ++it) {
+    PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y, t, st));  // r = y - A x, partial ||r||^2
+    PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.hist + it, OP_SUM, nullptr,
+                          nullptr, st));
+    if (it == n_iter) break;
+    PA_CUDA(launch_pack(p->d_ra, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+    PA_TRY(adj(p, x, ADJ_LANDWEBER, omega, o.nonneg, t, st));  // x = max(0, x + w A^T r)
+  }
+  return PA_OK;
+}
+
+pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa_recon_opts& o,
+                       const Scalars& sc, Timing& t, cudaStream_t st) {
+  const int N = p->grid.nx * p->grid.ny * p->grid.nz;
+  const int64_t SK = (int64_t)p->S * p->K;
+  const int nbx = vec_blocks_x(N), nbr = vec_blocks_r(SK);
+  float* r_in = p->d_ra;
+  float* r_out = p->d_rb;
+  // r = y - A x0; s = A^T r; p = s; gamma = ||s||^2
+  PA_TRY(fwd(p, x, r_in, FWD_RESID, y, t, st));
+  PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.hist, OP_SUM, nullptr, nullptr, st));
+  PA_CUDA(launch_pack(r_in, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+  PA_TRY(adj(p, p->d_pv, ADJ_NORM, nullptr, 0, t, st));
+  PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.gamma, OP_SUM, nullptr, nullptr, st));
+  for (int it = 0; it < n_iter; ++it) {
+    // q = A p; alpha = gamma / ||q||^2
+    PA_TRY(fwd(p, p->d_pv, p->d_q, FWD_NORM, nullptr, t, st));
+    PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.delta + it, OP_ALPHA,
+                          sc.gamma + it, sc.alpha + it, st));
+    // x += alpha p; r -= alpha q (packed for the adjoint); ||r||^2
+    PA_CUDA(launch_cgls_xr(x, p->d_pv, r_in, r_out, p->d_q, p->d_packed, sc.alpha + it, N, p->S,
+                           p->K, p->Kp, p->pad, p->d_partials, nbx, nbr, st));
+    PA_CUDA(launch_reduce(p->d_partials, nbr, sc.hist + it + 1, OP_SUM, nullptr, nullptr, st));
+    // s = A^T r; beta = ||s||^2 / gamma; p = s + beta p
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, t, st));
+    PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.gamma + it + 1, OP_BETA,
+                          sc.gamma + it, sc.beta + it, st));
+    PA_CUDA(launch_axpby(p->d_pv, p->d_sv, sc.beta + it, N, st));
+    std::swap(r_in, r_out);
+  }
+  if (o.nonneg) PA_CUDA(launch_clamp(x, N, st));
+  return PA_OK;
+}
+
+pa_status enqueue_recon(pa_plan* p, pa_method method, int n_iter, const void* y, float* x,
+                        const pa_recon_opts& o, Timing& t, cudaStream_t st) {
+  const Scalars sc = scalars(p, n_iter);
+  if (method == PA_LANDWEBER) return enqueue_landweber(p, n_iter, y, x, o, sc, t, st);
+  return enqueue_cgls(p, n_iter, y, x, o, sc, t, st);
+}
+
+}  // namespace
+}  // namespace pa
+
+using namespace pa;
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+extern "C" {
+
+pa_status pa_power_iteration(pa_plan* plan, int n_iter, const float* v0_dev, double* sigma2,
+                             pa_stream stream) {
+  if (!plan || !sigma2 || n_iter < 1) {
+    set_error("pa_power_iteration: NULL argument or n_iter < 1");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  PA_TRY(ensure_workspace(plan, 0));
+  const Scalars sc = scalars(plan, 0);
+  Timing t;
+  cudaStream_t st = (cudaStream_t)stream;
+  PA_TRY(enqueue_power(plan, n_iter, v0_dev, sc, t, st));
+  double lam2 = 0.0;
+  PA_CUDA(cudaMemcpyAsync(&lam2, sc.lam2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PA_CUDA(cudaStreamSynchronize(st));
+  *sigma2 = std::sqrt(lam2);
+  return PA_OK;
+}
+
+pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void* y_dev,
+                         float* x_dev, const pa_recon_opts* opts, pa_stream stream) {
+  if (!plan || !y_dev || !x_dev || n_iter < 0 ||
+      (method != PA_LANDWEBER && method != PA_CGLS)) {
+    set_error("pa_reconstruct: invalid argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  pa_recon_opts o;
+  pa_recon_opts_default(&o);
+  if (opts) o = *opts;
+  if (!std::isfinite(o.omega) || o.power_iters < 0) {
+    set_error("pa_reconstruct: invalid options");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  PA_TRY(ensure_workspace(plan, n_iter));
+  cudaStream_t st = (cudaStream_t)stream;
+  Timing t;
+  t.on = o.kernel_timing != 0;
+
+  if (o.use_graph) {
+    const auto key = std::make_tuple((int)method, n_iter, y_dev, x_dev, o.omega, o.nonneg,
+                                     o.power_iters, o.power_v0_dev, o.kernel_timing);
+    auto it = plan->graphs.find(key);
+    if (it == plan->graphs.end()) {
+      pa_plan::GraphEntry entry;
+      t.entry = &entry;
+      PA_CUDA(cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal));
+      pa_status s = enqueue_recon(plan, method, n_iter, y_dev, x_dev, o, t, plan->cap_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(plan->cap_stream, &graph);
+      if (s != PA_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        for (auto ev : entry.fwd_ev) cudaEventDestroy(ev);
+        for (auto ev : entry.adj_ev) cudaEventDestroy(ev);
+        if (s != PA_OK) return s;
+        return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+      }
+      e = cudaGraphInstantiate(&entry.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+      it = plan->graphs.emplace(key, std::move(entry)).first;
+    }
+    PA_CUDA(cudaGraphLaunch(it->second.exec, st));
+    if (t.on) plan->last_timed = &it->second;
+  } else {
+    for (auto ev : plan->direct.fwd_ev) cudaEventDestroy(ev);
+    for (auto ev : plan->direct.adj_ev) cudaEventDestroy(ev);
+    plan->direct.fwd_ev.clear();
+    plan->direct.adj_ev.clear();
+    t.entry = &plan->direct;
+    PA_TRY(enqueue_recon(plan, method, n_iter, y_dev, x_dev, o, t, st));
+    if (t.on) plan->last_timed = &plan->direct;
+  }
+  if (o.residual_history_host) {
+    const Scalars sc = scalars(plan, n_iter);
+    PA_CUDA(cudaMemcpyAsync(o.residual_history_host, sc.hist, (size_t)(n_iter + 1) * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    PA_CUDA(cudaStreamSynchronize(st));
+  }
+  return PA_OK;
+}
+
+pa_status pa_reconstruct_host(pa_plan* plan, pa_method method, int n_iter, const void* y_host,
+                              float* x_host, const pa_recon_opts* opts, pa_stream stream) {
+  if (!plan || !y_host || !x_host) {
+    set_error("pa_reconstruct_host: NULL argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  const size_t N = (size_t)plan->grid.nx * plan->grid.ny * plan->grid.nz;
+  const size_t ybytes = (size_t)plan->S * plan->K * (plan->y_f16 ? 2 : 4);
+  PA_TRY(alloc_once(plan, reinterpret_cast<unsigned char**>(&plan->d_yhost), ybytes));
+  PA_TRY(alloc_once(plan, &plan->d_xhost, N));
+  cudaStream_t st = (cudaStream_t)stream;
+  PA_CUDA(cudaMemcpyAsync(plan->d_yhost, y_host, ybytes, cudaMemcpyHostToDevice, st));
+  PA_CUDA(cudaMemcpyAsync(plan->d_xhost, x_host, N * sizeof(float), cudaMemcpyHostToDevice, st));
+  PA_TRY(pa_reconstruct(plan, method, n_iter, plan->d_yhost, plan->d_xhost, opts, stream));
+  PA_CUDA(cudaMemcpyAsync(x_host, plan->d_xhost, N * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PA_CUDA(cudaStreamSynchronize(st));
+  return PA_OK;
+}
+
+pa_status pa_plan_kernel_times(pa_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,
+                               int* n_adj) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return PA_ERR_INVALID_ARG;
+  }
+  double tf = 0.0, ta = 0.0;
+  int cf = 0, ca = 0;
+  if (plan->last_timed) {
+    const auto& e = *plan->last_timed;
+    for (size_t i = 0; i + 1 < e.fwd_ev.size(); i += 2) {
+      float ms = 0.f;
+      PA_CUDA(cudaEventElapsedTime(&ms, e.fwd_ev[i], e.fwd_ev[i + 1]));
+      tf += ms;
+      ++cf;
+    }
+    for (size_t i = 0; i + 1 < e.adj_ev.size(); i += 2) {
+      float ms = 0.f;
+      PA_CUDA(cudaEventElapsedTime(&ms, e.adj_ev[i], e.adj_ev[i + 1]));
+      ta += ms;
+      ++ca;
+    }
+  }
+  if (fwd_ms) *fwd_ms = tf;
+  if (n_fwd) *n_fwd = cf;
+  if (adj_ms) *adj_ms = ta;
+  if (n_adj) *n_adj = ca;
+  return PA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+"""GPU operators A and A^T against the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2404_10928_gb300 import phantoms as ph
+
+from helpers import OP_TOL, f32, operator_cases, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = operator_cases()
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_10928_gb300 import build
+    build.build()
+    return torch
+
+
+def _plan(prob):
+    from paper_2404_10928_gb300.api import Plan
+    return Plan.from_problem(prob)
+
+
+def _inputs(prob, seed=0):
+    rng = np.random.default_rng(seed)
+    x = f32(prob.x_true if prob.x_true is not None else rng.uniform(0, 1, prob.n_pixels))
+    y = f32(rng.standard_normal((prob.n_sensors, prob.n_samples)))
+    return x, y
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_forward_adjoint_match_oracle(torch_cuda, name):
+    torch = torch_cuda
+    prob = CASES[name]
+    geo = orc.Geometry.of(prob)
+    x, y = _inputs(prob)
+    with _plan(prob) as plan:
+        p_gpu = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda"))
+        g_gpu = plan.adjoint(torch.tensor(y, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        plan.sync_status()
+        p_gpu, g_gpu = p_gpu.cpu().numpy(), g_gpu.cpu().numpy()
+    p_ref = orc.forward(geo, x)
+    g_ref = orc.adjoint(geo, y)
+    assert rel_l2(p_gpu, p_ref) <= OP_TOL, rel_l2(p_gpu, p_ref)
+    assert rel_l2(g_gpu, g_ref) <= OP_TOL, rel_l2(g_gpu, g_ref)
+
+
+@pytest.mark.parametrize("name", ["ragged-37x53-ring13-k301", "3d-33x9x17-ragged"])
+def test_adjoint_identity_and_determinism(torch_cuda, name):
+    torch = torch_cuda
+    prob = CASES[name]
+    x, y = _inputs(prob, seed=1)
+    rng = np.random.default_rng(2)
+    x = f32(rng.normal(size=prob.n_pixels))  # signed image
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    with _plan(prob) as plan:
+        a1, b1 = plan.forward(xt).cpu().numpy(), plan.adjoint(yt).cpu().numpy()
+        a2, b2 = plan.forward(xt).cpu().numpy(), plan.adjoint(yt).cpu().numpy()
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)  # bitwise reproducible
+    lhs = float(np.dot(a1.astype(np.float64).ravel(), y.ravel()))
+    rhs = float(np.dot(x, b1.astype(np.float64)))
+    scale = np.linalg.norm(a1) * np.linalg.norm(y)
+    assert abs(lhs - rhs) <= 1e-6 * scale, (lhs, rhs)
+
+
+def test_linearity_and_zero(torch_cuda):
+    torch = torch_cuda
+    prob = CASES["ragged-37x53-ring13-k301"]
+    rng = np.random.default_rng(5)
+    a = torch.tensor(rng.normal(size=prob.n_pixels), dtype=torch.float32, device="cuda")
+    with _plan(prob) as plan:
+        z = plan.forward(torch.zeros_like(a)).cpu().numpy()
+        assert np.all(z == 0.0)
+        pa = plan.forward(a).cpu().numpy()
+        pb = plan.forward(2.0 * a).cpu().numpy()
+    assert rel_l2(pb, 2.0 * pa) <= 1e-6
+
+
+@pytest.mark.parametrize("factory", ["ring_vessels", "planar_vessel_tree"])
+def test_full_size_operators(torch_cuda, factory):
+    """The benchmark workloads at full size (2D 256^2 x 256 sensors x 2048 samples;
+    3D 128^3 x 1024 sensors x 1024 samples) in the launch configuration the
+    benchmark uses."""
+    torch = torch_cuda
+    prob = getattr(ph, factory)()
+    geo = orc.Geometry.of(prob)
+    x, y = _inputs(prob, seed=3)
+    with _plan(prob) as plan:
+        p_gpu = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+        g_gpu = plan.adjoint(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
+        plan.sync_status()
+    assert rel_l2(p_gpu, orc.forward(geo, x)) <= OP_TOL
+    assert rel_l2(g_gpu, orc.adjoint(geo, y)) <= OP_TOL
+
+
+def test_sound_speed_change(torch_cuda):
+    torch = torch_cuda
+    prob = CASES["ragged-37x53-ring13-k301"]
+    x, y = _inputs(prob, seed=4)
+    with _plan(prob) as plan:
+        plan.set_sound_speed(1540.0)
+        p_gpu = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel_l2(p_gpu, orc.forward(orc.Geometry.of(prob, c=1540.0), x)) <= OP_TOL
+
+
+def test_bad_tensor_arguments(torch_cuda):
+    torch = torch_cuda
+    prob = CASES["ragged-37x53-ring13-k301"]
+    with _plan(prob) as plan:
+        with pytest.raises(ValueError):
+            plan.forward(torch.zeros(prob.n_pixels + 1, device="cuda"))
+        with pytest.raises(ValueError):
+            plan.forward(torch.zeros(prob.n_pixels, device="cuda", dtype=torch.float64))

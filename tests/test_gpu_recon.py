@@ -1,0 +1,182 @@
+"""GPU Landweber / CGLS / power iteration against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2404_10928_gb300 import phantoms as ph
+
+from helpers import OP_TOL, RECON_TOL, f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_10928_gb300 import build
+    build.build()
+    return torch
+
+
+def _plan(prob, **kw):
+    from paper_2404_10928_gb300.api import Plan
+    return Plan.from_problem(prob, **kw)
+
+
+def _dev(torch, a, dtype=None):
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float32, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def disks():
+    prob = ph.linear_array_disks()
+    geo = orc.Geometry.of(prob)
+    y = f32(orc.forward(geo, prob.x_true))
+    v0 = f32(ph.power_start(prob.n_pixels))
+    lam = orc.power_iteration(geo, v0, 50)
+    return prob, geo, y, v0, lam
+
+
+def test_power_iteration(torch_cuda, disks):
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    with _plan(prob) as plan:
+        lam_gpu = plan.power_iteration(50, _dev(torch, v0))
+    assert abs(lam_gpu - lam) <= OP_TOL * lam, (lam_gpu, lam)
+
+
+def test_landweber_given_step(torch_cuda, disks):
+    """10 projected Landweber steps (the linear-array disk workload), step 1/sigma^2."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    x_ref, h_ref = orc.landweber(geo, y, 10, omega=1.0 / lam)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "landweber", 10, omega=1.0 / lam, history=True)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL, atol=RECON_TOL * h_ref[0])
+    assert np.all(np.diff(h) <= 1e-7 * h[0])
+    assert np.all(x >= 0.0)
+
+
+def test_landweber_own_power_iteration(torch_cuda, disks):
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    x_ref, _ = orc.landweber(geo, y, 10, omega=1.0 / lam)
+    with _plan(prob) as plan:
+        x = plan.reconstruct(_dev(torch, y), "landweber", 10, omega=0.0, power_iters=50,
+                             power_v0=_dev(torch, v0)).cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+
+
+@pytest.fixture(scope="module")
+def vessels():
+    prob = ph.ring_vessels()
+    geo = orc.Geometry.of(prob)
+    clean = orc.forward(geo, prob.x_true)
+    y = f32(ph.add_noise(clean, prob.noise_unit, prob.noise_level))
+    return prob, geo, y
+
+
+def test_cgls_ring_vessels_early(torch_cuda, vessels):
+    """CGLS before the semi-convergence knee: parity with the FP64 oracle at 1e-4."""
+    torch = torch_cuda
+    prob, geo, y = vessels
+    x_ref, h_ref = orc.cgls(geo, y, 5)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "cgls", 5, history=True)
+    assert rel_l2(x.cpu().numpy(), x_ref) <= RECON_TOL
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL)
+
+
+# Past ~8 iterations CGLS on this workload amplifies 1e-8-level perturbations to
+# the 1e-3 level: the FP64 oracle itself, with only its iteration vectors
+# rounded to FP32, departs from exact FP64 CGLS by 1.7e-3 (20 iterations) and
+# 2.2e-3 (50 iterations); with operator errors of 3e-6 (the FP32 operators'
+# level) the departure reaches 2.8e-2 in 3D.  The full-length runs are therefore
+# checked against that envelope, not against 1e-4.
+CGLS_X_ENVELOPE = 2e-2
+CGLS_HIST_ENVELOPE = 2e-3
+
+
+def test_cgls_ring_vessels_full(torch_cuda, vessels):
+    """50 CGLS iterations on the full 256^2 ring workload with 1% noise."""
+    torch = torch_cuda
+    prob, geo, y = vessels
+    x_ref, h_ref = orc.cgls(geo, y, 50)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "cgls", 50, history=True)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= CGLS_X_ENVELOPE, rel_l2(x, x_ref)
+    assert np.max(np.abs(h - h_ref)) <= CGLS_HIST_ENVELOPE * h_ref[0]
+    assert np.all(np.diff(h) <= 1e-7 * h[0])
+    # same reconstruction quality against the phantom
+    e_gpu, e_ref = rel_l2(x, prob.x_true), rel_l2(x_ref, prob.x_true)
+    assert abs(e_gpu - e_ref) <= 0.02 * e_ref, (e_gpu, e_ref)
+
+
+def test_graph_direct_and_host_paths_agree(torch_cuda, vessels):
+    """Graph replay, direct launches and the host-buffer entry point give
+    bitwise identical results (fixed-order reductions, no atomics)."""
+    torch = torch_cuda
+    prob, geo, y = vessels
+    with _plan(prob) as plan:
+        yd = _dev(torch, y)
+        a = plan.reconstruct(yd, "cgls", 8, use_graph=True).cpu().numpy()
+        b = plan.reconstruct(yd, "cgls", 8, use_graph=True).cpu().numpy()  # replay
+        c = plan.reconstruct(yd, "cgls", 8, use_graph=False).cpu().numpy()
+        d = plan.reconstruct_host(np.ascontiguousarray(y, dtype=np.float32), "cgls", 8)
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+
+
+def test_zero_iterations_and_warm_start(torch_cuda, disks):
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    rng = np.random.default_rng(3)
+    x0 = f32(rng.normal(size=prob.n_pixels))
+    with _plan(prob) as plan:
+        xl = plan.reconstruct(_dev(torch, y), "landweber", 0, x0=_dev(torch, x0), omega=1.0 / lam)
+        xc = plan.reconstruct(_dev(torch, y), "cgls", 0, x0=_dev(torch, x0))
+        xw, hw = plan.reconstruct(_dev(torch, y), "cgls", 5, x0=_dev(torch, x0), nonneg=False,
+                                  history=True)
+    assert np.array_equal(xl.cpu().numpy(), x0.astype(np.float32))  # untouched
+    assert np.array_equal(xc.cpu().numpy(), np.maximum(x0, 0).astype(np.float32))
+    x_ref, h_ref = orc.cgls(geo, y, 5, x0=x0, nonneg=False)
+    assert rel_l2(xw.cpu().numpy(), x_ref) <= RECON_TOL
+    np.testing.assert_allclose(hw, h_ref, rtol=RECON_TOL, atol=RECON_TOL * h_ref[0])
+
+
+def test_f16_measurements(torch_cuda, disks):
+    """Measured traces stored as FP16 (the ragged time-series workload's format);
+    both sides consume the same quantised values, arithmetic stays FP32."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    y16 = y.astype(np.float16)
+    x_ref, _ = orc.landweber(geo, y16.astype(np.float64), 10, omega=1.0 / lam)
+    with _plan(prob, y_dtype="f16") as plan:
+        x = plan.reconstruct(_dev(torch, y16, torch.float16), "landweber", 10,
+                             omega=1.0 / lam).cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL
+
+
+def test_cgls_3d_small(torch_cuda):
+    """3D planar-array vessel tree at 32^3 (the 128^3 workload's geometry, scaled):
+    5 CGLS iterations at 1e-4; 30 iterations within the rounding envelope."""
+    torch = torch_cuda
+    prob = ph.planar_vessel_tree(n=32)
+    geo = orc.Geometry.of(prob)
+    y = f32(orc.forward(geo, prob.x_true))
+    x5, h5 = orc.cgls(geo, y, 5)
+    x30, h30 = orc.cgls(geo, y, 30)
+    with _plan(prob) as plan:
+        g5, gh5 = plan.reconstruct(_dev(torch, y), "cgls", 5, history=True)
+        g30, gh30 = plan.reconstruct(_dev(torch, y), "cgls", 30, history=True)
+    assert rel_l2(g5.cpu().numpy(), x5) <= RECON_TOL
+    np.testing.assert_allclose(gh5, h5, rtol=RECON_TOL)
+    g30 = g30.cpu().numpy()
+    assert rel_l2(g30, x30) <= 5e-2
+    assert np.max(np.abs(gh30 - h30)) <= 5e-3 * h30[0]
+    assert np.all(np.diff(gh30) <= 1e-7 * gh30[0])
+    assert rel_l2(g30, prob.x_true) <= 2.0 * rel_l2(x30, prob.x_true)
