@@ -172,6 +172,33 @@ pa_status pa_reconstruct_host(pa_plan *plan, pa_method method, int n_iter, const
 pa_status pa_plan_kernel_times(pa_plan *plan, double *fwd_ms, int *n_fwd, double *adj_ms,
                                int *n_adj);
 
+/* x = A^T p like pa_adjoint, but without allocating any device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate GPU memory after start-up -- an application whose memory pool
+ * owns the whole device, a plugin whose host framework forbids allocations
+ * outside its own allocator, a real-time pipeline with a fixed memory budget.
+ * It takes the geometry directly (as pa_plan_create does: host sensors
+ * [n_sensors][dim], grid, c, fs, n_samples, optional opts) plus the caller's
+ * traces p_dev ([S][K] float32, device) and output image x_dev ([N] float32,
+ * device, fully overwritten).  All working memory lives in one device array of
+ * 32 MiB that the library declares statically: every GPU that loads the
+ * library holds it until the process exits.  Geometries needing more scratch
+ * than that, or a staged trace window of more than 48 KiB of shared memory,
+ * return PA_ERR_UNSUPPORTED with a message (use a plan instead).
+ *   - The first call on a device looks up the array's device address (a
+ *     runtime symbol query, not an allocation); make that first call before
+ *     any stream capture on that device.
+ *   - Each call rebuilds the geometry tables in the array and blocks until they
+ *     are built; the adjoint itself is then enqueued on `stream`.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (other streams, other host threads) race
+ *     and corrupt each other's results; serialise them.
+ *   - Device-side wait timeouts are not reported by this entry point. */
+pa_status pa_adjoint_static(const double *sensors_xyz, int n_sensors, const pa_grid *grid,
+                            double c, double fs, int n_samples, const pa_plan_opts *opts,
+                            const float *p_dev, float *x_dev, pa_stream stream);
+
 const char *pa_status_string(pa_status status);
 const char *pa_last_error(void);
 int pa_version(void);
