@@ -49,9 +49,10 @@ def cores():
 
 
 def cgls_launches(n_iter: int) -> int:
-    """Kernels of one CGLS reconstruction: setup (A, reduce, pack, A^T, reduce),
-    7 per iteration (A, reduce, update, reduce, A^T, reduce, p-update), final clamp."""
-    return 5 + 7 * n_iter + 1
+    """Kernels of one CGLS reconstruction (A is two kernels: tile gather + combine):
+    setup (A, reduce, pack, A^T, reduce) = 6, per iteration (A, reduce, x/r update,
+    reduce, A^T, reduce, p update) = 8, final clamp = 1."""
+    return 6 + 8 * n_iter + 1
 
 
 def cgls_applications(n_iter: int) -> int:
@@ -300,7 +301,7 @@ def run_gpu(args):
         dom_is_adj = adj_ms >= fwd_ms
         launch_ms = (adj_ms / max(n_adj, 1)) if dom_is_adj else (fwd_ms / max(n_fwd, 1))
         achieved = prob.pairs * FLOPS_PER_PAIR / (launch_ms * 1e-3) / 1e12
-        kname = "k_adjoint<2>" if dom_is_adj else "k_forward<2>"
+        kname = "k_adjoint<2>" if dom_is_adj else "k_fwd_tile<2>+k_fwd_combine"
         clk = clocks.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -116,7 +116,7 @@ typedef struct {
   int tile[3];              /* pixel tile of the gather kernels */
   int window;               /* trace samples staged per (tile, sensor) */
   int cluster;              /* CTAs per tile in the adjoint (sensor split) */
-  int fwd_bins;             /* samples per forward-gather CTA */
+  int fwd_sensors;          /* sensors per forward-gather CTA */
   int64_t device_bytes;     /* device memory owned by the plan */
 } pa_plan_info;
 

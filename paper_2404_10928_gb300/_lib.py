@@ -48,7 +48,7 @@ class pa_recon_opts(ctypes.Structure):
 class pa_plan_info(ctypes.Structure):
     _fields_ = [("n_pixels", c_int64), ("n_sensors", c_int64), ("n_samples", c_int64),
                 ("pairs", c_int64), ("tile", c_int * 3), ("window", c_int), ("cluster", c_int),
-                ("fwd_bins", c_int), ("device_bytes", c_int64)]
+                ("fwd_sensors", c_int), ("device_bytes", c_int64)]
 
 
 _P = c_void_p  # opaque pa_plan*

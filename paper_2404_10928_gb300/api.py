@@ -94,7 +94,7 @@ class Plan:
         check(self._lib.pa_plan_query(self._h, ctypes.byref(inf)), "pa_plan_query")
         return {"n_pixels": inf.n_pixels, "n_sensors": inf.n_sensors, "n_samples": inf.n_samples,
                 "pairs": inf.pairs, "tile": tuple(inf.tile), "window": inf.window,
-                "cluster": inf.cluster, "fwd_bins": inf.fwd_bins,
+                "cluster": inf.cluster, "fwd_sensors": inf.fwd_sensors,
                 "device_bytes": inf.device_bytes}
 
     def set_sound_speed(self, c: float):

@@ -96,17 +96,18 @@ struct AdjParams {
 
 struct FwdParams {
   const TileRef* table;   // [ntiles][S]
-  const int2* krange;     // [S][ntiles]: (first tap, last tap) or (kSkip, .)
-  const int* order;       // [S * nwin] CTA -> work item s * nwin + window, heaviest first
   const float* x;         // [N]
-  int S, K, W, ntiles, nwin;
+  float* part;            // [S][ntiles][L] window of each (tile, sensor) pair
+  const int2* sorted;     // [S][ntiles]: (tile, klo) of the pairs that are not skipped, by klo
+  const int* upper;       // [S][K + L]: at k + L, how many sorted tiles have klo <= k
+  int S, K, L, ntiles;
   GridF g;
-  float kappa, inv_kappa, half_inv_kappa, amp;
+  float kappa, inv_kappa, half_inv_kappa, amp, half_hmin;
   int mode;
   float* out;             // [S][K]
   const void* y;          // [S][K] measured traces (FWD_RESID), f32 or f16
   int y_f16;
-  double* partials;       // one FP64 partial per CTA (FWD_RESID / FWD_NORM)
+  double* partials;       // one FP64 partial per combine CTA (FWD_RESID / FWD_NORM)
   int* err;
 };
 
@@ -126,9 +127,10 @@ constexpr int kAdjSB = 8;                    // sensors per pipeline stage
 constexpr int kAdjStages = 4;
 
 // forward kernel shape
-constexpr int kFwdWarps = 8;
-constexpr int kFwdThreads = 32 * kFwdWarps;
-constexpr int kFwdBins = 256;                // samples per CTA
+constexpr int kFwdThreads = 256;             // 4 pixels of the tile per thread
+constexpr int kFwdSPC = 32;                  // sensors per tile CTA
+constexpr int kFwdSB = 8;                    // sensors per accumulation stage
+constexpr int kCombThreads = 256;            // samples per combine CTA
 
 // ---------------------------------------------------------------------------
 // launchers (pa_ops.cu)
@@ -142,7 +144,8 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
 int adjoint_smem_bytes(int L);
 cudaError_t configure_kernels(int smem_adj, int smem_fwd);
-int forward_smem_bytes(int ntiles);
+int forward_smem_bytes(int L);
+int forward_combine_blocks(int S, int K);
 pa_status validate_grid(const pa_grid* g);
 
 // reductions and vector updates
@@ -183,13 +186,14 @@ struct pa_plan {
   int pad = 0;      // zero samples on each side of a packed trace
   int Kp = 0;       // packed row length (even)
   int cluster = 1;  // adjoint CTAs per tile
-  int fwd_windows = 0;
 
   // device memory owned by the plan
   double* d_sensors = nullptr;
   pa::TileRef* d_table = nullptr;
   int2* d_krange = nullptr;
-  int* d_order = nullptr;
+  float* d_part = nullptr;    // forward window partials [S][ntiles][L]
+  int2* d_sorted = nullptr;   // [S][ntiles]
+  int* d_upper = nullptr;     // [S][K + L]
   float2* d_packed = nullptr;
   int* d_err = nullptr;
   double* d_partials = nullptr;

@@ -525,285 +525,194 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 }
 
 // ---------------------------------------------------------------------------
-// A: (sensor, window of W samples) gather.
+// A, stage 1: pixel-tile gather of per-(tile, sensor) trace windows.
 //
-// A CTA owns the W output samples [kb, kb + W) of one sensor.  It lists, in
-// tile order, the pixel tiles whose arrival span meets the window, then, a
-// batch of tiles at a time, keeps the 32-pixel chunks (a tile row in 2D, two
-// rows in 3D) whose conservative arrival range meets the window.  Warps take
-// the surviving chunks round robin; every pixel adds (x (1-f)/d, x f/d) to the
-// sample pair (k0, k0 + 1).  Along a row on one side of the sensor the arrival
-// grows monotonically with distance from the sensor, so equal k0 sit in
-// adjacent lanes: a segmented shuffle scan sums them (fixed tree order) and
-// the last lane of each segment adds the sum to the warp's private histogram,
-// one run (row, side) per round.  If FP32 rounding ever broke the monotone
-// order, the chunk falls back to adding its segments one lane at a time.  The
-// warp histograms are summed in warp order: no atomics, bitwise reproducible.
+// A CTA owns one 1024-pixel tile and kFwdSPC sensors: four pixels per thread,
+// kept in registers with their offsets.  For each sensor, every pixel adds its
+// two taps x (1-f)/d and x f/d to the (tile, sensor) window of L samples in
+// shared memory.  The taps are added as fixed-point integers (scaled so that a
+// window sum cannot exceed 2^30): integer addition is associative, so the
+// shared-memory atomics give the same bits in any order.  Windows are written
+// out (rescaled to float) once per stage of kFwdSB sensors.
+//
+// A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
+// k, in a fixed order (by window start), plus the residual / norm epilogue.
 // ---------------------------------------------------------------------------
-constexpr int kFwdBatchTiles = kFwdThreads / 32;  // 32 candidate chunks per tile
-
-int forward_smem_bytes(int ntiles) {
-  return kFwdWarps * (kFwdBins + 1) * (int)sizeof(float2) +   // warp histograms
-         ((ntiles + 3) / 4 * 4) * (int)sizeof(int) +          // hit tiles
-         kFwdThreads * (int)sizeof(int) +                     // surviving chunks
-         kFwdBatchTiles * (int)sizeof(TileRef) +              // references of a batch
-         kFwdBatchTiles * (int)sizeof(int4);                  // tile coordinates
+int forward_smem_bytes(int L) {
+  return kFwdSPC * (int)sizeof(TileRef) + 2 * kFwdSB * L * (int)sizeof(int);
 }
 
-// Block-wide ordered compaction: returns the number of `keep` threads with a
-// lower thread index (their output slot) and writes the total to *total.
-__device__ __forceinline__ int block_compact(bool keep, int* s_wcount, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned bal = __ballot_sync(0xffffffffu, keep);
-  if (lane == 0) s_wcount[warp] = __popc(bal);
-  __syncthreads();
-  int off = 0, tot = 0;
-  for (int w = 0; w < kFwdWarps; ++w) {
-    if (w < warp) off += s_wcount[w];
-    tot += s_wcount[w];
-  }
-  __syncthreads();
-  *total = tot;
-  return off + __popc(bal & ((1u << lane) - 1u));
-}
-
-// Conservative arrival range of chunk c of a tile (FP32; error ~1e-4 samples,
-// callers add a margin of one sample).
-template <int DIM>
-__device__ __forceinline__ void chunk_range(const TileRef& r, int c, int nvx, int nvy, int nvz,
-                                            const GridF& g, float kappa, float hik, float& umin,
-                                            float& umax) {
-  constexpr int TY = Tile<DIM>::Y;
-  const float ex = r.ex2k * hik, ey = r.ey2k * hik, ez = r.ez2k * hik;
-  const float ax0 = ex - (float)(nvx - 1) * g.hdx;
-  const float ax1 = ex + (float)(nvx - 1) * g.hdx;
-  const float mx = (ax0 > 0.f) ? ax0 : ((ax1 < 0.f) ? -ax1 : 0.f);
-  const float Mx = fmaxf(fabsf(ax0), fabsf(ax1));
-  float yz_min, yz_max;
-  if (DIM == 2) {
-    const float ay = ey + (float)(2 * c - (nvy - 1)) * g.hdy;
-    yz_min = yz_max = ay * ay;
-  } else {
-    const int ly0 = 2 * (c % (TY / 2)), lz = c / (TY / 2);
-    const int ly1 = min(ly0 + 1, nvy - 1);
-    const float ay0 = ey + (float)(2 * ly0 - (nvy - 1)) * g.hdy;
-    const float ay1 = ey + (float)(2 * ly1 - (nvy - 1)) * g.hdy;
-    const float az = ez + (float)(2 * lz - (nvz - 1)) * g.hdz;
-    yz_min = fminf(ay0 * ay0, ay1 * ay1) + az * az;
-    yz_max = fmaxf(ay0 * ay0, ay1 * ay1) + az * az;
-  }
-  const float dmin = sqrtf(mx * mx + yz_min), dmax = sqrtf(Mx * Mx + yz_max);
-  const float base = (float)r.klo + r.fref + 0.5f;
-  umin = base + kappa * (dmin - r.dref);
-  umax = base + kappa * (dmax - r.dref);
-}
-
-// lane -> tile-local pixel of chunk c (a row in 2D; two half-warp rows in 3D)
-template <int DIM>
-__device__ __forceinline__ void chunk_pixel(int c, int lane, int& lx, int& ly, int& lz) {
-  if (DIM == 2) {
-    lx = lane;
-    ly = c;
-    lz = 0;
-  } else {
-    lx = lane & 15;
-    ly = 2 * (c & 3) + (lane >> 4);
-    lz = c >> 2;
-  }
-}
+constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
 
 template <int DIM>
-__global__ void __launch_bounds__(kFwdThreads) k_forward(const FwdParams P) {
-  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
-  static_assert(TX * TY * TZ == 32 * 32, "32 chunks of 32 pixels per tile");
-  static_assert(DIM == 2 ? TX == 32 : (TX == 16 && TY == 8 && TZ == 8), "chunk layout");
-  constexpr int W = kFwdBins;
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
+  constexpr int PPT = kTilePixels / kFwdThreads;
   extern __shared__ __align__(128) unsigned char smem[];
-  float2* hist = reinterpret_cast<float2*>(smem);
-  int* tiles = reinterpret_cast<int*>(hist + kFwdWarps * (W + 1));
-  int* chunks = tiles + (P.ntiles + 3) / 4 * 4;
-  TileRef* refs = reinterpret_cast<TileRef*>(chunks + kFwdThreads);
-  int4* tcoord = reinterpret_cast<int4*>(refs + kFwdBatchTiles);
-  __shared__ int s_wcount[kFwdWarps];
-  __shared__ double s_red[kFwdWarps];
+  TileRef* refs = reinterpret_cast<TileRef*>(smem);
+  int* win = reinterpret_cast<int*>(refs + kFwdSPC);
+  __shared__ float s_max[kFwdThreads / 32];
 
-  const int item = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
-  const int s = item / P.nwin, win = item - s * P.nwin, kb = win * W;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float kappa = P.kappa, inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
+  const int L = P.L;
+  const int tile = blockIdx.y;
+  const int s0 = blockIdx.x * kFwdSPC;
+  const int ns = min(kFwdSPC, P.S - s0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
+  int nvx, nvy, nvz;
+  tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
 
-  for (int i = tid; i < kFwdWarps * (W + 1); i += kFwdThreads) hist[i] = make_float2(0.f, 0.f);
-
-  // ordered list of tiles whose taps can land in [kb, kb + W)
-  int n_hit = 0;
-  for (int t0 = 0; t0 < P.ntiles; t0 += kFwdThreads) {
-    const int t = t0 + tid;
-    bool hit = false;
-    if (t < P.ntiles) {
-      const int2 kr = P.krange[(int64_t)s * P.ntiles + t];
-      hit = kr.x != kSkip && kr.x <= kb + W - 1 && kr.y >= kb;
-    }
-    int tot;
-    const int slot = block_compact(hit, s_wcount, &tot);
-    if (hit) tiles[n_hit + slot] = t;
-    n_hit += tot;
+  float ddx[PPT], ddy[PPT], ddz[PPT], cm[PPT], xs[PPT];
+  float amax = 0.0f;
+  int nonfinite = 0;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) {
+    int lx, ly, lz;
+    pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
+    float xv = 0.0f;
+    if (lx < nvx && ly < nvy && lz < nvz)
+      xv = P.x[((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)];
+    amax = fmaxf(amax, fabsf(xv));
+    nonfinite |= !(fabsf(xv) <= 3.0e38f);
+    xs[m] = xv;
+    clamp_local<DIM>(tx, ty, tz, P.g, lx, ly, lz);
+    pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ddx[m], ddy[m], ddz[m], cm[m]);
   }
-  __syncthreads();  // the tile list is complete before any thread reads it
+  {
+    const int4* src = reinterpret_cast<const int4*>(P.table + (int64_t)tile * P.S + s0);
+    int4* dst = reinterpret_cast<int4*>(refs);
+    for (int i = tid; i < ns * 2; i += kFwdThreads) dst[i] = src[i];
+  }
+  for (int i = tid; i < 2 * kFwdSB * L; i += kFwdThreads) win[i] = 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) s_max[warp] = amax;
+  const bool finite = __syncthreads_or(nonfinite) == 0;
+  float xmax = 0.0f;
+  for (int w = 0; w < kFwdThreads / 32; ++w) xmax = fmaxf(xmax, s_max[w]);
+  // |pixel - sensor| >= d_ref - R for every pixel of the tile
+  const float hx = (float)(nvx - 1) * P.g.hdx, hy = (float)(nvy - 1) * P.g.hdy;
+  const float hz = (DIM == 3) ? (float)(nvz - 1) * P.g.hdz : 0.0f;
+  const float R = sqrtf(hx * hx + hy * hy + hz * hz) * 1.0001f;
+  const float xscale = (xmax > 0.0f && finite) ? kFixedScale / xmax : 0.0f;
+#pragma unroll
+  for (int m = 0; m < PPT; ++m) xs[m] *= xscale;  // |xs| <= 2^20
+  const float inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
 
-  float2* myhist = hist + warp * (W + 1);
-  for (int tb = 0; tb < n_hit; tb += kFwdBatchTiles) {
-    // ---- cull the batch's chunks by their conservative arrival range ----
-    const int hs = tid >> 5, c = lane;
-    bool keep = false;
-    if (tb + hs < n_hit) {
-      const int t = tiles[tb + hs];
-      const TileRef r = P.table[(int64_t)t * P.S + s];
-      const int tx = t % P.g.ntx, ty = (t / P.g.ntx) % P.g.nty, tz = t / (P.g.ntx * P.g.nty);
-      int nvx, nvy, nvz;
-      tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
-      if (c == 0) {
-        refs[hs] = r;
-        tcoord[hs] = make_int4(tx * TX, ty * TY, tz * TZ, nvx | (nvy << 8) | (nvz << 16));
-      }
-      int ly, lz;
-      if (DIM == 2) {
-        ly = c;
-        lz = 0;
-      } else {
-        ly = 2 * (c & 3);
-        lz = c >> 2;
-      }
-      if (ly < nvy && lz < nvz) {
-        float umin, umax;
-        chunk_range<DIM>(r, c, nvx, nvy, nvz, P.g, kappa, hik, umin, umax);
-        keep = (umin - 1.0f <= (float)(kb + W - 1)) && (umax + 2.0f >= (float)kb);
-      }
-    }
-    int nch;
-    const int slot = block_compact(keep, s_wcount, &nch);
-    if (keep) chunks[slot] = (hs << 5) | c;
-    __syncthreads();
-
-    // ---- evaluate the surviving chunks ----
-    for (int qi = warp; qi < nch; qi += kFwdWarps) {
-      const int code = chunks[qi];
-      const int hb = code >> 5, cc = code & 31;
-      const TileRef r = refs[hb];
-      const int4 tc = tcoord[hb];
-      int lx, ly, lz;
-      chunk_pixel<DIM>(cc, lane, lx, ly, lz);
-      const int gx = tc.x + lx, gy = tc.y + ly, gz = tc.z + lz;
-      float xv = 0.0f;
-      if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz)
-        xv = P.x[((int64_t)gz * P.g.ny + gy) * P.g.nx + gx];
-      if (!__any_sync(0xffffffffu, xv != 0.0f)) continue;
-      const int nvx = tc.w & 0xff, nvy = (tc.w >> 8) & 0xff, nvz = tc.w >> 16;
-      lx = min(lx, nvx - 1);
-      ly = min(ly, nvy - 1);
-      lz = min(lz, nvz - 1);
-      float ddx, ddy, ddz, cm, rinv, e;
-      int idx;
-      pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, kappa, ddx, ddy, ddz, cm);
-      if (r.flags & kNear)
-        time_of_flight<DIM, true>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv, e, idx);
-      else
-        time_of_flight<DIM, false>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv, e, idx);
-      const int j = r.klo + idx - (kb - 1);  // slot of the tap pair (k0, k0 + 1)
-      const bool inwin = (unsigned)j <= (unsigned)W;
-      const int side = (ddx >= -(r.ex2k * hik)) ? 1 : 0;  // pixel right of the sensor
-      const int run = (DIM == 3 ? ((lane >> 4) << 1) : 0) | side;
-      const float wgt = xv * rinv;
-      const float hw = 0.5f * wgt;
-      float a = inwin ? fmaf(-wgt, e, hw) : 0.0f;  // x (1 - f) / d  -> sample k0
-      float b = inwin ? fmaf(wgt, e, hw) : 0.0f;   // x f / d        -> sample k0 + 1
-      // slot clamped to [-1, W + 1] keeps the order of out-of-window lanes
-      const int jc = min(max(j, -1), W + 1);
-      const int key = (run << 16) | (jc + 1);
-      const int pkey = __shfl_up_sync(0xffffffffu, key, 1);
-      const bool same_run = lane > 0 && (pkey >> 16) == run;
-      const int pjc = (pkey & 0xffff) - 1;
-      const bool viol = same_run && (side ? (pjc > jc) : (pjc < jc));
-      const bool head = inwin && !(same_run && pjc == jc);
-      const unsigned heads = __ballot_sync(0xffffffffu, head);
-      const unsigned inw = __ballot_sync(0xffffffffu, inwin);
-      if (inw == 0u) continue;
-      const bool bad = __any_sync(0xffffffffu, viol);
-      const unsigned le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
-      const int seg = inwin ? 31 - __clz(heads & le) : lane;
-      const unsigned maxlen = __reduce_max_sync(0xffffffffu, (unsigned)(lane - seg + 1));
-      for (unsigned off = 1; off < maxlen; off <<= 1) {
-        const float a2 = __shfl_up_sync(0xffffffffu, a, off);
-        const float b2 = __shfl_up_sync(0xffffffffu, b, off);
-        if (inwin && lane - (int)off >= seg) {
-          a += a2;
-          b += b2;
-        }
-      }
-      const unsigned above = (lane == 31) ? 0u : (heads | ~inw) >> (lane + 1);
-      const bool tail = inwin && (lane == 31 || (above & 1u));
-      if (!bad) {
-        unsigned rmask = __reduce_or_sync(0xffffffffu, tail ? (1u << run) : 0u);
-        while (rmask) {
-          const int rr = __ffs(rmask) - 1;
-          rmask &= rmask - 1u;
-          if (tail && run == rr) {
-            float2 h = myhist[j];
-            h.x += a;
-            h.y += b;
-            myhist[j] = h;
+  for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
+    int* wb = win + buf * kFwdSB * L;
+    const int nsb = min(kFwdSB, ns - g0);
+    if (xscale > 0.0f) {
+      for (int sb = 0; sb < nsb; ++sb) {
+        const TileRef r = refs[g0 + sb];
+        if (r.klo == kSkip) continue;
+        const float dlo = fmaxf(r.dref - R, P.half_hmin);
+        int* w = wb + sb * L;
+        if (r.flags & kNear) {
+#pragma unroll
+          for (int m = 0; m < PPT; ++m) {
+            float rinv, e;
+            int idx;
+            time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
+                                      idx);
+            const float ws = (xs[m] * dlo) * rinv;
+            const int iw = __float_as_int(__fadd_rn(ws, kMagic)) - kMagicBits;
+            const int ia = __float_as_int(__fadd_rn(fmaf(-ws, e, 0.5f * ws), kMagic)) - kMagicBits;
+            atomicAdd(w + idx, ia);
+            atomicAdd(w + idx + 1, iw - ia);
           }
-          __syncwarp();
-        }
-      } else {
-        for (unsigned m = __ballot_sync(0xffffffffu, tail); m; m &= m - 1u) {
-          if (lane == __ffs(m) - 1) {
-            float2 h = myhist[j];
-            h.x += a;
-            h.y += b;
-            myhist[j] = h;
+        } else {
+#pragma unroll
+          for (int m = 0; m < PPT; ++m) {
+            float rinv, e;
+            int idx;
+            time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
+                                       idx);
+            const float ws = (xs[m] * dlo) * rinv;
+            const int iw = __float_as_int(__fadd_rn(ws, kMagic)) - kMagicBits;
+            const int ia = __float_as_int(__fadd_rn(fmaf(-ws, e, 0.5f * ws), kMagic)) - kMagicBits;
+            atomicAdd(w + idx, ia);
+            atomicAdd(w + idx + 1, iw - ia);
           }
-          __syncwarp();
         }
       }
     }
     __syncthreads();
+    for (int i = tid; i < kFwdSB * L; i += kFwdThreads) {
+      const int sb = i / L, k = i - sb * L;
+      if (sb < nsb) {
+        const TileRef& r = refs[g0 + sb];
+        if (r.klo != kSkip) {
+          float v;
+          if (!finite) {
+            v = __int_as_float(0x7fc00000);  // propagate NaN / Inf in x
+          } else if (xscale > 0.0f) {
+            const float dlo = fmaxf(r.dref - R, P.half_hmin);
+            v = (float)wb[i] * (xmax / (kFixedScale * dlo));
+          } else {
+            v = 0.0f;
+          }
+          P.part[((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L + k] = v;
+        }
+      }
+      wb[i] = 0;  // this buffer is reused two stages later, after the next barrier
+    }
   }
+}
 
+template <int MODE>
+__global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P) {
+  __shared__ double s_red[kCombThreads / 32];
+  const int s = blockIdx.y;
+  const int k = blockIdx.x * kCombThreads + threadIdx.x;
   double part = 0.0;
-  for (int m = tid; m < W; m += kFwdThreads) {
-    const int k = kb + m;
-    if (k >= P.K) continue;
+  if (k < P.K) {
+    const int* up = P.upper + (int64_t)s * (P.K + P.L);
+    const int i0 = up[k], i1 = up[k + P.L];  // windows starting in (k - L, k]
+    const int2* srt = P.sorted + (int64_t)s * P.ntiles;
+    const float* ps = P.part + (int64_t)s * P.ntiles * P.L;
     float v = 0.0f;
-    for (int w = 0; w < kFwdWarps; ++w) {
-      const float2* h = hist + w * (W + 1);
-      v += h[m + 1].x + h[m].y;
+    for (int i = i0; i < i1; ++i) {
+      const int2 tk = srt[i];
+      v += ps[(int64_t)tk.x * P.L + (k - tk.y)];
     }
     v *= P.amp;
     const int64_t o = (int64_t)s * P.K + k;
-    if (P.mode == FWD_RESID) {
+    if (MODE == FWD_RESID) {
       const float y = P.y_f16 ? __half2float(reinterpret_cast<const __half*>(P.y)[o])
                               : reinterpret_cast<const float*>(P.y)[o];
       const float rr = y - v;
       P.out[o] = rr;
-      part += (double)rr * (double)rr;
+      part = (double)rr * (double)rr;
     } else {
       P.out[o] = v;
-      part += (double)v * (double)v;
+      part = (double)v * (double)v;
     }
   }
-  if (P.mode != FWD_STORE) {
-    const double t = block_sum<kFwdWarps>(part, s_red);
-    if (tid == 0) P.partials[item] = t;
+  if (MODE != FWD_STORE) {
+    const double t = block_sum<kCombThreads / 32>(part, s_red);
+    if (threadIdx.x == 0) P.partials[(int64_t)s * gridDim.x + blockIdx.x] = t;
   }
 }
 
+int forward_combine_blocks(int S, int K) { return S * ((K + kCombThreads - 1) / kCombThreads); }
+
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
-  const int smem = forward_smem_bytes(p.ntiles);
-  const int grid = p.S * p.nwin;
+  const int smem = forward_smem_bytes(p.L);
+  dim3 grid1((p.S + kFwdSPC - 1) / kFwdSPC, p.ntiles, 1);
   if (dim == 2)
-    k_forward<2><<<grid, kFwdThreads, smem, st>>>(p);
+    k_fwd_tile<2><<<grid1, kFwdThreads, smem, st>>>(p);
   else
-    k_forward<3><<<grid, kFwdThreads, smem, st>>>(p);
+    k_fwd_tile<3><<<grid1, kFwdThreads, smem, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid2((p.K + kCombThreads - 1) / kCombThreads, p.S, 1);
+  if (p.mode == FWD_RESID)
+    k_fwd_combine<FWD_RESID><<<grid2, kCombThreads, 0, st>>>(p);
+  else if (p.mode == FWD_NORM)
+    k_fwd_combine<FWD_NORM><<<grid2, kCombThreads, 0, st>>>(p);
+  else
+    k_fwd_combine<FWD_STORE><<<grid2, kCombThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -817,10 +726,10 @@ cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
   if ((e = cudaFuncSetAttribute(k_adjoint<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_adj)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_forward<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_fwd_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_fwd)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_forward<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd);
+  return cudaFuncSetAttribute(k_fwd_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd);
 }
 
 // ---------------------------------------------------------------------------

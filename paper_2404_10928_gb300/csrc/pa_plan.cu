@@ -74,25 +74,36 @@ static pa_status build_table(pa_plan* p) {
     set_error("internal: a tile's arrival span exceeds the staged window (L=%d)", p->L);
     return PA_ERR_DEVICE_CHECK;
   }
-  // forward work order: (sensor, window) items sorted by the number of tiles
-  // they gather from, heaviest first (stable), so the longest CTAs start first
-  std::vector<int2> kr((size_t)p->S * p->ntiles);
-  PA_CUDA(cudaMemcpy(kr.data(), p->d_krange, kr.size() * sizeof(int2), cudaMemcpyDeviceToHost));
-  const int nwin = p->fwd_windows;
-  std::vector<int64_t> work((size_t)p->S * nwin, 0);
-  for (int s = 0; s < p->S; ++s)
+  // forward combine order: per sensor, the tiles that are not skipped sorted by
+  // window start (ties by tile index), and for every sample k the number of
+  // windows starting at or before k
+  const size_t n_tab = (size_t)p->ntiles * p->S;
+  std::vector<int> klo(n_tab);
+  PA_CUDA(cudaMemcpy2D(klo.data(), sizeof(int), p->d_table, sizeof(TileRef), sizeof(int), n_tab,
+                       cudaMemcpyDeviceToHost));
+  const int KL = p->K + p->L;
+  std::vector<int2> sorted(n_tab);
+  std::vector<int> upper((size_t)p->S * KL);
+  std::vector<int2> row;
+  for (int s = 0; s < p->S; ++s) {
+    row.clear();
     for (int t = 0; t < p->ntiles; ++t) {
-      const int2 r = kr[(size_t)s * p->ntiles + t];
-      if (r.x == kSkip) continue;
-      const int w0 = std::max(0, r.x) / kFwdBins;
-      const int w1 = std::min(nwin - 1, std::max(0, r.y) / kFwdBins);
-      for (int w = w0; w <= w1; ++w) ++work[(size_t)s * nwin + w];
+      const int k0 = klo[(size_t)t * p->S + s];
+      if (k0 != kSkip) row.push_back(make_int2(t, k0));
     }
-  std::vector<int> order(work.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return work[a] > work[b]; });
-  PA_CUDA(cudaMemcpy(p->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::sort(row.begin(), row.end(), [](const int2& a, const int2& b) {
+      return a.y < b.y || (a.y == b.y && a.x < b.x);
+    });
+    std::copy(row.begin(), row.end(), sorted.begin() + (size_t)s * p->ntiles);
+    size_t i = 0;
+    for (int j = 0; j < KL; ++j) {
+      const int k = j - p->L;
+      while (i < row.size() && row[i].y <= k) ++i;
+      upper[(size_t)s * KL + j] = (int)i;
+    }
+  }
+  PA_CUDA(cudaMemcpy(p->d_sorted, sorted.data(), n_tab * sizeof(int2), cudaMemcpyHostToDevice));
+  PA_CUDA(cudaMemcpy(p->d_upper, upper.data(), upper.size() * sizeof(int), cudaMemcpyHostToDevice));
   return PA_OK;
 }
 
@@ -124,7 +135,8 @@ static void free_plan(pa_plan* p) {
     for (auto ev : kv.second.adj_ev) cudaEventDestroy(ev);
   }
   p->graphs.clear();
-  void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_order, p->d_packed, p->d_err, p->d_partials,
+  void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
+                  p->d_packed, p->d_err, p->d_partials,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_sv,  p->d_scal,
                   p->d_yhost,   p->d_xhost};
   for (void* q : ptrs)
@@ -299,7 +311,6 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   }
   p->pad = p->L;
   p->Kp = (p->K + 2 * p->pad + 1) / 2 * 2;
-  p->fwd_windows = (p->K + kFwdBins - 1) / kFwdBins;
   {
     const int sms = num_sms(p->device);
     int C = 1;
@@ -307,7 +318,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     p->cluster = C;
   }
   const size_t smem_adj = (size_t)adjoint_smem_bytes(p->L);
-  if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->ntiles) > 200 * 1024) {
+  if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->L) > 200 * 1024) {
     set_error("geometry needs too much shared memory (window %d samples, %d tiles)", p->L,
               p->ntiles);
     delete p;
@@ -320,7 +331,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     static int configured_adj[64] = {0}, configured_fwd[64] = {0};
     const int dv = p->device & 63;
     const int want_adj = std::max<int>((int)smem_adj, configured_adj[dv]);
-    const int want_fwd = std::max<int>(forward_smem_bytes(p->ntiles), configured_fwd[dv]);
+    const int want_fwd = std::max<int>(forward_smem_bytes(p->L), configured_fwd[dv]);
     cudaError_t e = configure_kernels(want_adj, want_fwd);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
@@ -334,7 +345,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   const size_t n_pix = (size_t)grid->nx * grid->ny * grid->nz;
   const size_t n_tr = (size_t)p->S * p->K;
   p->n_partials = (int)std::max<int64_t>(
-      {(int64_t)p->ntiles * p->cluster, (int64_t)p->S * p->fwd_windows, 152 * 8, 1});
+      {(int64_t)p->ntiles * p->cluster, (int64_t)forward_combine_blocks(p->S, p->K), 152 * 8, 1});
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaStreamCreate failed");
@@ -344,7 +355,9 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   if ((st = dev_alloc(p, &p->d_sensors, p->sensors.size())) != PA_OK ||
       (st = dev_alloc(p, &p->d_table, n_tab)) != PA_OK ||
       (st = dev_alloc(p, &p->d_krange, n_tab)) != PA_OK ||
-      (st = dev_alloc(p, &p->d_order, (size_t)p->S * p->fwd_windows)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_part, n_tab * p->L)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_sorted, n_tab)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_upper, (size_t)p->S * (p->K + p->L))) != PA_OK ||
       (st = dev_alloc(p, &p->d_packed, (size_t)p->S * p->Kp)) != PA_OK ||
       (st = dev_alloc(p, &p->d_err, 1)) != PA_OK ||
       (st = dev_alloc(p, &p->d_partials, (size_t)p->n_partials)) != PA_OK) {
@@ -438,7 +451,7 @@ pa_status pa_plan_query(const pa_plan* plan, pa_plan_info* info) {
   info->tile[2] = plan->dim == 2 ? Tile<2>::Z : Tile<3>::Z;
   info->window = plan->L;
   info->cluster = plan->cluster;
-  info->fwd_bins = kFwdBins;
+  info->fwd_sensors = kFwdSPC;
   info->device_bytes = plan->bytes;
   return PA_OK;
 }
@@ -453,19 +466,22 @@ namespace pa {
 FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode, const void* y) {
   FwdParams f{};
   f.table = p->d_table;
-  f.krange = p->d_krange;
-  f.order = p->d_order;
   f.x = x;
+  f.part = p->d_part;
+  f.sorted = p->d_sorted;
+  f.upper = p->d_upper;
   f.S = p->S;
   f.K = p->K;
-  f.W = kFwdBins;
+  f.L = p->L;
   f.ntiles = p->ntiles;
-  f.nwin = p->fwd_windows;
   f.g = p->g;
   f.kappa = (float)(p->fs / p->c);
   f.inv_kappa = (float)(p->c / p->fs);
   f.half_inv_kappa = (float)(0.5 * p->c / p->fs);
   f.amp = (float)p->amp;
+  const double hmin = p->dim == 3 ? std::fmin(p->grid.dx, std::fmin(p->grid.dy, p->grid.dz))
+                                  : std::fmin(p->grid.dx, p->grid.dy);
+  f.half_hmin = (float)(0.5 * hmin * (1.0 - 1e-6));
   f.mode = mode;
   f.out = out;
   f.y = y;
@@ -498,7 +514,7 @@ AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* o
   return a;
 }
 
-int forward_partials(const pa_plan* p) { return p->S * p->fwd_windows; }
+int forward_partials(const pa_plan* p) { return forward_combine_blocks(p->S, p->K); }
 int adjoint_partials(const pa_plan* p) { return p->ntiles * p->cluster; }
 
 }  // namespace pa
