@@ -49,10 +49,11 @@ def cores():
 
 
 def cgls_launches(n_iter: int) -> int:
-    """Kernels of one CGLS reconstruction (A is two kernels: tile gather + combine):
-    setup (A, reduce, pack, A^T, reduce) = 6, per iteration (A, reduce, x/r update,
-    reduce, A^T, reduce, p update) = 8, final clamp = 1."""
-    return 6 + 8 * n_iter + 1
+    """Kernels of one CGLS reconstruction (A = tile gather + combine; every FP64
+    reduction is finished inside its producer): setup (A, pack, A^T) = 4, per
+    iteration (A with the fused direction update, x/r update, A^T) = 4, final
+    clamp = 1."""
+    return 4 + 4 * n_iter + 1
 
 
 def cgls_applications(n_iter: int) -> int:

@@ -75,9 +75,23 @@ struct GridF {
   float hdx, hdy, hdz;  // half spacings (FP32)
 };
 
+enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3 };
+
 // kernel modes
 enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2 };
 enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
+
+// Cross-CTA FP64 reduction finished inside the producing kernel: every CTA
+// stores its partial, the last CTA to arrive (decided by a counter) sums all
+// partials in index order and applies `op`.  Disabled when partials == nullptr.
+struct Reduce {
+  double* partials;      // one slot per CTA
+  unsigned* counter;     // 0 before the launch; the last CTA resets it
+  int op;                // ScalarOp
+  double* out_sum;       // nullable
+  const double* other;   // gamma for OP_ALPHA / OP_BETA
+  double* out2;          // alpha / beta / 1/sqrt(sum)
+};
 
 struct AdjParams {
   const TileRef* table;   // [ntiles][S]
@@ -89,7 +103,7 @@ struct AdjParams {
   int nonneg;
   float* out;             // [N] image (ADJ_STORE / ADJ_NORM) or x updated in place
   const double* omega;    // device scalar (ADJ_LANDWEBER)
-  double* partials;       // one FP64 partial of ||out||^2 per CTA (ADJ_NORM)
+  Reduce red;             // ||out||^2 (ADJ_NORM)
   int* err;
   int sensors_per_rank;
 };
@@ -107,7 +121,13 @@ struct FwdParams {
   float* out;             // [S][K]
   const void* y;          // [S][K] measured traces (FWD_RESID), f32 or f16
   int y_f16;
-  double* partials;       // one FP64 partial per combine CTA (FWD_RESID / FWD_NORM)
+  Reduce red;             // ||out||^2 (FWD_RESID / FWD_NORM)
+  // optional CGLS direction update fused into the gather: the image applied is
+  // x = s + beta p_old (s_in != nullptr), written to p_new by sensor chunk 0
+  const float* s_in;
+  const float* p_old;
+  float* p_new;
+  const double* beta;
   int* err;
 };
 
@@ -149,21 +169,16 @@ int forward_combine_blocks(int S, int K);
 pa_status validate_grid(const pa_grid* g);
 
 // reductions and vector updates
-enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3, OP_SIGMA = 4 };
-cudaError_t launch_reduce(const double* partials, int n, double* out_sum, int op,
-                          const double* other, double* out2, cudaStream_t st);
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const double* alpha, int N, int S,
-                           int K, int Kp, int pad, double* partials, int nblk_x, int nblk_r,
+                           int K, int Kp, int pad, const Reduce& red, int nblk_x, int nblk_r,
                            cudaStream_t st);
-cudaError_t launch_axpby(float* p, const float* s, const double* beta, int N, cudaStream_t st);
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
-cudaError_t launch_norm_partials(const float* v, int64_t n, double* partials, int nblk,
-                                 cudaStream_t st);
+cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
 
 }  // namespace pa
 
@@ -198,11 +213,13 @@ struct pa_plan {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   int n_partials = 0;
+  unsigned* d_counter = nullptr;  // last-CTA counter of the fused reductions
   // reconstruction workspace (allocated on first use)
   float* d_ra = nullptr;
   float* d_rb = nullptr;
   float* d_q = nullptr;
   float* d_pv = nullptr;
+  float* d_pb = nullptr;      // second CGLS direction buffer (ping-pong)
   float* d_sv = nullptr;
   double* d_scal = nullptr;   // scalar records, see pa_recon.cu
   int scal_cap = 0;

@@ -105,6 +105,42 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
   return t;  // valid in thread 0
 }
 
+// Finishes a Reduce inside the producing kernel (see Reduce).  `part` is the
+// CTA's partial, valid in thread 0; all threads of the CTA must call this.
+template <int NW>
+__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part, int bid, int nblk,
+                                                   double* s_red) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    R.partials[bid] = part;
+    __threadfence();
+    s_last = atomicAdd(R.counter, 1u) == (unsigned)nblk - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += 32 * NW) v += __ldcg(R.partials + i);
+  const double t = block_sum<NW>(v, s_red);
+  if (threadIdx.x == 0) {
+    if (R.out_sum) *R.out_sum = t;
+    switch (R.op) {
+      case OP_ALPHA:  // alpha = gamma / ||q||^2
+        *R.out2 = t > 0.0 ? *R.other / t : 0.0;
+        break;
+      case OP_BETA:  // beta = gamma_new / gamma_old
+        *R.out2 = *R.other > 0.0 ? t / *R.other : 0.0;
+        break;
+      case OP_INVSQRT:  // 1 / ||w||
+        *R.out2 = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+        break;
+      default:
+        break;
+    }
+    *R.counter = 0u;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // per-pixel geometry shared by A and A^T (identical FP32 arithmetic, so the two
 // kernels apply exactly the same matrix entries)
@@ -495,7 +531,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   }
   if (P.mode == ADJ_NORM) {
     const double t = block_sum<kAdjWarps + 1>(part, s_red);
-    if (tid == 0) P.partials[(int64_t)tile * C + rank] = t;
+    reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
   }
   cluster.sync();
   (void)TZ;
@@ -570,8 +606,15 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
     int lx, ly, lz;
     pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
     float xv = 0.0f;
-    if (lx < nvx && ly < nvy && lz < nvz)
-      xv = P.x[((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)];
+    if (lx < nvx && ly < nvy && lz < nvz) {
+      const int64_t i = ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx);
+      if (P.s_in) {  // CGLS direction p = s + beta p_old, stored once (sensor chunk 0)
+        xv = fmaf((float)(*P.beta), P.p_old[i], P.s_in[i]);
+        if (blockIdx.x == 0) P.p_new[i] = xv;
+      } else {
+        xv = P.x[i];
+      }
+    }
     amax = fmaxf(amax, fabsf(xv));
     nonfinite |= !(fabsf(xv) <= 3.0e38f);
     xs[m] = xv;
@@ -638,24 +681,17 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
       }
     }
     __syncthreads();
-    for (int i = tid; i < kFwdSB * L; i += kFwdThreads) {
-      const int sb = i / L, k = i - sb * L;
-      if (sb < nsb) {
-        const TileRef& r = refs[g0 + sb];
-        if (r.klo != kSkip) {
-          float v;
-          if (!finite) {
-            v = __int_as_float(0x7fc00000);  // propagate NaN / Inf in x
-          } else if (xscale > 0.0f) {
-            const float dlo = fmaxf(r.dref - R, P.half_hmin);
-            v = (float)wb[i] * (xmax / (kFixedScale * dlo));
-          } else {
-            v = 0.0f;
-          }
-          P.part[((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L + k] = v;
-        }
+    for (int sb = 0; sb < kFwdSB; ++sb) {
+      const bool store = sb < nsb && refs[g0 + sb].klo != kSkip;
+      float unscale = 0.0f;
+      if (store && finite && xscale > 0.0f)
+        unscale = xmax / (kFixedScale * fmaxf(refs[g0 + sb].dref - R, P.half_hmin));
+      float* dst = P.part + ((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L;
+      int* src = wb + sb * L;
+      for (int k = tid; k < L; k += kFwdThreads) {
+        if (store) dst[k] = finite ? (float)src[k] * unscale : __int_as_float(0x7fc00000);
+        src[k] = 0;  // this buffer is reused two stages later, after the next barrier
       }
-      wb[i] = 0;  // this buffer is reused two stages later, after the next barrier
     }
   }
 }
@@ -672,9 +708,21 @@ __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P)
     const int2* srt = P.sorted + (int64_t)s * P.ntiles;
     const float* ps = P.part + (int64_t)s * P.ntiles * P.L;
     float v = 0.0f;
-    for (int i = i0; i < i1; ++i) {
-      const int2 tk = srt[i];
-      v += ps[(int64_t)tk.x * P.L + (k - tk.y)];
+    int i = i0;
+    for (; i + 4 <= i1; i += 4) {  // four independent loads in flight, summed in order
+      const int2 a = srt[i], b = srt[i + 1], c = srt[i + 2], d = srt[i + 3];
+      const float va = __ldcg(ps + (int64_t)a.x * P.L + (k - a.y));
+      const float vb = __ldcg(ps + (int64_t)b.x * P.L + (k - b.y));
+      const float vc = __ldcg(ps + (int64_t)c.x * P.L + (k - c.y));
+      const float vd = __ldcg(ps + (int64_t)d.x * P.L + (k - d.y));
+      v += va;
+      v += vb;
+      v += vc;
+      v += vd;
+    }
+    for (; i < i1; ++i) {
+      const int2 a = srt[i];
+      v += __ldcg(ps + (int64_t)a.x * P.L + (k - a.y));
     }
     v *= P.amp;
     const int64_t o = (int64_t)s * P.K + k;
@@ -691,7 +739,8 @@ __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P)
   }
   if (MODE != FWD_STORE) {
     const double t = block_sum<kCombThreads / 32>(part, s_red);
-    if (threadIdx.x == 0) P.partials[(int64_t)s * gridDim.x + blockIdx.x] = t;
+    reduce_across_ctas<kCombThreads / 32>(P.red, t, s * gridDim.x + blockIdx.x,
+                                          gridDim.x * gridDim.y, s_red);
   }
 }
 
@@ -733,45 +782,8 @@ cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 reductions of per-CTA partials (one CTA, fixed order) and the scalar
-// steps of the iterations.
+// vector steps of the iterations
 // ---------------------------------------------------------------------------
-constexpr int kRedThreads = 1024;
-
-__global__ void __launch_bounds__(kRedThreads) k_reduce(const double* __restrict__ partials, int n,
-                                                        double* out_sum, int op,
-                                                        const double* other, double* out2) {
-  __shared__ double s_red[kRedThreads / 32];
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += kRedThreads) v += partials[i];
-  const double t = block_sum<kRedThreads / 32>(v, s_red);
-  if (threadIdx.x == 0) {
-    if (out_sum) *out_sum = t;
-    switch (op) {
-      case OP_ALPHA: {  // alpha = gamma / ||q||^2
-        *out2 = t > 0.0 ? *other / t : 0.0;
-        break;
-      }
-      case OP_BETA: {  // beta = gamma_new / gamma_old
-        *out2 = *other > 0.0 ? t / *other : 0.0;
-        break;
-      }
-      case OP_INVSQRT: {  // 1/||w||
-        *out2 = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
-        break;
-      }
-      default:
-        break;
-    }
-  }
-}
-
-cudaError_t launch_reduce(const double* partials, int n, double* out_sum, int op,
-                          const double* other, double* out2, cudaStream_t st) {
-  k_reduce<<<1, kRedThreads, 0, st>>>(partials, n, out_sum, op, other, out2);
-  return cudaGetLastError();
-}
-
 constexpr int kVecThreads = 256;
 
 // CGLS: x += alpha p (first nblk_x blocks); r_out = r_in - alpha q, packed
@@ -779,8 +791,8 @@ constexpr int kVecThreads = 256;
 __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     float* __restrict__ x, const float* __restrict__ pv, const float* __restrict__ r_in,
     float* __restrict__ r_out, const float* __restrict__ q, float2* __restrict__ packed,
-    const double* __restrict__ alpha_p, int N, int S, int K, int Kp, int pad,
-    double* __restrict__ partials, int nblk_x) {
+    const double* __restrict__ alpha_p, int N, int S, int K, int Kp, int pad, const Reduce red,
+    int nblk_x) {
   __shared__ double s_red[kVecThreads / 32];
   const float alpha = (float)(*alpha_p);
   if ((int)blockIdx.x < nblk_x) {
@@ -804,24 +816,16 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     part += (double)rk * (double)rk;
   }
   const double t = block_sum<kVecThreads / 32>(part, s_red);
-  if (threadIdx.x == 0) partials[b] = t;
+  reduce_across_ctas<kVecThreads / 32>(red, t, b, nb, s_red);
 }
 
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const double* alpha, int N, int S,
-                           int K, int Kp, int pad, double* partials, int nblk_x, int nblk_r,
+                           int K, int Kp, int pad, const Reduce& red, int nblk_x, int nblk_r,
                            cudaStream_t st) {
   k_cgls_xr<<<nblk_x + nblk_r, kVecThreads, 0, st>>>(x, pvec, r_in, r_out, q, packed, alpha, N, S,
-                                                     K, Kp, pad, partials, nblk_x);
+                                                     K, Kp, pad, red, nblk_x);
   return cudaGetLastError();
-}
-
-__global__ void k_axpby(float* __restrict__ p, const float* __restrict__ s,
-                        const double* __restrict__ beta_p, int N) {
-  const float beta = (float)(*beta_p);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(beta, p[i], s[i]);
 }
 
 __global__ void k_scale(float* __restrict__ v, const float* __restrict__ w,
@@ -846,25 +850,21 @@ __global__ void k_fill(float* __restrict__ dst, float v, int64_t n) {
     dst[i] = v;
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_norm_partials(const float* __restrict__ v,
-                                                               int64_t n, double* partials) {
+__global__ void __launch_bounds__(kVecThreads) k_norm(const float* __restrict__ v, int64_t n,
+                                                      const Reduce red) {
   __shared__ double s_red[kVecThreads / 32];
   double part = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kVecThreads)
     part += (double)v[i] * (double)v[i];
   const double t = block_sum<kVecThreads / 32>(part, s_red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  reduce_across_ctas<kVecThreads / 32>(red, t, blockIdx.x, gridDim.x, s_red);
 }
 
 static int vec_blocks(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecThreads - 1) / kVecThreads, 152 * 8));
 }
 
-cudaError_t launch_axpby(float* p, const float* s, const double* beta, int N, cudaStream_t st) {
-  k_axpby<<<vec_blocks(N), kVecThreads, 0, st>>>(p, s, beta, N);
-  return cudaGetLastError();
-}
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st) {
   k_scale<<<vec_blocks(N), kVecThreads, 0, st>>>(v, w, factor, N);
@@ -882,9 +882,8 @@ cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
   k_fill<<<vec_blocks(n), kVecThreads, 0, st>>>(dst, value, n);
   return cudaGetLastError();
 }
-cudaError_t launch_norm_partials(const float* v, int64_t n, double* partials, int nblk,
-                                 cudaStream_t st) {
-  k_norm_partials<<<nblk, kVecThreads, 0, st>>>(v, n, partials);
+cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st) {
+  k_norm<<<nblk, kVecThreads, 0, st>>>(v, n, red);
   return cudaGetLastError();
 }
 

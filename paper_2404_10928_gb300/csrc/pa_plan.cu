@@ -137,7 +137,8 @@ static void free_plan(pa_plan* p) {
   p->graphs.clear();
   void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
                   p->d_packed, p->d_err, p->d_partials,
-                  p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_sv,  p->d_scal,
+                  p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
+                  p->d_scal,    p->d_counter,
                   p->d_yhost,   p->d_xhost};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -360,7 +361,8 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
       (st = dev_alloc(p, &p->d_upper, (size_t)p->S * (p->K + p->L))) != PA_OK ||
       (st = dev_alloc(p, &p->d_packed, (size_t)p->S * p->Kp)) != PA_OK ||
       (st = dev_alloc(p, &p->d_err, 1)) != PA_OK ||
-      (st = dev_alloc(p, &p->d_partials, (size_t)p->n_partials)) != PA_OK) {
+      (st = dev_alloc(p, &p->d_partials, (size_t)p->n_partials)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_counter, 4)) != PA_OK) {
     free_plan(p);
     return st;
   }
@@ -370,6 +372,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
                              cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(p->d_packed, 0, (size_t)p->S * p->Kp * sizeof(float2), p->cap_stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counter, 0, 4 * sizeof(unsigned), p->cap_stream);
   if (e != cudaSuccess) {
     st = cuda_fail(e, "upload", __FILE__, __LINE__);
     free_plan(p);
@@ -486,7 +489,7 @@ FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode,
   f.out = out;
   f.y = y;
   f.y_f16 = p->y_f16;
-  f.partials = p->d_partials;
+  f.red = Reduce{};
   f.err = p->d_err;
   return f;
 }
@@ -508,14 +511,22 @@ AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* o
   a.nonneg = nonneg;
   a.out = out;
   a.omega = omega;
-  a.partials = p->d_partials;
+  a.red = Reduce{};
   a.err = p->d_err;
   a.sensors_per_rank = (p->S + p->cluster - 1) / p->cluster;
   return a;
 }
 
-int forward_partials(const pa_plan* p) { return forward_combine_blocks(p->S, p->K); }
-int adjoint_partials(const pa_plan* p) { return p->ntiles * p->cluster; }
+Reduce make_reduce(const pa_plan* p, int op, double* out_sum, const double* other, double* out2) {
+  Reduce r;
+  r.partials = p->d_partials;
+  r.counter = p->d_counter;
+  r.op = op;
+  r.out_sum = out_sum;
+  r.other = other;
+  r.out2 = out2;
+  return r;
+}
 
 }  // namespace pa
 

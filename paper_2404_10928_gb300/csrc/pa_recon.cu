@@ -11,8 +11,7 @@ namespace pa {
 
 FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode, const void* y);
 AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* omega, int nonneg);
-int forward_partials(const pa_plan* p);
-int adjoint_partials(const pa_plan* p);
+Reduce make_reduce(const pa_plan* p, int op, double* out_sum, const double* other, double* out2);
 
 namespace {
 
@@ -75,6 +74,7 @@ pa_status ensure_workspace(pa_plan* p, int n_iter) {
   PA_TRY(alloc_once(p, &p->d_rb, SK));
   PA_TRY(alloc_once(p, &p->d_q, SK));
   PA_TRY(alloc_once(p, &p->d_pv, N));
+  PA_TRY(alloc_once(p, &p->d_pb, N));
   PA_TRY(alloc_once(p, &p->d_sv, N));
   const int need = scalar_count(n_iter);
   if (p->scal_cap < need) {
@@ -107,19 +107,34 @@ pa_status mark(Timing& t, bool fwd, cudaStream_t st) {
   return PA_OK;
 }
 
-pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, Timing& t,
-              cudaStream_t st) {
+// A x (mode FWD_*), with an optional fused reduction of ||out||^2 and an
+// optional fused CGLS direction update (x = s + beta p_old, stored to p_new).
+struct DirUpdate {
+  const float* s = nullptr;
+  const float* p_old = nullptr;
+  float* p_new = nullptr;
+  const double* beta = nullptr;
+};
+
+pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, const Reduce& red,
+              Timing& t, cudaStream_t st, const DirUpdate& du = DirUpdate()) {
   PA_TRY(mark(t, true, st));
-  FwdParams f = forward_params(p, x, out, mode, y);
+  FwdParams f = forward_params(p, du.s ? nullptr : x, out, mode, y);
+  f.red = red;
+  f.s_in = du.s;
+  f.p_old = du.p_old;
+  f.p_new = du.p_new;
+  f.beta = du.beta;
   PA_CUDA(launch_forward(p->dim, f, st));
   PA_TRY(mark(t, true, st));
   return PA_OK;
 }
 
-pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg, Timing& t,
-              cudaStream_t st) {
+pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg,
+              const Reduce& red, Timing& t, cudaStream_t st) {
   PA_TRY(mark(t, false, st));
   AdjParams a = adjoint_params(p, out, mode, omega, nonneg);
+  a.red = red;
   PA_CUDA(launch_adjoint(p->dim, a, p->cluster, p->ntiles, st));
   PA_TRY(mark(t, false, st));
   return PA_OK;
@@ -133,20 +148,19 @@ int vec_blocks_r(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>
 pa_status enqueue_power(pa_plan* p, int n_pow, const float* v0, const Scalars& sc, Timing& t,
                         cudaStream_t st) {
   const int64_t N = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
+  const Reduce none{};
   if (v0)
     PA_CUDA(cudaMemcpyAsync(p->d_pv, v0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
   else
     PA_CUDA(launch_fill(p->d_pv, 1.0f, N, st));
-  const int nb = vec_blocks_r(N);
-  PA_CUDA(launch_norm_partials(p->d_pv, N, p->d_partials, nb, st));
-  PA_CUDA(launch_reduce(p->d_partials, nb, nullptr, OP_INVSQRT, nullptr, sc.inv_lam, st));
+  PA_CUDA(launch_norm(p->d_pv, N, make_reduce(p, OP_INVSQRT, nullptr, nullptr, sc.inv_lam),
+                      vec_blocks_r(N), st));
   PA_CUDA(launch_scale(p->d_pv, p->d_pv, sc.inv_lam, (int)N, st));
   for (int it = 0; it < n_pow; ++it) {
-    PA_TRY(fwd(p, p->d_pv, p->d_q, FWD_STORE, nullptr, t, st));
+    PA_TRY(fwd(p, p->d_pv, p->d_q, FWD_STORE, nullptr, none, t, st));
     PA_CUDA(launch_pack(p->d_q, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, t, st));
-    PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.lam2, OP_INVSQRT, nullptr,
-                          sc.inv_lam, st));
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0,
+               make_reduce(p, OP_INVSQRT, sc.lam2, nullptr, sc.inv_lam), t, st));
     PA_CUDA(launch_scale(p->d_pv, p->d_sv, sc.inv_lam, (int)N, st));
   }
   return PA_OK;
@@ -162,13 +176,14 @@ pa_status enqueue_landweber(pa_plan* p, int n_iter, const void* y, float* x,
     PA_TRY(enqueue_power(p, o.power_iters > 0 ? o.power_iters : 50, o.power_v0_dev, sc, t, st));
     omega = sc.inv_lam;
   }
+  const Reduce none{};
   for (int it = 0; it <= n_iter; ++it) {
-    PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y, t, st));  // r = y - A x, partial ||r||^2
-    PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.hist + it, OP_SUM, nullptr,
-                          nullptr, st));
+    // r = y - A x and ||r||^2
+    PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y, make_reduce(p, OP_SUM, sc.hist + it, nullptr, nullptr),
+               t, st));
     if (it == n_iter) break;
     PA_CUDA(launch_pack(p->d_ra, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-    PA_TRY(adj(p, x, ADJ_LANDWEBER, omega, o.nonneg, t, st));  // x = max(0, x + w A^T r)
+    PA_TRY(adj(p, x, ADJ_LANDWEBER, omega, o.nonneg, none, t, st));  // x = max(0, x + w A^T r)
   }
   return PA_OK;
 }
@@ -180,27 +195,37 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
   const int nbx = vec_blocks_x(N), nbr = vec_blocks_r(SK);
   float* r_in = p->d_ra;
   float* r_out = p->d_rb;
+  float* p_cur = p->d_pv;
+  float* p_prev = p->d_pb;
   // r = y - A x0; s = A^T r; p = s; gamma = ||s||^2
-  PA_TRY(fwd(p, x, r_in, FWD_RESID, y, t, st));
-  PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.hist, OP_SUM, nullptr, nullptr, st));
+  PA_TRY(fwd(p, x, r_in, FWD_RESID, y, make_reduce(p, OP_SUM, sc.hist, nullptr, nullptr), t, st));
   PA_CUDA(launch_pack(r_in, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-  PA_TRY(adj(p, p->d_pv, ADJ_NORM, nullptr, 0, t, st));
-  PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.gamma, OP_SUM, nullptr, nullptr, st));
+  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, make_reduce(p, OP_SUM, sc.gamma, nullptr, nullptr),
+             t, st));
   for (int it = 0; it < n_iter; ++it) {
+    // p = s + beta p (fused into the gather from the second iteration on);
     // q = A p; alpha = gamma / ||q||^2
-    PA_TRY(fwd(p, p->d_pv, p->d_q, FWD_NORM, nullptr, t, st));
-    PA_CUDA(launch_reduce(p->d_partials, forward_partials(p), sc.delta + it, OP_ALPHA,
-                          sc.gamma + it, sc.alpha + it, st));
+    const Reduce ra = make_reduce(p, OP_ALPHA, sc.delta + it, sc.gamma + it, sc.alpha + it);
+    if (it == 0) {
+      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, ra, t, st));
+    } else {
+      DirUpdate du;
+      du.s = p->d_sv;
+      du.p_old = p_prev;
+      du.p_new = p_cur;
+      du.beta = sc.beta + it - 1;
+      PA_TRY(fwd(p, nullptr, p->d_q, FWD_NORM, nullptr, ra, t, st, du));
+    }
     // x += alpha p; r -= alpha q (packed for the adjoint); ||r||^2
-    PA_CUDA(launch_cgls_xr(x, p->d_pv, r_in, r_out, p->d_q, p->d_packed, sc.alpha + it, N, p->S,
-                           p->K, p->Kp, p->pad, p->d_partials, nbx, nbr, st));
-    PA_CUDA(launch_reduce(p->d_partials, nbr, sc.hist + it + 1, OP_SUM, nullptr, nullptr, st));
-    // s = A^T r; beta = ||s||^2 / gamma; p = s + beta p
-    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, t, st));
-    PA_CUDA(launch_reduce(p->d_partials, adjoint_partials(p), sc.gamma + it + 1, OP_BETA,
-                          sc.gamma + it, sc.beta + it, st));
-    PA_CUDA(launch_axpby(p->d_pv, p->d_sv, sc.beta + it, N, st));
+    PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, sc.alpha + it, N, p->S,
+                           p->K, p->Kp, p->pad,
+                           make_reduce(p, OP_SUM, sc.hist + it + 1, nullptr, nullptr), nbx, nbr,
+                           st));
+    // s = A^T r; beta = ||s||^2 / gamma
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0,
+               make_reduce(p, OP_BETA, sc.gamma + it + 1, sc.gamma + it, sc.beta + it), t, st));
     std::swap(r_in, r_out);
+    std::swap(p_cur, p_prev);
   }
   if (o.nonneg) PA_CUDA(launch_clamp(x, N, st));
   return PA_OK;

@@ -193,7 +193,7 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   a.nonneg = 0;
   a.out = x_dev;
   a.omega = nullptr;
-  a.partials = nullptr;
+  a.red = Reduce{};
   a.err = d_err;
   a.sensors_per_rank = (n_sensors + C - 1) / C;
   PA_CUDA(launch_adjoint(dim, a, C, (int)ntiles, st));
