@@ -155,6 +155,25 @@ pa_status pa_adjoint(pa_plan *plan, const float *p_dev, float *x_dev, pa_stream 
 pa_status pa_power_iteration(pa_plan *plan, int n_iter, const float *v0_dev, double *sigma2,
                              pa_stream stream);
 
+/* Derivative of <g, A(x; c)> with respect to the speed of sound c (the c of
+ * Eq. 1 and Eq. 6), for speed-of-sound calibration:
+ *   dc = sum_s sum_i amp x_i / d_is * (g[s,k0+1] - g[s,k0]) * (-d_is fs / c^2),
+ * k0 = floor(u_is) (the one-sided derivative of the hat that its two-tap form
+ * implies at integer u).  x_dev: [N] float32; g_dev: [S][K] float32 (e.g. the
+ * gradient of a loss with respect to the traces); *dc_dev: one double on the
+ * device, overwritten.  The same value gives <v, (dA^T/dc) r> with x = v, g = r. */
+pa_status pa_dc(pa_plan *plan, const float *x_dev, const float *g_dev, double *dc_dev,
+                pa_stream stream);
+
+/* Smoothed isotropic total variation of an image on the plan's grid (the TV
+ * term of Eq. 8 with Psi' = identity):
+ *   TV(x) = sum_i sqrt(sum_a (x[i + e_a] - x[i])^2 + eps^2),
+ * forward differences, zero difference past the last index along each axis.
+ * *tv_dev (one device double) receives TV(x); grad_dev ([N] float32) receives
+ * dTV/dx.  eps > 0. */
+pa_status pa_tv(pa_plan *plan, const float *x_dev, double eps, double *tv_dev, float *grad_dev,
+                pa_stream stream);
+
 /* Iterative reconstruction minimising ||A x - y||^2 (Eq. 8 data term).
  * y_dev: [S][K] measured traces in the plan's y_dtype; x_dev: [N] float32, in:
  * start image x_0, out: result.  n_iter >= 0.  opts may be NULL (defaults). */

@@ -72,6 +72,8 @@ SIGNATURES = {
     "pa_reconstruct_host": (c_int, [_P, c_int, c_int, c_void_p, c_void_p,
                                     ctypes.POINTER(pa_recon_opts), _STREAM]),
     "pa_plan_kernel_times": (c_int, [_P, _DP, ctypes.POINTER(c_int), _DP, ctypes.POINTER(c_int)]),
+    "pa_dc": (c_int, [_P, c_void_p, c_void_p, c_void_p, _STREAM]),
+    "pa_tv": (c_int, [_P, c_void_p, c_double, c_void_p, c_void_p, _STREAM]),
     "pa_adjoint_static": (c_int, [_DP, c_int, ctypes.POINTER(pa_grid), c_double, c_double, c_int,
                                   ctypes.POINTER(pa_plan_opts), c_void_p, c_void_p, _STREAM]),
     "pa_status_string": (ctypes.c_char_p, [c_int]),

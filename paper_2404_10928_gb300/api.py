@@ -126,6 +126,27 @@ class Plan:
                                    _stream_handle(self.device)), "pa_adjoint")
         return out
 
+    def dc(self, x: torch.Tensor, g: torch.Tensor, out: Optional[torch.Tensor] = None):
+        """d/dc <g, A(x; c)> as a float64 scalar tensor on the device."""
+        self._check_tensor(x, self.n_pixels, "x")
+        self._check_tensor(g, self.n_sensors * self.n_samples, "g")
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        check(self._lib.pa_dc(self._h, x.data_ptr(), g.data_ptr(), out.data_ptr(),
+                              _stream_handle(self.device)), "pa_dc")
+        return out
+
+    def tv(self, x: torch.Tensor, eps: float = 1e-4, grad: Optional[torch.Tensor] = None):
+        """Smoothed TV of x and its gradient: (float64 scalar tensor, [N] float32)."""
+        self._check_tensor(x, self.n_pixels, "x")
+        if grad is None:
+            grad = torch.empty(self.n_pixels, dtype=torch.float32, device=self.device)
+        self._check_tensor(grad, self.n_pixels, "grad")
+        val = torch.empty((), dtype=torch.float64, device=self.device)
+        check(self._lib.pa_tv(self._h, x.data_ptr(), float(eps), val.data_ptr(), grad.data_ptr(),
+                              _stream_handle(self.device)), "pa_tv")
+        return val, grad
+
     def power_iteration(self, n_iter: int = 50, v0: Optional[torch.Tensor] = None) -> float:
         if v0 is not None:
             self._check_tensor(v0, self.n_pixels, "v0")

@@ -78,7 +78,7 @@ struct GridF {
 enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3 };
 
 // kernel modes
-enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2 };
+enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3 };
 enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
 
 // Cross-CTA FP64 reduction finished inside the producing kernel: every CTA
@@ -91,6 +91,7 @@ struct Reduce {
   double* out_sum;       // nullable
   const double* other;   // gamma for OP_ALPHA / OP_BETA
   double* out2;          // alpha / beta / 1/sqrt(sum)
+  double post_scale;     // out_sum receives sum * post_scale (0 means 1)
 };
 
 struct AdjParams {
@@ -102,6 +103,7 @@ struct AdjParams {
   int mode;
   int nonneg;
   float* out;             // [N] image (ADJ_STORE / ADJ_NORM) or x updated in place
+  const float* xin;       // [N] image weighting the slopes (ADJ_DC)
   const double* omega;    // device scalar (ADJ_LANDWEBER)
   Reduce red;             // ||out||^2 (ADJ_NORM)
   int* err;
@@ -179,6 +181,9 @@ cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
+cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
+                      const Reduce& red, cudaStream_t st);
+int tv_blocks(int64_t n);
 
 }  // namespace pa
 

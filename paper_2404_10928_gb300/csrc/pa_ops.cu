@@ -123,7 +123,7 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part,
   for (int i = threadIdx.x; i < nblk; i += 32 * NW) v += __ldcg(R.partials + i);
   const double t = block_sum<NW>(v, s_red);
   if (threadIdx.x == 0) {
-    if (R.out_sum) *R.out_sum = t;
+    if (R.out_sum) *R.out_sum = R.post_scale != 0.0 ? t * R.post_scale : t;
     switch (R.op) {
       case OP_ALPHA:  // alpha = gamma / ||q||^2
         *R.out2 = t > 0.0 ? *R.other / t : 0.0;
@@ -359,7 +359,7 @@ int adjoint_smem_bytes(int L) {
          2 * kAdjStages * (int)sizeof(uint64_t);
 }
 
-template <int DIM>
+template <int DIM, bool DC>
 __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -475,7 +475,10 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
             time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
                                       idx);
             const float2 v = win[idx];
-            acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
+            if (DC)
+              acc[m] += v.y;  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
+            else
+              acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
           }
         } else {
 #pragma unroll
@@ -485,7 +488,10 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
             time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
                                        idx);
             const float2 v = win[idx];
-            acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
+            if (DC)
+              acc[m] += v.y;  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
+            else
+              acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
           }
         }
       }
@@ -519,7 +525,9 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
     if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
       const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
       const float gval = P.amp * v;
-      if (P.mode == ADJ_LANDWEBER) {
+      if (DC) {
+        part += (double)P.xin[i] * (double)v;
+      } else if (P.mode == ADJ_LANDWEBER) {
         float xv = fmaf((float)(*P.omega), gval, P.out[i]);
         if (P.nonneg) xv = fmaxf(xv, 0.0f);
         P.out[i] = xv;
@@ -529,7 +537,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
       }
     }
   }
-  if (P.mode == ADJ_NORM) {
+  if (P.mode == ADJ_NORM || DC) {
     const double t = block_sum<kAdjWarps + 1>(part, s_red);
     reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
   }
@@ -552,10 +560,13 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
+  const bool dc = p.mode == ADJ_DC;
   if (dim == 2)
-    e = cudaLaunchKernelEx(&cfg, k_adjoint<2>, p);
+    e = dc ? cudaLaunchKernelEx(&cfg, k_adjoint<2, true>, p)
+           : cudaLaunchKernelEx(&cfg, k_adjoint<2, false>, p);
   else
-    e = cudaLaunchKernelEx(&cfg, k_adjoint<3>, p);
+    e = dc ? cudaLaunchKernelEx(&cfg, k_adjoint<3, true>, p)
+           : cudaLaunchKernelEx(&cfg, k_adjoint<3, false>, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -769,10 +780,16 @@ cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
 // plan is created, outside any stream capture).
 cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_adjoint<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_adj)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_adjoint<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_adj)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_adjoint<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_adj)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_adjoint<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_adj)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_fwd_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -884,6 +901,79 @@ cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
 }
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st) {
   k_norm<<<nblk, kVecThreads, 0, st>>>(v, n, red);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Smoothed isotropic total variation (the TV term of Eq. 8 with Psi' = I):
+//   TV(x) = sum_i sqrt(|grad_f x|_i^2 + eps^2),  forward differences, zero past
+// the last index (Neumann).  One thread per pixel writes the gradient
+//   dTV/dx_i = -sum_a a_a(i) + sum_a a_a(i - e_a),  a_a = (forward diff along a)/m,
+// recomputing its neighbours' terms (no inter-thread exchange); the value is
+// reduced in FP64 inside the kernel.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void tv_terms(const float* __restrict__ x, int i, int j, int l, int nx,
+                                         int ny, int nz, float eps2, float& ax, float& ay,
+                                         float& az, float& m) {
+  const int64_t o = ((int64_t)l * ny + j) * nx + i;
+  const float c = x[o];
+  const float gx = (i + 1 < nx) ? x[o + 1] - c : 0.0f;
+  const float gy = (j + 1 < ny) ? x[o + nx] - c : 0.0f;
+  const float gz = (DIM == 3 && l + 1 < nz) ? x[o + (int64_t)nx * ny] - c : 0.0f;
+  m = sqrtf(fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, eps2))));
+  const float inv = 1.0f / m;
+  ax = gx * inv;
+  ay = gy * inv;
+  az = gz * inv;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kVecThreads) k_tv(const float* __restrict__ x, int nx, int ny,
+                                                    int nz, float eps, float* __restrict__ grad,
+                                                    const Reduce red) {
+  __shared__ double s_red[kVecThreads / 32];
+  const float eps2 = eps * eps;
+  const int64_t n = (int64_t)nx * ny * nz;
+  double part = 0.0;
+  for (int64_t o = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; o < n;
+       o += (int64_t)gridDim.x * kVecThreads) {
+    const int i = (int)(o % nx), j = (int)((o / nx) % ny), l = (int)(o / ((int64_t)nx * ny));
+    float ax, ay, az, m;
+    tv_terms<DIM>(x, i, j, l, nx, ny, nz, eps2, ax, ay, az, m);
+    part += (double)m;
+    float g = -(ax + ay + az);
+    float bx, by, bz, mm;
+    if (i > 0) {
+      tv_terms<DIM>(x, i - 1, j, l, nx, ny, nz, eps2, bx, by, bz, mm);
+      g += bx;
+    }
+    if (j > 0) {
+      tv_terms<DIM>(x, i, j - 1, l, nx, ny, nz, eps2, bx, by, bz, mm);
+      g += by;
+    }
+    if (DIM == 3 && l > 0) {
+      tv_terms<DIM>(x, i, j, l - 1, nx, ny, nz, eps2, bx, by, bz, mm);
+      g += bz;
+    }
+    grad[o] = g;
+  }
+  const double t = block_sum<kVecThreads / 32>(part, s_red);
+  reduce_across_ctas<kVecThreads / 32>(red, t, blockIdx.x, gridDim.x, s_red);
+}
+
+int tv_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecThreads - 1) / kVecThreads, 152 * 8));
+}
+
+cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
+                      const Reduce& red, cudaStream_t st) {
+  const int nb = tv_blocks((int64_t)nx * ny * nz);
+  if (dim == 2)
+    k_tv<2><<<nb, kVecThreads, 0, st>>>(x, nx, ny, nz, eps, grad, red);
+  else
+    k_tv<3><<<nb, kVecThreads, 0, st>>>(x, nx, ny, nz, eps, grad, red);
   return cudaGetLastError();
 }
 

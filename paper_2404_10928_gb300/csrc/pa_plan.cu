@@ -525,6 +525,7 @@ Reduce make_reduce(const pa_plan* p, int op, double* out_sum, const double* othe
   r.out_sum = out_sum;
   r.other = other;
   r.out2 = out2;
+  r.post_scale = 0.0;
   return r;
 }
 
@@ -553,6 +554,36 @@ pa_status pa_adjoint(pa_plan* plan, const float* p_dev, float* x_dev, pa_stream 
   PA_CUDA(launch_pack(p_dev, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad, st));
   AdjParams a = adjoint_params(plan, x_dev, ADJ_STORE, nullptr, 0);
   PA_CUDA(launch_adjoint(plan->dim, a, plan->cluster, plan->ntiles, st));
+  return PA_OK;
+}
+
+pa_status pa_dc(pa_plan* plan, const float* x_dev, const float* g_dev, double* dc_dev,
+                pa_stream stream) {
+  if (!plan || !x_dev || !g_dev || !dc_dev) {
+    set_error("pa_dc: NULL argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  PA_CUDA(launch_pack(g_dev, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad, st));
+  AdjParams a = adjoint_params(plan, nullptr, ADJ_DC, nullptr, 0);
+  a.xin = x_dev;
+  a.red = make_reduce(plan, OP_SUM, dc_dev, nullptr, nullptr);
+  a.red.post_scale = -plan->amp * plan->fs / (plan->c * plan->c);  // d u / d c = -d fs / c^2
+  PA_CUDA(launch_adjoint(plan->dim, a, plan->cluster, plan->ntiles, st));
+  return PA_OK;
+}
+
+pa_status pa_tv(pa_plan* plan, const float* x_dev, double eps, double* tv_dev, float* grad_dev,
+                pa_stream stream) {
+  if (!plan || !x_dev || !tv_dev || !grad_dev || !(eps > 0.0) || !std::isfinite(eps)) {
+    set_error("pa_tv: NULL argument or eps <= 0");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(plan->device);
+  PA_CUDA(launch_tv(plan->dim, x_dev, plan->grid.nx, plan->grid.ny, plan->grid.nz, (float)eps,
+                    grad_dev, make_reduce(plan, OP_SUM, tv_dev, nullptr, nullptr),
+                    (cudaStream_t)stream));
   return PA_OK;
 }
 
