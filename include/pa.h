@@ -48,6 +48,7 @@ extern "C" {
 #define PA_VERSION 1
 
 typedef struct pa_plan pa_plan;
+typedef struct pa_batch pa_batch;
 typedef struct CUstream_st *pa_stream; /* == cudaStream_t */
 
 typedef enum {
@@ -74,15 +75,24 @@ typedef struct {
   double origin[3];
 } pa_grid;
 
-/* Optional plan settings.  t0: time of sample 0 in seconds (default 0; t0 = 1/fs
- * reproduces the 1-based t = s*dt of Eq. 6).  amp_scale: global amplitude of the
- * model (default 1; 1/(2*pi*c) gives Eq. 6's prefactor).  y_dtype: storage type
- * of the measured traces y passed to pa_reconstruct (PA_F32 or PA_F16; the
- * arithmetic stays FP32). */
+/* Optional plan settings (zero-initialise, then set what you need).
+ *   t0          time of sample 0 in seconds (default 0; t0 = 1/fs reproduces the
+ *               1-based t = s*dt of Eq. 6).
+ *   amp_scale   global amplitude of the model (0 means 1; 1/(2*pi*c) gives
+ *               Eq. 6's prefactor).
+ *   y_dtype     storage type of the measured traces y passed to pa_reconstruct
+ *               (PA_F32 or PA_F16; the arithmetic stays FP32).
+ *   adj_cluster CTAs that split one pixel tile's sensors in the adjoint (1, 2, 4
+ *               or 8; 0 = chosen from the grid size).  Results are identical up
+ *               to the order of the final per-pixel sum.
+ *   fwd_sensors_per_cta  sensors per forward-gather work item (1..256; 0 = 32).
+ * The last two are the tile shapes an autotuner may pick. */
 typedef struct {
   double t0;
   double amp_scale;
   int y_dtype;
+  int adj_cluster;
+  int fwd_sensors_per_cta;
 } pa_plan_opts;
 
 /* Reconstruction settings (fill with pa_recon_opts_default first).
@@ -217,6 +227,27 @@ pa_status pa_plan_kernel_times(pa_plan *plan, double *fwd_ms, int *n_fwd, double
 pa_status pa_adjoint_static(const double *sensors_xyz, int n_sensors, const pa_grid *grid,
                             double c, double fs, int n_samples, const pa_plan_opts *opts,
                             const float *p_dev, float *x_dev, pa_stream stream);
+
+/* Batched projected Landweber over many frames of uneven size (grid, sensors,
+ * samples may all differ; a hemodynamic time series, say), one plan per frame.
+ * pa_batch_create groups existing plans (same device and dimension); the plans'
+ * workspaces are used by the batch, so they must not run other work meanwhile.
+ * pa_batch_landweber runs n_iter steps x_f <- max(0, x_f + omega_f A_f^T(y_f -
+ * A_f x_f)) (projection only if nonneg) for every frame f in ONE persistent
+ * cooperative kernel launch (work items of all frames share per-phase queues;
+ * phases are separated by grid barriers whose waits are bounded), captured as
+ * a CUDA graph and replayed while (y_dev, x_dev, omega, n_iter) are unchanged.
+ * y_dev[f]: [S_f][K_f] traces in frame f's y_dtype; x_dev[f]: [N_f] float32, in:
+ * x_0, out: result; omega[f] > 0 (host).  residual_history_host: NULL or
+ * n_frames*(n_iter+1) doubles (frame-major) receiving ||y_f - A_f x_{f,n}||^2;
+ * when given the call waits for the stream and reports PA_ERR_TIMEOUT if a
+ * device wait gave up.  The arithmetic of every frame is that of pa_reconstruct
+ * with a plan whose adj_cluster is 1. */
+pa_status pa_batch_create(pa_batch **out, pa_plan *const *plans, int n_frames);
+pa_status pa_batch_destroy(pa_batch *batch);
+pa_status pa_batch_landweber(pa_batch *batch, int n_iter, const void *const *y_dev,
+                             float *const *x_dev, const double *omega, int nonneg,
+                             double *residual_history_host, pa_stream stream);
 
 const char *pa_status_string(pa_status status);
 const char *pa_last_error(void);

@@ -36,7 +36,8 @@ class pa_grid(ctypes.Structure):
 
 
 class pa_plan_opts(ctypes.Structure):
-    _fields_ = [("t0", c_double), ("amp_scale", c_double), ("y_dtype", c_int)]
+    _fields_ = [("t0", c_double), ("amp_scale", c_double), ("y_dtype", c_int),
+                ("adj_cluster", c_int), ("fwd_sensors_per_cta", c_int)]
 
 
 class pa_recon_opts(ctypes.Structure):
@@ -73,6 +74,10 @@ SIGNATURES = {
                                     ctypes.POINTER(pa_recon_opts), _STREAM]),
     "pa_plan_kernel_times": (c_int, [_P, _DP, ctypes.POINTER(c_int), _DP, ctypes.POINTER(c_int)]),
     "pa_dc": (c_int, [_P, c_void_p, c_void_p, c_void_p, _STREAM]),
+    "pa_batch_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int]),
+    "pa_batch_destroy": (c_int, [c_void_p]),
+    "pa_batch_landweber": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p),
+                                   ctypes.POINTER(c_void_p), _DP, c_int, _DP, _STREAM]),
     "pa_tv": (c_int, [_P, c_void_p, c_double, c_void_p, c_void_p, _STREAM]),
     "pa_adjoint_static": (c_int, [_DP, c_int, ctypes.POINTER(pa_grid), c_double, c_double, c_int,
                                   ctypes.POINTER(pa_plan_opts), c_void_p, c_void_p, _STREAM]),

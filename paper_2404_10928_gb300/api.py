@@ -27,7 +27,8 @@ class Plan:
 
     def __init__(self, sensors, shape, spacing, origin, c: float, fs: float, n_samples: int,
                  t0: float = 0.0, amp_scale: float = 1.0, y_dtype: str = "f32",
-                 dim: Optional[int] = None, device=None):
+                 dim: Optional[int] = None, device=None, adj_cluster: int = 0,
+                 fwd_sensors_per_cta: int = 0):
         self._lib = _lib.load()
         sensors = np.ascontiguousarray(sensors, dtype=np.float64)
         dim = int(dim if dim is not None else sensors.shape[1])
@@ -45,7 +46,8 @@ class Plan:
         self._sensors = sensors  # keep alive for the call
         grid = _lib.pa_grid(dim, shape[0], shape[1], shape[2], spacing[0], spacing[1], spacing[2],
                             (ctypes.c_double * 3)(*origin))
-        opts = _lib.pa_plan_opts(self.t0, self.amp_scale, PA_F16 if y_dtype == "f16" else PA_F32)
+        opts = _lib.pa_plan_opts(self.t0, self.amp_scale, PA_F16 if y_dtype == "f16" else PA_F32,
+                                 int(adj_cluster), int(fwd_sensors_per_cta))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = self._lib.pa_plan_create(ctypes.byref(handle),
@@ -223,3 +225,53 @@ class Plan:
                                              ctypes.byref(am), ctypes.byref(an)),
               "pa_plan_kernel_times")
         return {"fwd_ms": fm.value, "n_fwd": fn.value, "adj_ms": am.value, "n_adj": an.value}
+
+
+class Batch:
+    """Several plans (frames of uneven size) reconstructed together by one
+    persistent launch per call (see ``pa_batch_landweber``)."""
+
+    def __init__(self, plans):
+        self._lib = _lib.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(self._lib.pa_batch_create(ctypes.byref(h), arr, len(self.plans)), "pa_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def landweber(self, ys, xs, omegas, n_iter: int, nonneg: bool = True, history: bool = False):
+        """Run n_iter projected Landweber steps on every frame in place (xs are the
+        start images and receive the results)."""
+        n = len(self.plans)
+        if not (len(ys) == len(xs) == len(omegas) == n):
+            raise ValueError("need one y, x and omega per frame")
+        for p, y, x in zip(self.plans, ys, xs):
+            ydt = torch.float16 if p.y_dtype == "f16" else torch.float32
+            p._check_tensor(y, p.n_sensors * p.n_samples, "y", ydt)
+            p._check_tensor(x, p.n_pixels, "x")
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        om = (ctypes.c_double * n)(*[float(o) for o in omegas])
+        hist = np.zeros((n, n_iter + 1)) if history else None
+        hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None
+        check(self._lib.pa_batch_landweber(self._h, int(n_iter), yp, xp, om, int(bool(nonneg)), hp,
+                                           _stream_handle(self.plans[0].device)),
+              "pa_batch_landweber")
+        return hist

@@ -117,6 +117,7 @@ struct FwdParams {
   const int2* sorted;     // [S][ntiles]: (tile, klo) of the pairs that are not skipped, by klo
   const int* upper;       // [S][K + L]: at k + L, how many sorted tiles have klo <= k
   int S, K, L, ntiles;
+  int spc;                // sensors per forward tile work item
   GridF g;
   float kappa, inv_kappa, half_inv_kappa, amp, half_hmin;
   int mode;
@@ -131,6 +132,15 @@ struct FwdParams {
   float* p_new;
   const double* beta;
   int* err;
+};
+
+// One frame of a batched reconstruction (see k_batch_landweber).
+struct BatchFrame {
+  FwdParams f;        // FWD_RESID: r = y - A x, ||r||^2 reduced in the kernel
+  AdjParams a;        // ADJ_LANDWEBER: x = max(0, x + omega A^T r)
+  int fwd_chunks;     // sensor chunks per tile in the forward gather
+  int n_kblk;         // sample blocks per sensor in the combine
+  double* hist;       // [n_iter + 1] ||r_n||^2
 };
 
 // tile shapes
@@ -150,7 +160,7 @@ constexpr int kAdjStages = 4;
 
 // forward kernel shape
 constexpr int kFwdThreads = 256;             // 4 pixels of the tile per thread
-constexpr int kFwdSPC = 32;                  // sensors per tile CTA
+constexpr int kFwdSPC = 32;                  // default sensors per tile work item
 constexpr int kFwdSB = 8;                    // sensors per accumulation stage
 constexpr int kCombThreads = 256;            // samples per combine CTA
 
@@ -166,7 +176,7 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
 int adjoint_smem_bytes(int L);
 cudaError_t configure_kernels(int smem_adj, int smem_fwd);
-int forward_smem_bytes(int L);
+int forward_smem_bytes(int L, int spc);
 int forward_combine_blocks(int S, int K);
 pa_status validate_grid(const pa_grid* g);
 
@@ -184,6 +194,10 @@ cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, 
 cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
                       const Reduce& red, cudaStream_t st);
 int tv_blocks(int64_t n);
+cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm);
+cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_frames, const int* pre,
+                                   int n_iter, unsigned* state, int* err, int grid, size_t smem,
+                                   cudaStream_t st);
 
 }  // namespace pa
 
@@ -206,6 +220,7 @@ struct pa_plan {
   int pad = 0;      // zero samples on each side of a packed trace
   int Kp = 0;       // packed row length (even)
   int cluster = 1;  // adjoint CTAs per tile
+  int fwd_spc = 32; // sensors per forward tile work item
 
   // device memory owned by the plan
   double* d_sensors = nullptr;

@@ -92,8 +92,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // Deterministic FP64 block sum: xor-tree within warps, warps in index order.
-template <int NW>
-__device__ __forceinline__ double block_sum(double v, double* s_red) {
+// nw = warps in the block; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* s_red, int nw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -101,16 +101,22 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x == 0)
-    for (int w = 0; w < NW; ++w) t += s_red[w];
-  return t;  // valid in thread 0
+    for (int w = 0; w < nw; ++w) t += s_red[w];
+  __syncthreads();
+  return t;
+}
+template <int NW>
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  return block_sum(v, s_red, NW);
 }
 
 // Finishes a Reduce inside the producing kernel (see Reduce).  `part` is the
 // CTA's partial, valid in thread 0; all threads of the CTA must call this.
-template <int NW>
+// bid / nblk: this CTA's slot and the number of CTAs (work items) reducing.
 __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part, int bid, int nblk,
                                                    double* s_red) {
   __shared__ int s_last;
+  const int nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     R.partials[bid] = part;
     __threadfence();
@@ -120,8 +126,8 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part,
   if (!s_last) return;
   __threadfence();
   double v = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += 32 * NW) v += __ldcg(R.partials + i);
-  const double t = block_sum<NW>(v, s_red);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(R.partials + i);
+  const double t = block_sum(v, s_red, nw);
   if (threadIdx.x == 0) {
     if (R.out_sum) *R.out_sum = R.post_scale != 0.0 ? t * R.post_scale : t;
     switch (R.op) {
@@ -139,6 +145,12 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part,
     }
     *R.counter = 0u;
   }
+  __syncthreads();
+}
+template <int NW>
+__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part, int bid, int nblk,
+                                                   double* s_red) {
+  reduce_across_ctas(R, part, bid, nblk, s_red);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,10 +371,12 @@ int adjoint_smem_bytes(int L) {
          2 * kAdjStages * (int)sizeof(uint64_t);
 }
 
+// Accumulates, for every pixel of `tile`, the sum over sensors [s_begin, s_end)
+// into s_acc (shared, kTilePixels floats; returned).  Block of kAdjThreads
+// threads: warp kAdjWarps produces, warps 0..kAdjWarps-1 compute.
 template <int DIM, bool DC>
-__global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
-  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, int s_begin,
+                                                 int s_end, unsigned char* smem) {
   const int L = P.L;
   float2* s_trace = reinterpret_cast<float2*>(smem);
   TileRef* s_ref = reinterpret_cast<TileRef*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
@@ -371,15 +385,8 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   uint64_t* s_empty = s_full + kAdjStages;
   __shared__ int s_abort;
   __shared__ int s_issued;
-  __shared__ double s_red[kAdjWarps + 1];
 
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const int C = (int)cluster.num_blocks();
-  const int tile = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int s_begin = rank * P.sensors_per_rank;
-  const int s_end = min(P.S, s_begin + P.sensors_per_rank);
   const int n_stages = s_end > s_begin ? (s_end - s_begin + kAdjSB - 1) / kAdjSB : 0;
 
   if (tid == 0) {
@@ -510,6 +517,24 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
       mbar_wait_bounded(&s_full[jj % kAdjStages], (jj / kAdjStages) & 1);
   }
 
+  __syncthreads();
+  return s_acc;
+}
+
+template <int DIM, bool DC>
+__global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double s_red[kAdjWarps + 1];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int C = (int)cluster.num_blocks();
+  const int tile = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int s_begin = rank * P.sensors_per_rank;
+  const int s_end = min(P.S, s_begin + P.sensors_per_rank);
+  float* s_acc = adj_accumulate<DIM, DC>(P, tile, s_begin, s_end, smem);
+
   cluster.sync();
   // --------------- cluster reduction in rank order + epilogue ---------------
   const int per = (kTilePixels + C - 1) / C;
@@ -585,25 +610,29 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
 // k, in a fixed order (by window start), plus the residual / norm epilogue.
 // ---------------------------------------------------------------------------
-int forward_smem_bytes(int L) {
-  return kFwdSPC * (int)sizeof(TileRef) + 2 * kFwdSB * L * (int)sizeof(int);
+int forward_smem_bytes(int L, int spc) {
+  return spc * (int)sizeof(TileRef) + 2 * kFwdSB * L * (int)sizeof(int);
 }
 
 constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
 
+// One (tile, sensor chunk) work item of the forward gather.  The first
+// kFwdThreads threads own four pixels each; any further threads of the block
+// only help with the copies and barriers.
 template <int DIM>
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
+__device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int chunk,
+                                               unsigned char* smem) {
   constexpr int PPT = kTilePixels / kFwdThreads;
-  extern __shared__ __align__(128) unsigned char smem[];
   TileRef* refs = reinterpret_cast<TileRef*>(smem);
-  int* win = reinterpret_cast<int*>(refs + kFwdSPC);
-  __shared__ float s_max[kFwdThreads / 32];
+  int* win = reinterpret_cast<int*>(refs + P.spc);
+  __shared__ float s_max[32];
 
   const int L = P.L;
-  const int tile = blockIdx.y;
-  const int s0 = blockIdx.x * kFwdSPC;
-  const int ns = min(kFwdSPC, P.S - s0);
+  const int s0 = chunk * P.spc;
+  const int ns = min(P.spc, P.S - s0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = blockDim.x;
+  const bool owner = tid < kFwdThreads;
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
   int nvx, nvy, nvz;
   tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
@@ -617,11 +646,11 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
     int lx, ly, lz;
     pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
     float xv = 0.0f;
-    if (lx < nvx && ly < nvy && lz < nvz) {
+    if (owner && lx < nvx && ly < nvy && lz < nvz) {
       const int64_t i = ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx);
       if (P.s_in) {  // CGLS direction p = s + beta p_old, stored once (sensor chunk 0)
         xv = fmaf((float)(*P.beta), P.p_old[i], P.s_in[i]);
-        if (blockIdx.x == 0) P.p_new[i] = xv;
+        if (chunk == 0) P.p_new[i] = xv;
       } else {
         xv = P.x[i];
       }
@@ -635,15 +664,15 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
   {
     const int4* src = reinterpret_cast<const int4*>(P.table + (int64_t)tile * P.S + s0);
     int4* dst = reinterpret_cast<int4*>(refs);
-    for (int i = tid; i < ns * 2; i += kFwdThreads) dst[i] = src[i];
+    for (int i = tid; i < ns * 2; i += nt) dst[i] = src[i];
   }
-  for (int i = tid; i < 2 * kFwdSB * L; i += kFwdThreads) win[i] = 0;
+  for (int i = tid; i < 2 * kFwdSB * L; i += nt) win[i] = 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if (lane == 0) s_max[warp] = amax;
   const bool finite = __syncthreads_or(nonfinite) == 0;
   float xmax = 0.0f;
-  for (int w = 0; w < kFwdThreads / 32; ++w) xmax = fmaxf(xmax, s_max[w]);
+  for (int w = 0; w < (nt >> 5); ++w) xmax = fmaxf(xmax, s_max[w]);
   // |pixel - sensor| >= d_ref - R for every pixel of the tile
   const float hx = (float)(nvx - 1) * P.g.hdx, hy = (float)(nvy - 1) * P.g.hdy;
   const float hz = (DIM == 3) ? (float)(nvz - 1) * P.g.hdz : 0.0f;
@@ -656,7 +685,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
   for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
     int* wb = win + buf * kFwdSB * L;
     const int nsb = min(kFwdSB, ns - g0);
-    if (xscale > 0.0f) {
+    if (owner && xscale > 0.0f) {
       for (int sb = 0; sb < nsb; ++sb) {
         const TileRef r = refs[g0 + sb];
         if (r.klo == kSkip) continue;
@@ -699,19 +728,27 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
         unscale = xmax / (kFixedScale * fmaxf(refs[g0 + sb].dref - R, P.half_hmin));
       float* dst = P.part + ((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L;
       int* src = wb + sb * L;
-      for (int k = tid; k < L; k += kFwdThreads) {
+      for (int k = tid; k < L; k += nt) {
         if (store) dst[k] = finite ? (float)src[k] * unscale : __int_as_float(0x7fc00000);
         src[k] = 0;  // this buffer is reused two stages later, after the next barrier
       }
     }
   }
+  __syncthreads();  // the block's shared memory is free for the next work item
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  fwd_tile_block<DIM>(P, blockIdx.y, blockIdx.x, smem);
+}
+
+// One (sensor, block of blockDim samples) work item of the combine; nkblk =
+// sample blocks per sensor (for the in-kernel reduction's slot numbering).
 template <int MODE>
-__global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P) {
-  __shared__ double s_red[kCombThreads / 32];
-  const int s = blockIdx.y;
-  const int k = blockIdx.x * kCombThreads + threadIdx.x;
+__device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kblk, int nkblk) {
+  __shared__ double s_red[32];
+  const int k = kblk * blockDim.x + threadIdx.x;
   double part = 0.0;
   if (k < P.K) {
     const int* up = P.upper + (int64_t)s * (P.K + P.L);
@@ -749,17 +786,21 @@ __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P)
     }
   }
   if (MODE != FWD_STORE) {
-    const double t = block_sum<kCombThreads / 32>(part, s_red);
-    reduce_across_ctas<kCombThreads / 32>(P.red, t, s * gridDim.x + blockIdx.x,
-                                          gridDim.x * gridDim.y, s_red);
+    const double t = block_sum(part, s_red, blockDim.x >> 5);
+    reduce_across_ctas(P.red, t, s * nkblk + kblk, P.S * nkblk, s_red);
   }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P) {
+  combine_block<MODE>(P, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 int forward_combine_blocks(int S, int K) { return S * ((K + kCombThreads - 1) / kCombThreads); }
 
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
-  const int smem = forward_smem_bytes(p.L);
-  dim3 grid1((p.S + kFwdSPC - 1) / kFwdSPC, p.ntiles, 1);
+  const int smem = forward_smem_bytes(p.L, p.spc);
+  dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, 1);
   if (dim == 2)
     k_fwd_tile<2><<<grid1, kFwdThreads, smem, st>>>(p);
   else
@@ -975,6 +1016,164 @@ cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps
   else
     k_tv<3><<<nb, kVecThreads, 0, st>>>(x, nx, ny, nz, eps, grad, red);
   return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched projected Landweber over frames of uneven size, in one persistent
+// cooperative launch (co-residency of all CTAs is guaranteed by the launch).
+// Per iteration: every frame's forward tile items, then its combine items
+// (r = y - A x and ||r||^2), then the packing of r, then its adjoint items with
+// the Landweber update.  Items come from one global queue per phase, so CTAs
+// balance the ragged work among themselves; every item's arithmetic is the
+// same as in the single-frame kernels.  Phases are separated by a grid barrier
+// whose wait is bounded: if it gives up, an error flag is set and the CTA goes
+// on (the result is then invalid, but the launch ends).
+// state: [0] arrivals, [1] generation, [2] forward queue, [3] combine queue,
+// [4] adjoint queue.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_barrier(unsigned* st, unsigned nblocks, int* err,
+                                             unsigned* queue_to_reset) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = st + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(st, 1u) == nblocks - 1u) {
+      st[0] = 0u;
+      if (queue_to_reset) *queue_to_reset = 0u;
+      __threadfence();
+      atomicAdd(st + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      for (uint32_t it = 1; *gen == g; ++it) {
+        if ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+          atomicOr(err, ERR_WAIT_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int grab_item(unsigned* queue) {
+  __shared__ int s_item;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+  __syncthreads();
+  return s_item;
+}
+
+// frame of global item gi: the last f with pre[f] <= gi
+__device__ __forceinline__ int frame_of(const int* pre, int nf, int gi) {
+  int lo = 0, hi = nf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= gi) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int DIM>
+__device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile,
+                                                    unsigned char* smem) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  float* s_acc = adj_accumulate<DIM, false>(P, tile, 0, P.S, smem);
+  const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
+  const float om = (float)(*P.omega);
+  for (int p = threadIdx.x; p < kTilePixels; p += blockDim.x) {
+    int lx, ly, lz;
+    pixel_local<DIM>(p, lx, ly, lz);
+    const int gx = tx * TX + lx, gy = ty * TY + ly, gz = tz * TZ + lz;
+    if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
+      const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
+      float xv = fmaf(om, P.amp * s_acc[p], P.out[i]);
+      if (P.nonneg) xv = fmaxf(xv, 0.0f);
+      P.out[i] = xv;
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kAdjThreads) k_batch_landweber(
+    const BatchFrame* __restrict__ frames, int nf, const int* __restrict__ pre, int n_iter,
+    unsigned* state, int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const unsigned nb = gridDim.x;
+  const int* pf = pre;                 // forward items
+  const int* pc = pre + (nf + 1);      // combine items
+  const int* pa = pre + 2 * (nf + 1);  // adjoint items
+  for (int it = 0; it <= n_iter; ++it) {
+    for (int gi = grab_item(state + 2); gi < pf[nf]; gi = grab_item(state + 2)) {
+      const int f = frame_of(pf, nf, gi);
+      const int li = gi - pf[f];
+      const int chunks = frames[f].fwd_chunks;
+      fwd_tile_block<DIM>(frames[f].f, li / chunks, li % chunks, smem);
+    }
+    grid_barrier(state, nb, err, state + 2);
+    for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
+      const int f = frame_of(pc, nf, gi);
+      const int li = gi - pc[f];
+      FwdParams P = frames[f].f;
+      P.red.out_sum = frames[f].hist + it;
+      const int nk = frames[f].n_kblk;
+      combine_block<FWD_RESID>(P, li / nk, li % nk, nk);
+    }
+    grid_barrier(state, nb, err, state + 3);
+    if (it == n_iter) break;
+    for (int f = 0; f < nf; ++f) {  // pack r of every frame (grid-stride)
+      const FwdParams& F = frames[f].f;
+      const AdjParams& A = frames[f].a;
+      const int64_t row = F.K + 1, total = (int64_t)F.S * row;
+      for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+           idx += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / row);
+        const int k = (int)(idx % row) - 1;
+        const float* rs = F.out + (int64_t)s * F.K;
+        const float a = (k >= 0) ? rs[k] : 0.0f;
+        const float b = (k + 1 < F.K) ? rs[k + 1] : 0.0f;
+        const_cast<float2*>(A.packed)[(int64_t)s * A.Kp + A.pad + k] =
+            make_float2(0.5f * (a + b), b - a);
+      }
+    }
+    grid_barrier(state, nb, err, nullptr);
+    for (int gi = grab_item(state + 4); gi < pa[nf]; gi = grab_item(state + 4)) {
+      const int f = frame_of(pa, nf, gi);
+      adj_landweber_block<DIM>(frames[f].a, gi - pa[f], smem);
+    }
+    grid_barrier(state, nb, err, state + 4);
+  }
+}
+
+cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm) {
+  cudaError_t e;
+  if (dim == 2) {
+    e = cudaFuncSetAttribute(k_batch_landweber<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_landweber<2>,
+                                                         kAdjThreads, smem);
+  }
+  e = cudaFuncSetAttribute(k_batch_landweber<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_landweber<3>,
+                                                       kAdjThreads, smem);
+}
+
+cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_frames, const int* pre,
+                                   int n_iter, unsigned* state, int* err, int grid, size_t smem,
+                                   cudaStream_t st) {
+  void* args[] = {(void*)&frames, (void*)&n_frames, (void*)&pre, (void*)&n_iter, (void*)&state,
+                  (void*)&err};
+  if (dim == 2)
+    return cudaLaunchCooperativeKernel((const void*)k_batch_landweber<2>, dim3(grid),
+                                       dim3(kAdjThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel((const void*)k_batch_landweber<3>, dim3(grid),
+                                     dim3(kAdjThreads), args, smem, st);
 }
 
 }  // namespace pa

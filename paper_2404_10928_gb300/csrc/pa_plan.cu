@@ -240,8 +240,15 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     return PA_ERR_UNSUPPORTED;
   }
   const double t0 = opts ? opts->t0 : 0.0;
-  const double amp = opts ? opts->amp_scale : 1.0;
+  const double amp = (opts && opts->amp_scale != 0.0) ? opts->amp_scale : 1.0;
   const int ydt = opts ? opts->y_dtype : PA_F32;
+  if (opts && (opts->adj_cluster < 0 || opts->adj_cluster > 8 ||
+               (opts->adj_cluster & (opts->adj_cluster - 1)) != 0 ||
+               opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256)) {
+    set_error("invalid plan options: adj_cluster must be 0, 1, 2, 4 or 8 and "
+              "fwd_sensors_per_cta in [0, 256]");
+    return PA_ERR_INVALID_ARG;
+  }
   if (!std::isfinite(t0) || !std::isfinite(amp) || (ydt != PA_F32 && ydt != PA_F16)) {
     set_error("invalid plan options");
     return PA_ERR_INVALID_ARG;
@@ -317,9 +324,11 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     int C = 1;
     while (C < 8 && (int64_t)p->ntiles * C < 2LL * sms && 2 * C <= p->S) C *= 2;
     p->cluster = C;
+    if (opts && opts->adj_cluster > 0) p->cluster = std::min(opts->adj_cluster, p->S);
+    if (opts && opts->fwd_sensors_per_cta > 0) p->fwd_spc = opts->fwd_sensors_per_cta;
   }
   const size_t smem_adj = (size_t)adjoint_smem_bytes(p->L);
-  if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->L) > 200 * 1024) {
+  if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->L, p->fwd_spc) > 200 * 1024) {
     set_error("geometry needs too much shared memory (window %d samples, %d tiles)", p->L,
               p->ntiles);
     delete p;
@@ -332,7 +341,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     static int configured_adj[64] = {0}, configured_fwd[64] = {0};
     const int dv = p->device & 63;
     const int want_adj = std::max<int>((int)smem_adj, configured_adj[dv]);
-    const int want_fwd = std::max<int>(forward_smem_bytes(p->L), configured_fwd[dv]);
+    const int want_fwd = std::max<int>(forward_smem_bytes(p->L, p->fwd_spc), configured_fwd[dv]);
     cudaError_t e = configure_kernels(want_adj, want_fwd);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
@@ -454,7 +463,7 @@ pa_status pa_plan_query(const pa_plan* plan, pa_plan_info* info) {
   info->tile[2] = plan->dim == 2 ? Tile<2>::Z : Tile<3>::Z;
   info->window = plan->L;
   info->cluster = plan->cluster;
-  info->fwd_sensors = kFwdSPC;
+  info->fwd_sensors = plan->fwd_spc;
   info->device_bytes = plan->bytes;
   return PA_OK;
 }
@@ -477,6 +486,7 @@ FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode,
   f.K = p->K;
   f.L = p->L;
   f.ntiles = p->ntiles;
+  f.spc = p->fwd_spc;
   f.g = p->g;
   f.kappa = (float)(p->fs / p->c);
   f.inv_kappa = (float)(p->c / p->fs);

@@ -67,7 +67,7 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
     return PA_ERR_INVALID_ARG;
   }
   const double t0 = opts ? opts->t0 : 0.0;
-  const double amp = opts ? opts->amp_scale : 1.0;
+  const double amp = (opts && opts->amp_scale != 0.0) ? opts->amp_scale : 1.0;
   if (!std::isfinite(t0) || !std::isfinite(amp)) {
     set_error("pa_adjoint_static: invalid options");
     return PA_ERR_INVALID_ARG;

@@ -48,7 +48,8 @@ def test_struct_layouts_match_header(tmp_path):
 #include "pa.h"
 int main(void) {
   printf("pa_grid %zu %zu %zu\n", sizeof(pa_grid), offsetof(pa_grid, dx), offsetof(pa_grid, origin));
-  printf("pa_plan_opts %zu %zu\n", sizeof(pa_plan_opts), offsetof(pa_plan_opts, y_dtype));
+  printf("pa_plan_opts %zu %zu %zu\n", sizeof(pa_plan_opts), offsetof(pa_plan_opts, y_dtype),
+         offsetof(pa_plan_opts, fwd_sensors_per_cta));
   printf("pa_recon_opts %zu %zu %zu %zu\n", sizeof(pa_recon_opts), offsetof(pa_recon_opts, power_v0_dev),
          offsetof(pa_recon_opts, residual_history_host), offsetof(pa_recon_opts, kernel_timing));
   printf("pa_plan_info %zu %zu %zu\n", sizeof(pa_plan_info), offsetof(pa_plan_info, tile),
@@ -63,7 +64,8 @@ int main(void) {
                                     check=True).stdout.splitlines()}
     S = _lib
     assert rows["pa_grid"] == [ctypes.sizeof(S.pa_grid), S.pa_grid.dx.offset, S.pa_grid.origin.offset]
-    assert rows["pa_plan_opts"] == [ctypes.sizeof(S.pa_plan_opts), S.pa_plan_opts.y_dtype.offset]
+    assert rows["pa_plan_opts"] == [ctypes.sizeof(S.pa_plan_opts), S.pa_plan_opts.y_dtype.offset,
+                                    S.pa_plan_opts.fwd_sensors_per_cta.offset]
     assert rows["pa_recon_opts"] == [ctypes.sizeof(S.pa_recon_opts), S.pa_recon_opts.power_v0_dev.offset,
                                      S.pa_recon_opts.residual_history_host.offset,
                                      S.pa_recon_opts.kernel_timing.offset]
@@ -99,7 +101,7 @@ def test_argument_validation_without_gpu(lib):
     near = np.array([[0.5e-4 + 0.2e-4, 0.5e-4]])
     assert _create(lib, near, _grid())[0] == _lib.PA_ERR_GEOMETRY
     assert b"half the pixel" in lib.pa_last_error()
-    bad_opts = _lib.pa_plan_opts(0.0, 1.0, 7)
+    bad_opts = _lib.pa_plan_opts(0.0, 1.0, 7, 0, 0)
     assert _create(lib, far, _grid(), opts=bad_opts)[0] == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_plan_destroy(None) == _lib.PA_OK
     assert lib.pa_forward(None, None, None, None) == _lib.PA_ERR_INVALID_ARG

@@ -47,7 +47,7 @@ def test_static_adjoint_matches_plan_adjoint_twice():
             ref = plan.adjoint(p).cpu().numpy()
         sensors = np.ascontiguousarray(prob.sensors, dtype=np.float64)
         grid = _grid(prob)
-        opts = _lib.pa_plan_opts(prob.t0, prob.amp_scale, _lib.PA_F32)
+        opts = _lib.pa_plan_opts(prob.t0, prob.amp_scale, _lib.PA_F32, 0, 0)
         for _ in range(2):
             x = torch.full((prob.n_pixels,), float("nan"), dtype=torch.float32, device="cuda")
             st = lib.pa_adjoint_static(sensors.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
