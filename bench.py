@@ -190,6 +190,109 @@ def read_traffic(kernel: str):
     return None
 
 
+def _events_time(torch, fn, reps: int) -> float:
+    """Median seconds of fn() measured with CUDA events on the current stream."""
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(times)
+
+
+def bench_batched(torch, tuner, n_iter: int = 20, reps: int = 3) -> dict:
+    """Ragged time series: 64 frames (grids 128^2..512^2, 128-512 ring sensors,
+    1024-4096 samples at 40 MHz, FP16 traces), 20 projected Landweber iterations
+    each: one persistent batched launch vs a loop of per-frame reconstructions."""
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Batch, Plan
+    frames = ph.ragged_time_series()
+    plans, ys, xs, omegas = [], [], [], []
+    for prob in frames:
+        t = tuner.best(prob)
+        plan = Plan.from_problem(prob, adj_cluster=1, fwd_sensors_per_cta=t["fwd_sensors_per_cta"])
+        x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
+        ys.append(plan.forward(x_true).to(torch.float16))
+        omegas.append(1.0 / plan.power_iteration(20))
+        xs.append(torch.zeros(prob.n_pixels, dtype=torch.float32, device="cuda"))
+        plans.append(plan)
+    pairs = sum(p.pairs for p in frames) * (2 * n_iter + 1)
+
+    def plain():
+        for plan, y, x, om in zip(plans, ys, xs, omegas):
+            x.zero_()
+            plan.reconstruct(y, "landweber", n_iter, omega=om, out=x)
+
+    batch = Batch(plans)
+
+    def batched():
+        for x in xs:
+            x.zero_()
+        batch.landweber(ys, xs, omegas, n_iter)
+
+    plain()
+    batched()
+    t_plain = _events_time(torch, plain, reps)
+    t_batch = _events_time(torch, batched, reps)
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"workload": f"{len(frames)} ragged frames (grids 128^2..512^2, 128-512 ring sensors, "
+                        f"1024-4096 samples, FP16 y), {n_iter} projected Landweber iterations",
+            "frames_per_s_batched": len(frames) / t_batch,
+            "frames_per_s_plain": len(frames) / t_plain,
+            "speedup": t_plain / t_batch,
+            "pairs_per_s_batched": pairs / t_batch,
+            "launches_batched": 2, "launches_plain": len(frames),
+            "timing": f"median of {reps}, CUDA events"}
+
+
+def bench_differentiable(torch, reps: int = 3) -> dict:
+    """Speed-of-sound calibration workload: batch of 8 vessel frames (256^2,
+    128-sensor ring, 2048 samples); loss ||A(x;c) - p||^2 + 1e-3 TV(x) and its
+    gradients in x and c; and a 10-step unrolled Landweber with per-step
+    checkpointing, differentiated end to end."""
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Plan
+    from paper_2404_10928_gb300.autograd import UnrolledLandweber, data_tv_loss
+    frames = ph.ring_vessels_batch()
+    prob = frames[0]
+    plan = Plan.from_problem(prob, c=1500.0)
+    xs = torch.tensor(np.stack([f.x_true for f in frames]), dtype=torch.float32, device="cuda")
+    plan.set_sound_speed(1540.0)
+    ps = torch.stack([plan.forward(x) for x in xs])
+    plan.set_sound_speed(1500.0)
+    omega = 1.0 / plan.power_iteration(20)
+
+    def loss_grad():
+        x = xs.clone().requires_grad_(True)
+        c = torch.tensor(1500.0, dtype=torch.float64, device="cuda", requires_grad=True)
+        data_tv_loss(plan, x, c, ps, 1e-3).backward()
+
+    net = UnrolledLandweber(plan, 10, omega, checkpointing=True)
+
+    def unrolled():
+        c = torch.tensor(1500.0, dtype=torch.float64, device="cuda", requires_grad=True)
+        x0 = torch.zeros_like(xs, requires_grad=True)
+        (net(x0, ps, c).double() ** 2).sum().backward()
+
+    loss_grad()
+    unrolled()
+    t_lg = _events_time(torch, loss_grad, reps)
+    t_un = _events_time(torch, unrolled, reps)
+    plan.close()
+    apps_lg = len(frames) * 3           # A; backward A^T and d/dc, per frame
+    apps_un = len(frames) * 10 * 8      # per step: A, A^T; recomputed A, A^T; backward A^T, A, 2 d/dc
+    return {"workload": "batch of 8 vessel frames, 256^2, 128-sensor ring, 2048 samples, c=1500",
+            "loss_grad_ms": t_lg * 1e3, "loss_grad_frames_per_s": len(frames) / t_lg,
+            "unrolled10_grad_ms": t_un * 1e3,
+            "operator_applications": {"loss_grad": apps_lg, "unrolled10_grad": apps_un},
+            "timing": f"median of {reps}, CUDA events"}
+
+
 def run_gpu(args):
     import torch
 
@@ -208,7 +311,11 @@ def run_gpu(args):
     prob = ph.ring_vessels(seed=1002)
     # each rank reconstructs its own frame (same geometry, its own noise draw)
     noise = np.random.default_rng(2003 + rank).standard_normal(prob.noise_unit.shape)
-    plan = Plan.from_problem(prob)
+    from paper_2404_10928_gb300.autotune import Autotuner
+    tuner = Autotuner(os.path.join(ROOT, "gpurun_out", f"autotune_rank{rank}.json"))
+    tuned = tuner.best(prob)
+    plan = Plan.from_problem(prob, adj_cluster=tuned["adj_cluster"],
+                             fwd_sensors_per_cta=tuned["fwd_sensors_per_cta"])
     x_true = torch.tensor(prob.x_true, dtype=torch.float32, device=dev)
     clean = plan.forward(x_true).cpu().numpy().astype(np.float64)
     y_host = ph.add_noise(clean, noise, prob.noise_level).astype(np.float32)
@@ -282,6 +389,11 @@ def run_gpu(args):
         e2e_t = float(t.item())
     e2e_value = pairs_all / e2e_t
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra["batched"] = bench_batched(torch, tuner)
+        extra["differentiable"] = bench_differentiable(torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, n_it = oracle_sample(prob, y_host.astype(np.float64))
@@ -328,10 +440,13 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(y_host.nbytes + prob.n_pixels * 4),
                     "d2h_bytes_per_step": int(prob.n_pixels * 4)},
+            "autotuned": {"adj_cluster": tuned["adj_cluster"],
+                          "fwd_sensors_per_cta": tuned["fwd_sensors_per_cta"]},
             "gpu_launches": cgls_launches(N_ITER) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
@@ -346,6 +461,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and differentiable workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

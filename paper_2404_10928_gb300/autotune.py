@@ -1,0 +1,127 @@
+"""Autotuner for the gathers' work decomposition ("tile shapes" at run time).
+
+Two plan options change how the work of A and A^T is cut into CTAs without
+changing what is computed:
+
+* ``adj_cluster``: how many CTAs (a thread-block cluster) split one pixel
+  tile's sensors in the adjoint;
+* ``fwd_sensors_per_cta``: how many sensors one forward tile work item covers.
+
+For a size class (GPU, dimension, and the pixel / sensor / sample counts
+rounded up to powers of two) the tuner builds a plan per candidate, times a
+few forward + adjoint applications with CUDA events and keeps the fastest.
+Results are cached in a JSON file (``PA_TUNE_CACHE``, default
+``~/.cache/pa_gb300/autotune.json``).
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from typing import Callable, Dict, Iterable, Optional, Tuple
+
+ADJ_CLUSTERS = (1, 2, 4, 8)
+FWD_SENSORS = (16, 32, 64)
+
+
+def _pow2(n: int) -> int:
+    p = 1
+    while p < n:
+        p *= 2
+    return p
+
+
+def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int) -> str:
+    return f"{gpu}|{dim}d|N{_pow2(n_pixels)}|S{_pow2(n_sensors)}|K{_pow2(n_samples)}"
+
+
+def candidates(n_sensors: int) -> Iterable[Tuple[int, int]]:
+    for c in ADJ_CLUSTERS:
+        if c > 1 and 2 * c > n_sensors:
+            continue
+        for spc in FWD_SENSORS:
+            yield c, spc
+
+
+def default_cache_path() -> str:
+    return os.environ.get("PA_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "pa_gb300",
+                                       "autotune.json"))
+
+
+class Autotuner:
+    """Pick (adj_cluster, fwd_sensors_per_cta) per size class.
+
+    ``measure(prob, adj_cluster, spc) -> seconds`` defaults to timing real plans
+    on the current GPU; tests inject their own."""
+
+    def __init__(self, cache_path: Optional[str] = None,
+                 measure: Optional[Callable] = None, gpu_name: Optional[str] = None):
+        self.cache_path = cache_path or default_cache_path()
+        self.measure = measure or _measure_gpu
+        self._gpu = gpu_name
+        self.cache: Dict[str, dict] = {}
+        if os.path.exists(self.cache_path):
+            try:
+                with open(self.cache_path) as f:
+                    self.cache = json.load(f)
+            except (OSError, ValueError):
+                self.cache = {}
+
+    @property
+    def gpu(self) -> str:
+        if self._gpu is None:
+            import torch
+            self._gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+        return self._gpu
+
+    def key(self, prob) -> str:
+        return size_key(self.gpu, prob.dim, prob.n_pixels, prob.n_sensors, prob.n_samples)
+
+    def best(self, prob, force: bool = False) -> dict:
+        k = self.key(prob)
+        if not force and k in self.cache:
+            return self.cache[k]
+        timings = {}
+        for c, spc in candidates(prob.n_sensors):
+            timings[f"{c},{spc}"] = float(self.measure(prob, c, spc))
+        choice = min(timings, key=lambda s: (timings[s], s))
+        c, spc = (int(v) for v in choice.split(","))
+        entry = {"adj_cluster": c, "fwd_sensors_per_cta": spc, "timings_s": timings}
+        self.cache[k] = entry
+        self._save()
+        return entry
+
+    def _save(self) -> None:
+        os.makedirs(os.path.dirname(self.cache_path) or ".", exist_ok=True)
+        tmp = self.cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(self.cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.cache_path)
+
+
+def _measure_gpu(prob, adj_cluster: int, spc: int, reps: int = 5) -> float:
+    """Median time (s) of one forward + one adjoint application on the GPU."""
+    import torch
+
+    from .api import Plan
+
+    with Plan.from_problem(prob, adj_cluster=adj_cluster, fwd_sensors_per_cta=spc) as plan:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.rand(prob.n_pixels, device="cuda", generator=g)
+        y = torch.randn(prob.n_sensors, prob.n_samples, device="cuda", generator=g)
+        p = torch.empty_like(y)
+        z = torch.empty_like(x)
+        for _ in range(2):
+            plan.forward(x, out=p)
+            plan.adjoint(y, out=z)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.forward(x, out=p)
+            plan.adjoint(y, out=z)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b) * 1e-3)
+        return statistics.median(times)

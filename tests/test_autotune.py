@@ -1,0 +1,36 @@
+"""Autotuner host logic (no GPU): size classes, candidate sets, selection and cache."""
+import json
+
+from paper_2404_10928_gb300 import autotune, phantoms as ph
+
+
+def test_size_key_buckets():
+    k = autotune.size_key("GB300", 2, 65536, 256, 2048)
+    assert k == "GB300|2d|N65536|S256|K2048"
+    assert autotune.size_key("GB300", 2, 65537, 200, 1500) == "GB300|2d|N131072|S256|K2048"
+
+
+def test_candidates_respect_sensor_count():
+    c = list(autotune.candidates(6))
+    assert all(cl in (1, 2) for cl, _ in c)  # 4 and 8 need at least 8 and 16 sensors
+    assert len(list(autotune.candidates(512))) == 12
+
+
+def test_selection_and_cache(tmp_path):
+    prob = ph.custom(2, (40, 30), (1e-4, 1e-4), ph.ring_sensors(64, 5e-3), 300, seed=1)
+    calls = []
+
+    def fake(prob_, c, spc):
+        calls.append((c, spc))
+        return 1.0 + 0.1 * abs(c - 4) + 0.01 * abs(spc - 16)
+
+    path = tmp_path / "tune.json"
+    t = autotune.Autotuner(str(path), measure=fake, gpu_name="GB300")
+    best = t.best(prob)
+    assert (best["adj_cluster"], best["fwd_sensors_per_cta"]) == (4, 16)
+    assert len(calls) == 12
+    # cached: a second tuner reads the file and does not measure again
+    t2 = autotune.Autotuner(str(path), measure=lambda *a: 1 / 0, gpu_name="GB300")
+    assert t2.best(prob)["adj_cluster"] == 4
+    data = json.loads(path.read_text())
+    assert list(data) == [t.key(prob)]

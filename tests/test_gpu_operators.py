@@ -119,3 +119,22 @@ def test_bad_tensor_arguments(torch_cuda):
             plan.forward(torch.zeros(prob.n_pixels + 1, device="cuda"))
         with pytest.raises(ValueError):
             plan.forward(torch.zeros(prob.n_pixels, device="cuda", dtype=torch.float64))
+
+
+def test_autotuned_plan_matches_default(torch_cuda, tmp_path):
+    """The autotuner picks a valid decomposition; the tuned plan computes the same
+    operators (A bitwise; A^T up to the order of the per-pixel cluster sum)."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300.api import Plan
+    from paper_2404_10928_gb300.autotune import Autotuner
+    prob = CASES["ragged-37x53-ring13-k301"]
+    best = Autotuner(str(tmp_path / "t.json")).best(prob)
+    assert best["adj_cluster"] in (1, 2, 4, 8) and best["fwd_sensors_per_cta"] in (16, 32, 64)
+    x, y = _inputs(prob, seed=9)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    with Plan.from_problem(prob) as a, Plan.from_problem(
+            prob, adj_cluster=best["adj_cluster"],
+            fwd_sensors_per_cta=best["fwd_sensors_per_cta"]) as b:
+        assert torch.equal(a.forward(xt), b.forward(xt))
+        assert rel_l2(a.adjoint(yt).cpu().numpy(), b.adjoint(yt).cpu().numpy()) <= 1e-6
