@@ -293,6 +293,50 @@ def bench_differentiable(torch, reps: int = 3) -> dict:
             "timing": f"median of {reps}, CUDA events"}
 
 
+def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
+    """3D workload: 128^3 voxels at 0.2 mm, 32x32 planar array (0.8 mm pitch,
+    5 mm from the volume), 1024 samples; A and A^T rates, a 30-iteration CGLS
+    and the speed-of-sound derivative."""
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Plan
+    prob = ph.planar_vessel_tree()
+    t = tuner.best(prob)
+    plan = Plan.from_problem(prob, adj_cluster=t["adj_cluster"],
+                             fwd_sensors_per_cta=t["fwd_sensors_per_cta"])
+    x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
+    y = plan.forward(x_true)
+    # operator timings on a dense image (an all-zero tile skips its work, so the
+    # sparse phantom itself would flatter the forward gather)
+    x = torch.rand(prob.n_pixels, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    p = torch.empty_like(y)
+    g = torch.empty_like(x)
+    out = torch.zeros_like(x)
+    plan.adjoint(y, out=g)
+    plan.reconstruct(y, "cgls", 30, out=out)
+    t_f = _events_time(torch, lambda: plan.forward(x, out=p), reps)
+    t_a = _events_time(torch, lambda: plan.adjoint(y, out=g), reps)
+
+    def cgls():
+        out.zero_()
+        plan.reconstruct(y, "cgls", 30, out=out)
+
+    t_c = _events_time(torch, cgls, reps)
+    t_d = _events_time(torch, lambda: plan.dc(x, y), reps)
+    plan.close()
+    pairs = prob.pairs
+    return {"workload": "3D 128^3 at 0.2 mm, 32x32 planar array 0.8 mm pitch 5 mm from the "
+                        "volume, 1024 samples, vessel tree",
+            "pairs_per_application": pairs,
+            "autotuned": {"adj_cluster": t["adj_cluster"],
+                          "fwd_sensors_per_cta": t["fwd_sensors_per_cta"]},
+            "forward_ms": t_f * 1e3, "adjoint_ms": t_a * 1e3,
+            "forward_pairs_per_s": pairs / t_f, "adjoint_pairs_per_s": pairs / t_a,
+            "adjoint_frac_fp32": pairs * FLOPS_PER_PAIR / t_a / 1e12 / peak_tflops,
+            "forward_frac_fp32": pairs * FLOPS_PER_PAIR / t_f / 1e12 / peak_tflops,
+            "cgls30_ms": t_c * 1e3, "cgls30_frames_per_s": 1.0 / t_c, "dc_ms": t_d * 1e3,
+            "timing": f"median of {reps}, CUDA events (inputs far larger than L2)"}
+
+
 def run_gpu(args):
     import torch
 
@@ -393,6 +437,11 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extras:
         extra["batched"] = bench_batched(torch, tuner)
         extra["differentiable"] = bench_differentiable(torch)
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        sm_max = json.load(open(pk)).get("sm_max_mhz", 2070.0) if os.path.exists(pk) else 2070.0
+        peak = (torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * sm_max
+                * 1e6 / 1e12)
+        extra["volume3d"] = bench_volume(torch, tuner, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

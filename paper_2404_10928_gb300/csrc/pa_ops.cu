@@ -699,10 +699,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
             time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
                                       idx);
             const float ws = (xs[m] * dlo) * rinv;
-            const int iw = __float_as_int(__fadd_rn(ws, kMagic)) - kMagicBits;
-            const int ia = __float_as_int(__fadd_rn(fmaf(-ws, e, 0.5f * ws), kMagic)) - kMagicBits;
+            // rounded to integers: 0.5 ws to the magic grid first, then + -/+ ws e
+            const float hm = fmaf(ws, 0.5f, kMagic);
+            const int ia = __float_as_int(fmaf(-ws, e, hm)) - kMagicBits;  // x (1 - f) / d
+            const int ib = __float_as_int(fmaf(ws, e, hm)) - kMagicBits;   // x f / d
             atomicAdd(w + idx, ia);
-            atomicAdd(w + idx + 1, iw - ia);
+            atomicAdd(w + idx + 1, ib);
           }
         } else {
 #pragma unroll
@@ -712,10 +714,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
             time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
                                        idx);
             const float ws = (xs[m] * dlo) * rinv;
-            const int iw = __float_as_int(__fadd_rn(ws, kMagic)) - kMagicBits;
-            const int ia = __float_as_int(__fadd_rn(fmaf(-ws, e, 0.5f * ws), kMagic)) - kMagicBits;
+            // rounded to integers: 0.5 ws to the magic grid first, then + -/+ ws e
+            const float hm = fmaf(ws, 0.5f, kMagic);
+            const int ia = __float_as_int(fmaf(-ws, e, hm)) - kMagicBits;  // x (1 - f) / d
+            const int ib = __float_as_int(fmaf(ws, e, hm)) - kMagicBits;   // x f / d
             atomicAdd(w + idx, ia);
-            atomicAdd(w + idx + 1, iw - ia);
+            atomicAdd(w + idx + 1, ib);
           }
         }
       }
@@ -727,12 +731,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
       if (store && finite && xscale > 0.0f)
         unscale = xmax / (kFixedScale * fmaxf(refs[g0 + sb].dref - R, P.half_hmin));
       float* dst = P.part + ((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L;
-      int* src = wb + sb * L;
-      for (int k = tid; k < L; k += nt) {
+      const int* src = wb + sb * L;
+      for (int k = tid; k < L; k += nt)
         if (store) dst[k] = finite ? (float)src[k] * unscale : __int_as_float(0x7fc00000);
-        src[k] = 0;  // this buffer is reused two stages later, after the next barrier
-      }
     }
+    __syncthreads();
+    for (int i = tid; i < kFwdSB * L; i += nt) wb[i] = 0;  // reused two stages later
   }
   __syncthreads();  // the block's shared memory is free for the next work item
 }
