@@ -21,7 +21,7 @@ import statistics
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 ADJ_CLUSTERS = (1, 2, 4, 8)
-FWD_SENSORS = (16, 32, 64)
+FWD_SENSORS = (8, 12, 16, 20, 24, 32, 48, 64)
 
 
 def _pow2(n: int) -> int:

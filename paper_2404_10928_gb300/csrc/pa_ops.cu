@@ -626,6 +626,8 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   TileRef* refs = reinterpret_cast<TileRef*>(smem);
   int* win = reinterpret_cast<int*>(refs + P.spc);
   __shared__ float s_max[32];
+  __shared__ float s_unscale[kFwdSB];
+  __shared__ int s_store[kFwdSB];
 
   const int L = P.L;
   const int s0 = chunk * P.spc;
@@ -724,16 +726,23 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
         }
       }
     }
+    __syncthreads();  // all taps of the stage are in the windows
+    // rescale factor of each sensor of the stage (0: nothing to store)
+    if (tid < kFwdSB) {
+      float u = 0.0f;
+      if (tid < nsb && refs[g0 + tid].klo != kSkip)
+        u = !finite ? __int_as_float(0x7fc00000)
+            : (xscale > 0.0f ? __fdividef(xmax, kFixedScale * fmaxf(refs[g0 + tid].dref - R,
+                                                                    P.half_hmin))
+                             : 0.0f);
+      s_unscale[tid] = u;
+      s_store[tid] = tid < nsb && refs[g0 + tid].klo != kSkip;
+    }
     __syncthreads();
-    for (int sb = 0; sb < kFwdSB; ++sb) {
-      const bool store = sb < nsb && refs[g0 + sb].klo != kSkip;
-      float unscale = 0.0f;
-      if (store && finite && xscale > 0.0f)
-        unscale = xmax / (kFixedScale * fmaxf(refs[g0 + sb].dref - R, P.half_hmin));
-      float* dst = P.part + ((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L;
-      const int* src = wb + sb * L;
-      for (int k = tid; k < L; k += nt)
-        if (store) dst[k] = finite ? (float)src[k] * unscale : __int_as_float(0x7fc00000);
+    for (int i = tid; i < nsb * L; i += nt) {
+      const int sb = i / L, k = i - sb * L;
+      if (s_store[sb])
+        P.part[((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L + k] = (float)wb[i] * s_unscale[sb];
     }
     __syncthreads();
     for (int i = tid; i < kFwdSB * L; i += nt) wb[i] = 0;  // reused two stages later

@@ -121,6 +121,11 @@ def test_bad_tensor_arguments(torch_cuda):
             plan.forward(torch.zeros(prob.n_pixels, device="cuda", dtype=torch.float64))
 
 
+def autotune_sizes():
+    from paper_2404_10928_gb300.autotune import FWD_SENSORS
+    return FWD_SENSORS
+
+
 def test_autotuned_plan_matches_default(torch_cuda, tmp_path):
     """The autotuner picks a valid decomposition; the tuned plan computes the same
     operators (A bitwise; A^T up to the order of the per-pixel cluster sum)."""
@@ -129,7 +134,8 @@ def test_autotuned_plan_matches_default(torch_cuda, tmp_path):
     from paper_2404_10928_gb300.autotune import Autotuner
     prob = CASES["ragged-37x53-ring13-k301"]
     best = Autotuner(str(tmp_path / "t.json")).best(prob)
-    assert best["adj_cluster"] in (1, 2, 4, 8) and best["fwd_sensors_per_cta"] in (16, 32, 64)
+    assert best["adj_cluster"] in (1, 2, 4, 8)
+    assert best["fwd_sensors_per_cta"] in autotune_sizes()
     x, y = _inputs(prob, seed=9)
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     yt = torch.tensor(y, dtype=torch.float32, device="cuda")
