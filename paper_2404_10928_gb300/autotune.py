@@ -36,11 +36,13 @@ def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int) 
 
 
 def candidates(n_sensors: int) -> Iterable[Tuple[int, int]]:
-    for c in ADJ_CLUSTERS:
-        if c > 1 and 2 * c > n_sensors:
-            continue
-        for spc in FWD_SENSORS:
-            yield c, spc
+    """adj_cluster only changes the adjoint and fwd_sensors_per_cta only the
+    forward, so each is varied with the other at its default."""
+    for spc in FWD_SENSORS:
+        yield 1, spc
+    for c in ADJ_CLUSTERS[1:]:
+        if 2 * c <= n_sensors:
+            yield c, 32
 
 
 def default_cache_path() -> str:
@@ -85,8 +87,10 @@ class Autotuner:
         timings = {}
         for c, spc in candidates(prob.n_sensors):
             timings[f"{c},{spc}"] = float(self.measure(prob, c, spc))
-        choice = min(timings, key=lambda s: (timings[s], s))
-        c, spc = (int(v) for v in choice.split(","))
+        by_spc = {int(k.split(",")[1]): t for k, t in timings.items() if k.startswith("1,")}
+        by_c = {int(k.split(",")[0]): t for k, t in timings.items() if k.endswith(",32")}
+        spc = min(by_spc, key=lambda v: (by_spc[v], v))
+        c = min(by_c, key=lambda v: (by_c[v], v))
         entry = {"adj_cluster": c, "fwd_sensors_per_cta": spc, "timings_s": timings}
         self.cache[k] = entry
         self._save()
