@@ -69,6 +69,8 @@ def _load():
                 fn.restype = None
             lib.oracle_dc.argtypes = geo + [dp, dp, dp]
             lib.oracle_dc.restype = ctypes.c_double
+            lib.oracle_dc_flip_bound.argtypes = geo + [dp, dp, ctypes.c_double]
+            lib.oracle_dc_flip_bound.restype = ctypes.c_double
             lib.oracle_min_distance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.oracle_min_distance.restype = ctypes.c_double
@@ -151,6 +153,15 @@ def dc(geo: Geometry, x, g, c=None) -> float:
     g = _f64(g).reshape(geo.n_sensors, geo.n_samples)
     per = np.empty(geo.n_sensors)
     return float(_load().oracle_dc(*geo._args(c), _ptr(x), _ptr(g), _ptr(per)))
+
+
+def dc_flip_bound(geo: Geometry, x, g, delta: float, c=None) -> float:
+    """Largest change of dc() that arrivals rounded by up to `delta` samples can
+    cause: pairs within delta of an integer may take either one-sided derivative
+    of the hat."""
+    x = _f64(x).ravel()
+    g = _f64(g).reshape(geo.n_sensors, geo.n_samples)
+    return float(_load().oracle_dc_flip_bound(*geo._args(c), _ptr(x), _ptr(g), float(delta)))
 
 
 def min_distance(geo: Geometry) -> float:

@@ -176,6 +176,44 @@ double oracle_dc(int dim, int nx, int ny, int nz, const double *spacing,
   return total;
 }
 
+/*
+ * How far d/dc may legitimately move under arrival rounding.  The hat's
+ * derivative jumps where u crosses an integer m: just below m the taps are
+ * (m-1, m), just above (m, m+1).  An implementation that evaluates u with an
+ * error up to `delta` samples may take either side for pairs with
+ * |u - m| < delta; the two choices differ by
+ *     amp * x_i / d * (g[m+1] - 2 g[m] + g[m-1]) * du/dc.
+ * Returns the sum of the magnitudes of those differences (samples outside
+ * [0, K) read as 0).
+ */
+double oracle_dc_flip_bound(int dim, int nx, int ny, int nz, const double *spacing,
+                            const double *origin, const double *sensors, int n_sensors,
+                            double c, double fs, double t0, double amp, int n_samples,
+                            const double *x, const double *g, double delta) {
+  long n_pix = (long)nx * ny * nz;
+  double total = 0.0;
+  for (int s = 0; s < n_sensors; ++s) {
+    const double *rs = sensors + (long)s * dim;
+    const double *gs = g + (long)s * n_samples;
+    for (long i = 0; i < n_pix; ++i) {
+      if (x[i] == 0.0) continue;
+      double pos[3];
+      pixel_position(i, nx, ny, spacing, origin, pos);
+      double d = distance(dim, pos, rs);
+      double u = d * fs / c - t0 * fs;
+      double m = floor(u + 0.5);
+      if (fabs(u - m) >= delta) continue;
+      long k = (long)m;
+      double gm1 = (k - 1 >= 0 && k - 1 < n_samples) ? gs[k - 1] : 0.0;
+      double g0 = (k >= 0 && k < n_samples) ? gs[k] : 0.0;
+      double gp1 = (k + 1 >= 0 && k + 1 < n_samples) ? gs[k + 1] : 0.0;
+      double dudc = -d * fs / (c * c);
+      total += fabs(amp * x[i] / d * (gp1 - 2.0 * g0 + gm1) * dudc);
+    }
+  }
+  return total;
+}
+
 /* Minimum pixel-sensor distance (geometry validation). */
 double oracle_min_distance(int dim, int nx, int ny, int nz, const double *spacing,
                            const double *origin, const double *sensors, int n_sensors) {

@@ -193,6 +193,32 @@ def test_dc_matches_finite_differences():
     assert abs(an - fd) <= 1e-6 * abs(fd)
 
 
+def test_dc_flip_bound_is_the_derivative_jump():
+    """A pixel whose arrival sits on an integer sample m: the bound equals the
+    jump between the one-sided finite-difference derivatives of <g, A(x; c)>
+    in c, and vanishes once delta is below the distance to the integer."""
+    fs, c0, m = 40e6, 1500.0, 57
+    d = m * c0 / fs
+    geo = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                       np.array([[d, 0.0]]), c0, fs, 128, 0.0, 0.7)
+    rng = np.random.default_rng(11)
+    x = np.array([0.8])
+    g = rng.normal(size=(1, 128))
+    f = lambda cc: float(np.sum(g * orc.forward(geo, x, c=cc)))
+    h = 1e-3
+    d_plus = (f(c0 + h) - f(c0)) / h    # u just below m: taps (m-1, m)
+    d_minus = (f(c0) - f(c0 - h)) / h   # u just above m: taps (m, m+1)
+    jump = abs(d_plus - d_minus)
+    assert jump > 0.0
+    bound = orc.dc_flip_bound(geo, x, g, 1e-6)
+    assert abs(bound - jump) <= 1e-4 * jump, (bound, jump)
+    # moving the sensor a quarter sample away takes the pair out of range
+    geo2 = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                        np.array([[d + 0.25 * c0 / fs, 0.0]]), c0, fs, 128, 0.0, 0.7)
+    assert orc.dc_flip_bound(geo2, x, g, 0.2) == 0.0
+    assert orc.dc_flip_bound(geo2, x, g, 0.3) > 0.0
+
+
 def test_tv_constant_and_fd():
     eps = 1e-4
     img = np.full((5, 7), 0.3)
