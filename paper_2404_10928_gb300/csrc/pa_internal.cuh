@@ -52,21 +52,35 @@ constexpr int kSkip = INT_MIN;
 // lets FP32 evaluate the sample position with the error of the small
 // difference instead of the error of d itself (u reaches ~1300 samples, where
 // an FP32 ulp is ~1e-4 samples).  u_ref is formed in FP64 when the table is
-// built and stored relative to the start of the staged trace window.
+// built and stored relative to the centre of the staged trace window, so the
+// FP32 position within the window carries at most L/2 in magnitude.
 // ---------------------------------------------------------------------------
 struct __align__(16) TileRef {
-  int klo;      // first sample of the staged window (even), or kSkip
-  float fref;   // u_ref - klo - 0.5
+  int klo;      // first sample of the staged window (even) | kNear, or kSkip
+  float fref;   // u_ref - (klo & ~1) - 0.5 - L/2
   float dref;   // |centre - sensor|
   float dref2;  // d_ref^2
   float ex2k;   // 2*kappa*(centre - sensor).x
   float ey2k;   // 2*kappa*(centre - sensor).y
   float ez2k;   // 2*kappa*(centre - sensor).z (0 in 2D)
-  int flags;    // kNear: the sensor is much closer to some pixel than to the centre
+  float dlo;    // lower bound on |pixel - sensor| over the tile (>= half a pixel)
 };
-// d^2 = d_ref^2 + q/kappa cancels when d << d_ref; such pairs form d^2 from the
+// Low bit of klo: the sensor is much closer to some pixel than to the tile
+// centre, where d^2 = d_ref^2 + q/kappa cancels; such pairs form d^2 from the
 // explicit offset vector instead (sensors inside or next to the grid).
 constexpr int kNear = 1;
+__host__ __device__ inline int window_start(int klo) { return klo & ~kNear; }
+
+// A TileRef as staged in shared memory for packed (two-pixel) FP32 math: every
+// operand field appears twice, so one 64-bit shared load yields a register
+// pair ready for the f32x2 instructions.
+struct __align__(16) TileRef2 {
+  float2 ex2k, ey2k, ez2k, dref2, dref, fref;
+  int klo;
+  float dlo;
+  int pad0, pad1;
+};
+static_assert(sizeof(TileRef2) == 64, "TileRef2 must be 64 bytes");
 static_assert(sizeof(TileRef) == 32, "TileRef must be 32 bytes");
 
 struct GridF {
@@ -119,7 +133,7 @@ struct FwdParams {
   int S, K, L, ntiles;
   int spc;                // sensors per forward tile work item
   GridF g;
-  float kappa, inv_kappa, half_inv_kappa, amp, half_hmin;
+  float kappa, inv_kappa, half_inv_kappa, amp;
   int mode;
   float* out;             // [S][K]
   const void* y;          // [S][K] measured traces (FWD_RESID), f32 or f16

@@ -80,6 +80,32 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return mbar_wait_slow(bar, parity);
 }
 
+// Shared-memory accesses through 32-bit shared-window addresses, so that the
+// per-pair address is one shift-add of a staged base (see the magic-number
+// indexing below).
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void reds_add(uint32_t a, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Packed FP32 on pixel pairs: one f32x2 instruction performs the same IEEE
+// operation on both lanes (bitwise what the scalar form gives per lane) in one
+// issue slot.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ void set_lane(float2& v, int i, float x) {
+  if (i)
+    v.y = x;
+  else
+    v.x = x;
+}
+
 // 1D bulk copy global -> shared, completion counted in bytes on `bar`.
 // Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
@@ -203,37 +229,61 @@ __device__ __forceinline__ void clamp_local(int tx, int ty, int tz, const GridF&
 
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
 constexpr int kMagicBits = 0x4B400000;
+// t = w + kMagic holds round(w) in its low mantissa bits: bits(t) = kMagicBits +
+// round(w) for |w| < 2^22.  A window element n (centred index n - L/2) of
+// `size`-byte elements is then addressed as base + (bits(t) << log2 size) with
+// base = window centre - (kMagicBits << log2 size), all modulo 2^32.
+__device__ __forceinline__ uint32_t magic_base(uint32_t centre, int log2size) {
+  return centre - ((uint32_t)kMagicBits << log2size);
+}
 
-// Sample position of one (pixel, sensor) pair relative to the staged window:
-// returns the window index n = floor(u_loc) through `idx`, e = u_loc - n - 0.5
-// in [-0.5, 0.5] and rinv = 1/d.  NEAR pairs (kNear) form d^2 from the offset
-// vector (centre - sensor) + delta instead of d_ref^2 + q/kappa.
+// Sample positions of two pixels (a packed pair) for one sensor, relative to
+// the centre of the staged window: returns w = u_loc - 0.5 - L/2 per lane (the
+// element n_c = round(w) of the centred window holds samples n_c and n_c + 1,
+// with the arrival at fraction w - n_c + 1/2 between them) and rinv = 1/d.
+// NEAR pairs (kNear) form d^2 from the offset vector (centre - sensor) + delta
+// instead of d_ref^2 + q/kappa.
 template <int DIM, bool NEAR>
-__device__ __forceinline__ void time_of_flight(const TileRef& r, float ddx, float ddy, float ddz,
-                                               float cm, float inv_kappa, float half_inv_kappa,
-                                               float& rinv, float& e, int& idx) {
-  float q;
+__device__ __forceinline__ float2 arrival2(const TileRef2& r, float2 ddx, float2 ddy, float2 ddz,
+                                           float2 cm, float2 inv_kappa, float2 half_inv_kappa,
+                                           float2& rinv) {
+  float2 q;
   if (DIM == 3)
-    q = fmaf(r.ex2k, ddx, fmaf(r.ey2k, ddy, fmaf(r.ez2k, ddz, cm)));
+    q = fma2(r.ex2k, ddx, fma2(r.ey2k, ddy, fma2(r.ez2k, ddz, cm)));
   else
-    q = fmaf(r.ex2k, ddx, fmaf(r.ey2k, ddy, cm));
-  float d2;
+    q = fma2(r.ex2k, ddx, fma2(r.ey2k, ddy, cm));
+  float2 d2;
   if (NEAR) {
-    const float ax = fmaf(r.ex2k, half_inv_kappa, ddx);
-    const float ay = fmaf(r.ey2k, half_inv_kappa, ddy);
-    const float az = (DIM == 3) ? fmaf(r.ez2k, half_inv_kappa, ddz) : 0.0f;
-    d2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+    const float2 ax = fma2(r.ex2k, half_inv_kappa, ddx);
+    const float2 ay = fma2(r.ey2k, half_inv_kappa, ddy);
+    if (DIM == 3) {
+      const float2 az = fma2(r.ez2k, half_inv_kappa, ddz);
+      d2 = fma2(ax, ax, fma2(ay, ay, mul2(az, az)));
+    } else {
+      d2 = fma2(ax, ax, mul2(ay, ay));
+    }
   } else {
-    d2 = fmaf(q, inv_kappa, r.dref2);   // |r_i - r_s|^2
+    d2 = fma2(q, inv_kappa, r.dref2);  // |r_i - r_s|^2
   }
-  rinv = rsqrt_approx(d2);
-  const float d = d2 * rinv;
-  const float rden = rcp_approx(d + r.dref);
-  const float w = fmaf(q, rden, r.fref);         // u_loc - 0.5
-  const float t = __fadd_rn(w, kMagic);
-  const float n = __fsub_rn(t, kMagic);
-  e = __fsub_rn(w, n);
-  idx = __float_as_int(t) - kMagicBits;
+  rinv = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+  const float2 den = fma2(d2, rinv, r.dref);  // d + d_ref
+  const float2 rden = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+  return fma2(q, rden, r.fref);
+}
+
+// Expands a table entry into its shared-memory form.
+__device__ __forceinline__ TileRef2 expand_ref(const TileRef& r) {
+  TileRef2 e;
+  e.ex2k = f2(r.ex2k);
+  e.ey2k = f2(r.ey2k);
+  e.ez2k = f2(r.ez2k);
+  e.dref2 = f2(r.dref2);
+  e.dref = f2(r.dref);
+  e.fref = f2(r.fref);
+  e.klo = r.klo;
+  e.dlo = r.dlo;
+  e.pad0 = e.pad1 = 0;
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -287,7 +337,8 @@ __global__ void k_build_table(TileRef* __restrict__ table, int2* __restrict__ kr
     r.ez2k = (float)(2.0 * kappa * ez);
     const bool skip = (k0max + 1.0 < 0.0) || (k0min > (double)(K - 1));
     // every pixel is >= hmin/2 from every sensor (checked at plan creation)
-    r.flags = (dref > 4.0 * fmax(dmin, 0.5 * hmin)) ? kNear : 0;
+    const int near = (dref > 4.0 * fmax(dmin, 0.5 * hmin)) ? kNear : 0;
+    r.dlo = (float)fmax(dmin, 0.5 * hmin);
     int2 kr;
     if (skip) {
       r.klo = kSkip;
@@ -297,8 +348,8 @@ __global__ void k_build_table(TileRef* __restrict__ table, int2* __restrict__ kr
       long long kl = (long long)k0min - 2;
       kl = kl & ~1LL;  // round down to even (16-byte aligned float2 window)
       if ((long long)k0max - kl + 1 > (long long)L - 2) atomicOr(err, ERR_WINDOW);
-      r.klo = (int)kl;
-      r.fref = (float)(uref - (double)kl - 0.5);
+      r.klo = (int)kl | near;
+      r.fref = (float)(uref - (double)kl - 0.5 - 0.5 * (double)L);
       kr = make_int2((int)k0min - 1, (int)k0max + 2);
     }
     table[idx] = r;
@@ -361,14 +412,37 @@ cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, in
 // the sensors.  A producer warp stages, per pipeline stage, the reference
 // entries of kAdjSB sensors and each sensor's window of L packed trace samples
 // (one cp.async.bulk per sensor, completion tracked by an mbarrier); eight
-// compute warps evaluate four pixels per thread per sensor from shared memory.
-// The C partial images are summed through distributed shared memory in rank
-// order, then the epilogue (store / Landweber update / norm) runs once.
+// compute warps evaluate four pixels per thread per sensor from shared memory,
+// as two packed pixel pairs.  The C partial images are summed through
+// distributed shared memory in rank order, then the epilogue (store /
+// Landweber update / norm) runs once.
 // ---------------------------------------------------------------------------
 int adjoint_smem_bytes(int L) {
   return kAdjStages * kAdjSB * L * (int)sizeof(float2) +
-         kAdjStages * kAdjSB * (int)sizeof(TileRef) + kTilePixels * (int)sizeof(float) +
+         kAdjStages * kAdjSB * (int)sizeof(TileRef2) + kTilePixels * (int)sizeof(float) +
          2 * kAdjStages * (int)sizeof(uint64_t);
+}
+
+// Terms of A^T (DC: of the c-derivative's pixel sums) for a pixel pair and one
+// sensor: `base` is the magic_base of the sensor's centred window of packed
+// (mid, slope) samples; the interpolated value is mid + (w - n_c) slope.
+template <int DIM, bool NEAR, bool DC>
+__device__ __forceinline__ void adj_pair2(const TileRef2& r, uint32_t base, float2 ddx, float2 ddy,
+                                          float2 ddz, float2 cm, float2 inv_kappa, float2 hik,
+                                          float& acc0, float& acc1) {
+  float2 rinv;
+  const float2 w = arrival2<DIM, NEAR>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv);
+  const float2 t = add2(w, f2(kMagic));
+  const float2 v0 = lds_f2(base + ((uint32_t)__float_as_int(t.x) << 3));
+  const float2 v1 = lds_f2(base + ((uint32_t)__float_as_int(t.y) << 3));
+  if (DC) {  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
+    acc0 += v0.y;
+    acc1 += v1.y;
+  } else {
+    const float2 e = fma2(add2(t, f2(-kMagic)), f2(-1.0f), w);  // w - n_c, in [-1/2, 1/2]
+    acc0 = fmaf(fmaf(e.x, v0.y, v0.x), rinv.x, acc0);
+    acc1 = fmaf(fmaf(e.y, v1.y, v1.x), rinv.y, acc1);
+  }
 }
 
 // Accumulates, for every pixel of `tile`, the sum over sensors [s_begin, s_end)
@@ -379,7 +453,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
                                                  int s_end, unsigned char* smem) {
   const int L = P.L;
   float2* s_trace = reinterpret_cast<float2*>(smem);
-  TileRef* s_ref = reinterpret_cast<TileRef*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
+  TileRef2* s_ref = reinterpret_cast<TileRef2*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
   float* s_acc = reinterpret_cast<float*>(s_ref + kAdjStages * kAdjSB);
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_acc + kTilePixels);
   uint64_t* s_empty = s_full + kAdjStages;
@@ -422,16 +496,19 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
       const float2* src = nullptr;
       if (lane < kAdjSB) {
         TileRef r;
+        r.klo = kSkip;
         if (s < s_end) {
           r = P.table[(int64_t)tile * P.S + s];
           if (r.klo != kSkip) {
             bytes = (uint32_t)L * (uint32_t)sizeof(float2);
-            src = P.packed + (int64_t)s * P.Kp + P.pad + r.klo;
+            src = P.packed + (int64_t)s * P.Kp + P.pad + window_start(r.klo);
           }
-        } else {
-          r.klo = kSkip;
         }
-        s_ref[slot * kAdjSB + lane] = r;
+        if (r.klo != kSkip) {
+          s_ref[slot * kAdjSB + lane] = expand_ref(r);
+        } else {
+          s_ref[slot * kAdjSB + lane].klo = kSkip;
+        }
       }
       const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
       __syncwarp();
@@ -442,7 +519,9 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
     if (lane == 0) s_issued = j;
   } else {
     // ----------------------------- compute warps -----------------------------
-    float ddx[kAdjPPT], ddy[kAdjPPT], ddz[kAdjPPT], cm[kAdjPPT], acc[kAdjPPT];
+    // pixels tid + m * 256, m = 0..3, as packed pairs (m = 0, 1) and (2, 3)
+    float2 ddx[2], ddy[2], ddz[2], cm[2];
+    float acc[kAdjPPT];
     const int ttx = tile % P.g.ntx, tty = (tile / P.g.ntx) % P.g.nty;
     const int ttz = tile / (P.g.ntx * P.g.nty);
     int nvx, nvy, nvz;
@@ -450,12 +529,18 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
 #pragma unroll
     for (int m = 0; m < kAdjPPT; ++m) {
       int lx, ly, lz;
+      float ox, oy, oz, oc;
       pixel_local<DIM>(tid + m * 32 * kAdjWarps, lx, ly, lz);
       clamp_local<DIM>(ttx, tty, ttz, P.g, lx, ly, lz);
-      pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ddx[m], ddy[m], ddz[m], cm[m]);
+      pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ox, oy, oz, oc);
+      set_lane(ddx[m >> 1], m & 1, ox);
+      set_lane(ddy[m >> 1], m & 1, oy);
+      set_lane(ddz[m >> 1], m & 1, oz);
+      set_lane(cm[m >> 1], m & 1, oc);
       acc[m] = 0.0f;
     }
-    const float inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
+    const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
+    const uint32_t trace_u32 = smem_u32(s_trace);
     for (int j = 0; j < n_stages; ++j) {
       const int slot = j % kAdjStages;
       const bool ok = mbar_wait_bounded(&s_full[slot], (j / kAdjStages) & 1);
@@ -467,39 +552,22 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
         break;
       }
       if (*(volatile int*)&s_abort) break;
-      const TileRef* refs = s_ref + slot * kAdjSB;
-      const float2* trs = s_trace + slot * kAdjSB * L;
+      const TileRef2* refs = s_ref + slot * kAdjSB;
+      uint32_t base = magic_base(trace_u32 + (uint32_t)(slot * kAdjSB * L + L / 2) * 8u, 3);
 #pragma unroll 1
-      for (int sb = 0; sb < kAdjSB; ++sb) {
-        const TileRef r = refs[sb];
+      for (int sb = 0; sb < kAdjSB; ++sb, base += 8u * (uint32_t)L) {
+        const TileRef2 r = refs[sb];
         if (r.klo == kSkip) continue;
-        const float2* win = trs + sb * L;
-        if (r.flags & kNear) {
+        if (r.klo & kNear) {
 #pragma unroll
-          for (int m = 0; m < kAdjPPT; ++m) {
-            float rinv, e;
-            int idx;
-            time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
-                                      idx);
-            const float2 v = win[idx];
-            if (DC)
-              acc[m] += v.y;  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
-            else
-              acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
-          }
+          for (int h = 0; h < 2; ++h)
+            adj_pair2<DIM, true, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
+                                     acc[2 * h], acc[2 * h + 1]);
         } else {
 #pragma unroll
-          for (int m = 0; m < kAdjPPT; ++m) {
-            float rinv, e;
-            int idx;
-            time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
-                                       idx);
-            const float2 v = win[idx];
-            if (DC)
-              acc[m] += v.y;  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
-            else
-              acc[m] = fmaf(fmaf(e, v.y, v.x), rinv, acc[m]);
-          }
+          for (int h = 0; h < 2; ++h)
+            adj_pair2<DIM, false, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
+                                      acc[2 * h], acc[2 * h + 1]);
         }
       }
       __syncwarp();
@@ -611,23 +679,48 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // k, in a fixed order (by window start), plus the residual / norm epilogue.
 // ---------------------------------------------------------------------------
 int forward_smem_bytes(int L, int spc) {
-  return spc * (int)sizeof(TileRef) + 2 * kFwdSB * L * (int)sizeof(int);
+  return spc * (int)sizeof(TileRef2) + 2 * kFwdSB * L * (int)sizeof(int);
 }
 
 constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
 
+// Deposits the two taps xs (1-f)/d and xs f/d of a pixel pair for one sensor
+// (xs_dlo: the pixel values in fixed-point units times d_lo, so every tap is at
+// most 2^20) into the sensor's centred window of int32 (`base`: its
+// magic_base).  Rounding: ws = xs d_lo / d and the first tap ws (1 - f) are
+// each rounded to the nearest integer on the magic grid (W and a); the second
+// tap is W - a, so the taps of every pair sum exactly to its rounded weight.
+template <int DIM, bool NEAR>
+__device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, float2 ddx, float2 ddy,
+                                          float2 ddz, float2 cm, float2 xs_dlo, float2 inv_kappa,
+                                          float2 hik) {
+  float2 rinv;
+  const float2 w = arrival2<DIM, NEAR>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv);
+  const float2 t = add2(w, f2(kMagic));
+  const float2 n5 = add2(add2(t, f2(-kMagic)), f2(0.5f));  // n_c + 1/2 (exact)
+  const float2 hf = fma2(w, f2(-1.0f), n5);                // 1 - f (exact)
+  const float2 ws = mul2(xs_dlo, rinv);
+  const float2 ta = fma2(ws, hf, f2(kMagic));              // ws (1 - f)
+  const float2 tw = add2(ws, f2(kMagic));                  // ws
+  const uint32_t a0 = base + ((uint32_t)__float_as_int(t.x) << 2);
+  const uint32_t a1 = base + ((uint32_t)__float_as_int(t.y) << 2);
+  reds_add(a0, __float_as_int(ta.x) - kMagicBits);
+  reds_add(a0 + 4u, __float_as_int(tw.x) - __float_as_int(ta.x));
+  reds_add(a1, __float_as_int(ta.y) - kMagicBits);
+  reds_add(a1 + 4u, __float_as_int(tw.y) - __float_as_int(ta.y));
+}
+
 // One (tile, sensor chunk) work item of the forward gather.  The first
-// kFwdThreads threads own four pixels each; any further threads of the block
-// only help with the copies and barriers.
+// kFwdThreads threads own four pixels each (two packed pairs); any further
+// threads of the block only help with the copies and barriers.
 template <int DIM>
 __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int chunk,
                                                unsigned char* smem) {
   constexpr int PPT = kTilePixels / kFwdThreads;
-  TileRef* refs = reinterpret_cast<TileRef*>(smem);
+  static_assert(PPT == 4, "two packed pixel pairs per thread");
+  TileRef2* refs = reinterpret_cast<TileRef2*>(smem);
   int* win = reinterpret_cast<int*>(refs + P.spc);
   __shared__ float s_max[32];
-  __shared__ float s_unscale[kFwdSB];
-  __shared__ int s_store[kFwdSB];
 
   const int L = P.L;
   const int s0 = chunk * P.spc;
@@ -640,7 +733,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
 
-  float ddx[PPT], ddy[PPT], ddz[PPT], cm[PPT], xs[PPT];
+  float2 ddx[2], ddy[2], ddz[2], cm[2], xs[2];
   float amax = 0.0f;
   int nonfinite = 0;
 #pragma unroll
@@ -659,14 +752,21 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     }
     amax = fmaxf(amax, fabsf(xv));
     nonfinite |= !(fabsf(xv) <= 3.0e38f);
-    xs[m] = xv;
+    set_lane(xs[m >> 1], m & 1, xv);
     clamp_local<DIM>(tx, ty, tz, P.g, lx, ly, lz);
-    pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ddx[m], ddy[m], ddz[m], cm[m]);
+    float ox, oy, oz, oc;
+    pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ox, oy, oz, oc);
+    set_lane(ddx[m >> 1], m & 1, ox);
+    set_lane(ddy[m >> 1], m & 1, oy);
+    set_lane(ddz[m >> 1], m & 1, oz);
+    set_lane(cm[m >> 1], m & 1, oc);
   }
-  {
-    const int4* src = reinterpret_cast<const int4*>(P.table + (int64_t)tile * P.S + s0);
-    int4* dst = reinterpret_cast<int4*>(refs);
-    for (int i = tid; i < ns * 2; i += nt) dst[i] = src[i];
+  for (int i = tid; i < ns; i += nt) {
+    const TileRef r = P.table[(int64_t)tile * P.S + s0 + i];
+    if (r.klo != kSkip)
+      refs[i] = expand_ref(r);
+    else
+      refs[i].klo = kSkip;
   }
   for (int i = tid; i < 2 * kFwdSB * L; i += nt) win[i] = 0;
 #pragma unroll
@@ -675,77 +775,54 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   const bool finite = __syncthreads_or(nonfinite) == 0;
   float xmax = 0.0f;
   for (int w = 0; w < (nt >> 5); ++w) xmax = fmaxf(xmax, s_max[w]);
-  // |pixel - sensor| >= d_ref - R for every pixel of the tile
-  const float hx = (float)(nvx - 1) * P.g.hdx, hy = (float)(nvy - 1) * P.g.hdy;
-  const float hz = (DIM == 3) ? (float)(nvz - 1) * P.g.hdz : 0.0f;
-  const float R = sqrtf(hx * hx + hy * hy + hz * hz) * 1.0001f;
   const float xscale = (xmax > 0.0f && finite) ? kFixedScale / xmax : 0.0f;
 #pragma unroll
-  for (int m = 0; m < PPT; ++m) xs[m] *= xscale;  // |xs| <= 2^20
-  const float inv_kappa = P.inv_kappa, hik = P.half_inv_kappa;
+  for (int h = 0; h < 2; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
+  const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
 
+  const uint32_t win_u32 = smem_u32(win);
   for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
     int* wb = win + buf * kFwdSB * L;
     const int nsb = min(kFwdSB, ns - g0);
     if (owner && xscale > 0.0f) {
-      for (int sb = 0; sb < nsb; ++sb) {
-        const TileRef r = refs[g0 + sb];
+      uint32_t base = magic_base(win_u32 + (uint32_t)(buf * kFwdSB * L + L / 2) * 4u, 2);
+#pragma unroll 1
+      for (int sb = 0; sb < nsb; ++sb, base += 4u * (uint32_t)L) {
+        const TileRef2 r = refs[g0 + sb];
         if (r.klo == kSkip) continue;
-        const float dlo = fmaxf(r.dref - R, P.half_hmin);
-        int* w = wb + sb * L;
-        if (r.flags & kNear) {
+        const float2 dlo = f2(r.dlo);
+        if (r.klo & kNear) {
 #pragma unroll
-          for (int m = 0; m < PPT; ++m) {
-            float rinv, e;
-            int idx;
-            time_of_flight<DIM, true>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
-                                      idx);
-            const float ws = (xs[m] * dlo) * rinv;
-            // rounded to integers: 0.5 ws to the magic grid first, then + -/+ ws e
-            const float hm = fmaf(ws, 0.5f, kMagic);
-            const int ia = __float_as_int(fmaf(-ws, e, hm)) - kMagicBits;  // x (1 - f) / d
-            const int ib = __float_as_int(fmaf(ws, e, hm)) - kMagicBits;   // x f / d
-            atomicAdd(w + idx, ia);
-            atomicAdd(w + idx + 1, ib);
-          }
+          for (int h = 0; h < 2; ++h)
+            fwd_pair2<DIM, true>(r, base, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
+                                 inv_kappa, hik);
         } else {
 #pragma unroll
-          for (int m = 0; m < PPT; ++m) {
-            float rinv, e;
-            int idx;
-            time_of_flight<DIM, false>(r, ddx[m], ddy[m], ddz[m], cm[m], inv_kappa, hik, rinv, e,
-                                       idx);
-            const float ws = (xs[m] * dlo) * rinv;
-            // rounded to integers: 0.5 ws to the magic grid first, then + -/+ ws e
-            const float hm = fmaf(ws, 0.5f, kMagic);
-            const int ia = __float_as_int(fmaf(-ws, e, hm)) - kMagicBits;  // x (1 - f) / d
-            const int ib = __float_as_int(fmaf(ws, e, hm)) - kMagicBits;   // x f / d
-            atomicAdd(w + idx, ia);
-            atomicAdd(w + idx + 1, ib);
-          }
+          for (int h = 0; h < 2; ++h)
+            fwd_pair2<DIM, false>(r, base, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
+                                  inv_kappa, hik);
         }
       }
     }
     __syncthreads();  // all taps of the stage are in the windows
-    // rescale factor of each sensor of the stage (0: nothing to store)
-    if (tid < kFwdSB) {
-      float u = 0.0f;
-      if (tid < nsb && refs[g0 + tid].klo != kSkip)
-        u = !finite ? __int_as_float(0x7fc00000)
-            : (xscale > 0.0f ? __fdividef(xmax, kFixedScale * fmaxf(refs[g0 + tid].dref - R,
-                                                                    P.half_hmin))
-                             : 0.0f);
-      s_unscale[tid] = u;
-      s_store[tid] = tid < nsb && refs[g0 + tid].klo != kSkip;
+    // warp w rescales sensor g0 + w's window to float, stores it and clears it
+    // for the stage after next (whose deposits follow the next stage's barrier)
+    if (warp < nsb) {
+      const int klo = refs[g0 + warp].klo;
+      if (klo != kSkip) {
+        const float u = !finite ? __int_as_float(0x7fc00000)
+                        : (xscale > 0.0f ? __fdividef(xmax, kFixedScale * refs[g0 + warp].dlo)
+                                         : 0.0f);
+        int4* src = reinterpret_cast<int4*>(wb + warp * L);
+        float4* dst = reinterpret_cast<float4*>(
+            P.part + ((int64_t)(s0 + g0 + warp) * P.ntiles + tile) * L);
+        for (int k4 = lane; k4 < L / 4; k4 += 32) {
+          const int4 v = src[k4];
+          dst[k4] = make_float4((float)v.x * u, (float)v.y * u, (float)v.z * u, (float)v.w * u);
+          src[k4] = make_int4(0, 0, 0, 0);
+        }
+      }
     }
-    __syncthreads();
-    for (int i = tid; i < nsb * L; i += nt) {
-      const int sb = i / L, k = i - sb * L;
-      if (s_store[sb])
-        P.part[((int64_t)(s0 + g0 + sb) * P.ntiles + tile) * L + k] = (float)wb[i] * s_unscale[sb];
-    }
-    __syncthreads();
-    for (int i = tid; i < kFwdSB * L; i += nt) wb[i] = 0;  // reused two stages later
   }
   __syncthreads();  // the block's shared memory is free for the next work item
 }

@@ -89,7 +89,7 @@ static pa_status build_table(pa_plan* p) {
     row.clear();
     for (int t = 0; t < p->ntiles; ++t) {
       const int k0 = klo[(size_t)t * p->S + s];
-      if (k0 != kSkip) row.push_back(make_int2(t, k0));
+      if (k0 != kSkip) row.push_back(make_int2(t, window_start(k0)));
     }
     std::sort(row.begin(), row.end(), [](const int2& a, const int2& b) {
       return a.y < b.y || (a.y == b.y && a.x < b.x);
@@ -494,7 +494,6 @@ FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode,
   f.amp = (float)p->amp;
   const double hmin = p->dim == 3 ? std::fmin(p->grid.dx, std::fmin(p->grid.dy, p->grid.dz))
                                   : std::fmin(p->grid.dx, p->grid.dy);
-  f.half_hmin = (float)(0.5 * hmin * (1.0 - 1e-6));
   f.mode = mode;
   f.out = out;
   f.y = y;
