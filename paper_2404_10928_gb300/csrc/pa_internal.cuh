@@ -169,6 +169,11 @@ static_assert(Tile<3>::X * Tile<3>::Y * Tile<3>::Z == kTilePixels, "tile");
 constexpr int kAdjWarps = 8;                 // compute warps (+1 producer warp)
 constexpr int kAdjThreads = 32 * (kAdjWarps + 1);
 constexpr int kAdjPPT = kTilePixels / (32 * kAdjWarps);  // pixels per compute thread
+// the persistent batch kernel runs every phase with one block size: the
+// forward's kFwdThreads pixel owners plus a warp; its adjoint phase uses eight
+// compute warps (four pixels per thread) and one producer warp
+constexpr int kBatchThreads = 288;
+constexpr int kBatchAdjWarps = 8;
 constexpr int kAdjSB = 8;                    // sensors per pipeline stage
 constexpr int kAdjStages = 4;
 

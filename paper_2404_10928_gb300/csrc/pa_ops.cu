@@ -290,8 +290,8 @@ __device__ __forceinline__ TileRef2 expand_ref(const TileRef& r) {
 // setup: per (tile, sensor) reference table, FP64
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void k_build_table(TileRef* __restrict__ table, int2* __restrict__ krange,
-                              const double* __restrict__ sensors, int S, int nx, int ny, int nz,
+__global__ void k_build_table(TileRef* table, int2* krange,
+                              const double* sensors, int S, int nx, int ny, int nz,
                               double dx, double dy, double dz, double ox, double oy, double oz,
                               int ntx, int nty, int ntz, double kappa, double t0fs, int K, int L,
                               double hmin, int* err) {
@@ -357,23 +357,39 @@ __global__ void k_build_table(TileRef* __restrict__ table, int2* __restrict__ kr
   }
 }
 
+// Launches `kernel` (as clusters of `cluster` CTAs along x when cluster > 0)
+// and returns the launch status.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     int cluster, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cluster > 0) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = cluster > 0 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const double* sensors_dev,
                                int S, const pa_grid& grid, const GridF& g, double kappa,
                                double t0fs, int K, int L, double hmin, int* err, cudaStream_t st) {
   const int64_t total = (int64_t)g.ntx * g.nty * g.ntz * S;
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 65535);
-  if (dim == 2)
-    k_build_table<2><<<blocks, threads, 0, st>>>(
-        table, krange, sensors_dev, S, grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz,
-        grid.origin[0], grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, kappa, t0fs, K, L,
-        hmin, err);
-  else
-    k_build_table<3><<<blocks, threads, 0, st>>>(
-        table, krange, sensors_dev, S, grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz,
-        grid.origin[0], grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, kappa, t0fs, K, L,
-        hmin, err);
-  return cudaGetLastError();
+  auto kernel = dim == 2 ? k_build_table<2> : k_build_table<3>;
+  return launch_k(kernel, dim3(blocks), dim3(threads), 0, st, 0, table, krange, sensors_dev, S,
+                  grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.origin[0],
+                  grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, kappa, t0fs, K, L, hmin,
+                  err);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +397,7 @@ cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const doub
 // mid = (r_k + r_{k+1})/2, slope = r_{k+1} - r_k, with r_{-1} = r_K = 0.
 // Linear interpolation at r_k + f (f in [0,1]) is then mid + (f - 1/2) slope.
 // ---------------------------------------------------------------------------
-__global__ void k_pack(const float* __restrict__ r, float2* __restrict__ packed, int S, int K,
+__global__ void k_pack(const float* r, float2* packed, int S, int K,
                        int Kp, int pad) {
   const int64_t row = K + 1;
   const int64_t total = (int64_t)S * row;
@@ -401,8 +417,7 @@ cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, in
   const int64_t total = (int64_t)S * (K + 1);
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 152 * 16);
-  k_pack<<<blocks, threads, 0, st>>>(r, packed, S, K, Kp, pad);
-  return cudaGetLastError();
+  return launch_k(k_pack, dim3(blocks), dim3(threads), 0, st, 0, r, packed, S, K, Kp, pad);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,11 +461,15 @@ __device__ __forceinline__ void adj_pair2(const TileRef2& r, uint32_t base, floa
 }
 
 // Accumulates, for every pixel of `tile`, the sum over sensors [s_begin, s_end)
-// into s_acc (shared, kTilePixels floats; returned).  Block of kAdjThreads
-// threads: warp kAdjWarps produces, warps 0..kAdjWarps-1 compute.
-template <int DIM, bool DC>
+// into s_acc (shared, kTilePixels floats; returned).  Warps 0..NW-1 compute
+// (kTilePixels / (32 NW) pixels per thread, as packed pairs), warp NW produces;
+// any further warps of the block only take part in the barriers.
+template <int DIM, bool DC, int NW>
 __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, int s_begin,
                                                  int s_end, unsigned char* smem) {
+  constexpr int PPT = kTilePixels / (32 * NW);
+  constexpr int NPAIR = PPT / 2;
+  static_assert(PPT % 2 == 0, "pixels are processed in pairs");
   const int L = P.L;
   float2* s_trace = reinterpret_cast<float2*>(smem);
   TileRef2* s_ref = reinterpret_cast<TileRef2*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
@@ -466,7 +485,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
   if (tid == 0) {
     for (int i = 0; i < kAdjStages; ++i) {
       mbar_init(&s_full[i], 1);
-      mbar_init(&s_empty[i], kAdjWarps);
+      mbar_init(&s_empty[i], NW);
     }
     s_abort = 0;
     s_issued = 0;
@@ -474,7 +493,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
   }
   __syncthreads();
 
-  if (warp == kAdjWarps) {
+  if (warp == NW) {
     // ----------------------------- producer warp -----------------------------
     int j = 0;
     for (; j < n_stages; ++j) {
@@ -517,20 +536,20 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
       if (bytes) bulk_g2s(s_trace + (slot * kAdjSB + lane) * L, src, bytes, &s_full[slot]);
     }
     if (lane == 0) s_issued = j;
-  } else {
+  } else if (warp < NW) {
     // ----------------------------- compute warps -----------------------------
-    // pixels tid + m * 256, m = 0..3, as packed pairs (m = 0, 1) and (2, 3)
-    float2 ddx[2], ddy[2], ddz[2], cm[2];
-    float acc[kAdjPPT];
+    // pixels tid + m * 32 NW, m = 0..PPT-1, as packed pairs (m = 2h, 2h + 1)
+    float2 ddx[NPAIR], ddy[NPAIR], ddz[NPAIR], cm[NPAIR];
+    float acc[PPT];
     const int ttx = tile % P.g.ntx, tty = (tile / P.g.ntx) % P.g.nty;
     const int ttz = tile / (P.g.ntx * P.g.nty);
     int nvx, nvy, nvz;
     tile_valid<DIM>(ttx, tty, ttz, P.g, nvx, nvy, nvz);
 #pragma unroll
-    for (int m = 0; m < kAdjPPT; ++m) {
+    for (int m = 0; m < PPT; ++m) {
       int lx, ly, lz;
       float ox, oy, oz, oc;
-      pixel_local<DIM>(tid + m * 32 * kAdjWarps, lx, ly, lz);
+      pixel_local<DIM>(tid + m * 32 * NW, lx, ly, lz);
       clamp_local<DIM>(ttx, tty, ttz, P.g, lx, ly, lz);
       pixel_offset<DIM>(lx, ly, lz, nvx, nvy, nvz, P.g, P.kappa, ox, oy, oz, oc);
       set_lane(ddx[m >> 1], m & 1, ox);
@@ -560,12 +579,12 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
         if (r.klo == kSkip) continue;
         if (r.klo & kNear) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < NPAIR; ++h)
             adj_pair2<DIM, true, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
                                      acc[2 * h], acc[2 * h + 1]);
         } else {
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < NPAIR; ++h)
             adj_pair2<DIM, false, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
                                       acc[2 * h], acc[2 * h + 1]);
         }
@@ -574,7 +593,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
       if (lane == 0) mbar_arrive(&s_empty[slot]);
     }
 #pragma unroll
-    for (int m = 0; m < kAdjPPT; ++m) s_acc[tid + m * 32 * kAdjWarps] = acc[m];
+    for (int m = 0; m < PPT; ++m) s_acc[tid + m * 32 * NW] = acc[m];
   }
   __syncthreads();
   if (tid == 0 && s_abort) {
@@ -601,7 +620,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   const int tid = threadIdx.x;
   const int s_begin = rank * P.sensors_per_rank;
   const int s_end = min(P.S, s_begin + P.sensors_per_rank);
-  float* s_acc = adj_accumulate<DIM, DC>(P, tile, s_begin, s_end, smem);
+  float* s_acc = adj_accumulate<DIM, DC, kAdjWarps>(P, tile, s_begin, s_end, smem);
 
   cluster.sync();
   // --------------- cluster reduction in rank order + epilogue ---------------
@@ -639,29 +658,11 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
 }
 
 cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st) {
-  const int smem = adjoint_smem_bytes(p.L);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster, ntiles, 1);
-  cfg.blockDim = dim3(kAdjThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e;
   const bool dc = p.mode == ADJ_DC;
-  if (dim == 2)
-    e = dc ? cudaLaunchKernelEx(&cfg, k_adjoint<2, true>, p)
-           : cudaLaunchKernelEx(&cfg, k_adjoint<2, false>, p);
-  else
-    e = dc ? cudaLaunchKernelEx(&cfg, k_adjoint<3, true>, p)
-           : cudaLaunchKernelEx(&cfg, k_adjoint<3, false>, p);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  auto kernel = dim == 2 ? (dc ? k_adjoint<2, true> : k_adjoint<2, false>)
+                         : (dc ? k_adjoint<3, true> : k_adjoint<3, false>);
+  return launch_k(kernel, dim3(cluster, ntiles, 1), dim3(kAdjThreads), adjoint_smem_bytes(p.L), st,
+                  cluster, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -891,20 +892,14 @@ int forward_combine_blocks(int S, int K) { return S * ((K + kCombThreads - 1) / 
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
   const int smem = forward_smem_bytes(p.L, p.spc);
   dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, 1);
-  if (dim == 2)
-    k_fwd_tile<2><<<grid1, kFwdThreads, smem, st>>>(p);
-  else
-    k_fwd_tile<3><<<grid1, kFwdThreads, smem, st>>>(p);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = launch_k(dim == 2 ? k_fwd_tile<2> : k_fwd_tile<3>, grid1,
+                                 dim3(kFwdThreads), smem, st, 0, p);
   if (e != cudaSuccess) return e;
-  dim3 grid2((p.K + kCombThreads - 1) / kCombThreads, p.S, 1);
-  if (p.mode == FWD_RESID)
-    k_fwd_combine<FWD_RESID><<<grid2, kCombThreads, 0, st>>>(p);
-  else if (p.mode == FWD_NORM)
-    k_fwd_combine<FWD_NORM><<<grid2, kCombThreads, 0, st>>>(p);
-  else
-    k_fwd_combine<FWD_STORE><<<grid2, kCombThreads, 0, st>>>(p);
-  return cudaGetLastError();
+  const dim3 grid2((p.K + kCombThreads - 1) / kCombThreads, p.S, 1);
+  auto combine = p.mode == FWD_RESID ? k_fwd_combine<FWD_RESID>
+                 : p.mode == FWD_NORM ? k_fwd_combine<FWD_NORM>
+                                      : k_fwd_combine<FWD_STORE>;
+  return launch_k(combine, grid2, dim3(kCombThreads), 0, st, 0, p);
 }
 
 // Raise the dynamic shared-memory limit of the gather kernels (called when a
@@ -937,9 +932,9 @@ constexpr int kVecThreads = 256;
 // CGLS: x += alpha p (first nblk_x blocks); r_out = r_in - alpha q, packed
 // residual and FP64 partials of ||r_out||^2 (remaining blocks, one partial each).
 __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
-    float* __restrict__ x, const float* __restrict__ pv, const float* __restrict__ r_in,
-    float* __restrict__ r_out, const float* __restrict__ q, float2* __restrict__ packed,
-    const double* __restrict__ alpha_p, int N, int S, int K, int Kp, int pad, const Reduce red,
+    float* x, const float* pv, const float* r_in,
+    float* r_out, const float* q, float2* packed,
+    const double* alpha_p, int N, int S, int K, int Kp, int pad, const Reduce red,
     int nblk_x) {
   __shared__ double s_red[kVecThreads / 32];
   const float alpha = (float)(*alpha_p);
@@ -971,34 +966,35 @@ cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float
                            const float* q, float2* packed, const double* alpha, int N, int S,
                            int K, int Kp, int pad, const Reduce& red, int nblk_x, int nblk_r,
                            cudaStream_t st) {
-  k_cgls_xr<<<nblk_x + nblk_r, kVecThreads, 0, st>>>(x, pvec, r_in, r_out, q, packed, alpha, N, S,
-                                                     K, Kp, pad, red, nblk_x);
-  return cudaGetLastError();
+  return launch_k(k_cgls_xr, dim3(nblk_x + nblk_r), dim3(kVecThreads), 0, st, 0, x, pvec, r_in,
+                  r_out, q, packed, alpha, N, S, K, Kp, pad, red, nblk_x);
 }
 
-__global__ void k_scale(float* __restrict__ v, const float* __restrict__ w,
-                        const double* __restrict__ f_p, int N) {
+__global__ void k_scale(float* v, const float* w,
+                        const double* f_p, int N) {
   const float f = (float)(*f_p);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
     v[i] = w[i] * f;
 }
 
-__global__ void k_clamp(float* __restrict__ x, int N) {
+__global__ void k_clamp(float* x, int N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = fmaxf(x[i], 0.0f);
 }
 
-__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+__global__ void k_set_scalar(double* dst, double v) {
+  *dst = v;
+}
 
-__global__ void k_fill(float* __restrict__ dst, float v, int64_t n) {
+__global__ void k_fill(float* dst, float v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = v;
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_norm(const float* __restrict__ v, int64_t n,
+__global__ void __launch_bounds__(kVecThreads) k_norm(const float* v, int64_t n,
                                                       const Reduce red) {
   __shared__ double s_red[kVecThreads / 32];
   double part = 0.0;
@@ -1015,24 +1011,19 @@ static int vec_blocks(int64_t n) {
 
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st) {
-  k_scale<<<vec_blocks(N), kVecThreads, 0, st>>>(v, w, factor, N);
-  return cudaGetLastError();
+  return launch_k(k_scale, dim3(vec_blocks(N)), dim3(kVecThreads), 0, st, 0, v, w, factor, N);
 }
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st) {
-  k_clamp<<<vec_blocks(N), kVecThreads, 0, st>>>(x, N);
-  return cudaGetLastError();
+  return launch_k(k_clamp, dim3(vec_blocks(N)), dim3(kVecThreads), 0, st, 0, x, N);
 }
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st) {
-  k_set_scalar<<<1, 1, 0, st>>>(dst, value);
-  return cudaGetLastError();
+  return launch_k(k_set_scalar, dim3(1), dim3(1), 0, st, 0, dst, value);
 }
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
-  k_fill<<<vec_blocks(n), kVecThreads, 0, st>>>(dst, value, n);
-  return cudaGetLastError();
+  return launch_k(k_fill, dim3(vec_blocks(n)), dim3(kVecThreads), 0, st, 0, dst, value, n);
 }
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st) {
-  k_norm<<<nblk, kVecThreads, 0, st>>>(v, n, red);
-  return cudaGetLastError();
+  return launch_k(k_norm, dim3(nblk), dim3(kVecThreads), 0, st, 0, v, n, red);
 }
 
 
@@ -1045,7 +1036,7 @@ cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, 
 // reduced in FP64 inside the kernel.
 // ---------------------------------------------------------------------------
 template <int DIM>
-__device__ __forceinline__ void tv_terms(const float* __restrict__ x, int i, int j, int l, int nx,
+__device__ __forceinline__ void tv_terms(const float* x, int i, int j, int l, int nx,
                                          int ny, int nz, float eps2, float& ax, float& ay,
                                          float& az, float& m) {
   const int64_t o = ((int64_t)l * ny + j) * nx + i;
@@ -1061,8 +1052,8 @@ __device__ __forceinline__ void tv_terms(const float* __restrict__ x, int i, int
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kVecThreads) k_tv(const float* __restrict__ x, int nx, int ny,
-                                                    int nz, float eps, float* __restrict__ grad,
+__global__ void __launch_bounds__(kVecThreads) k_tv(const float* x, int nx, int ny,
+                                                    int nz, float eps, float* grad,
                                                     const Reduce red) {
   __shared__ double s_red[kVecThreads / 32];
   const float eps2 = eps * eps;
@@ -1101,11 +1092,8 @@ int tv_blocks(int64_t n) {
 cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
                       const Reduce& red, cudaStream_t st) {
   const int nb = tv_blocks((int64_t)nx * ny * nz);
-  if (dim == 2)
-    k_tv<2><<<nb, kVecThreads, 0, st>>>(x, nx, ny, nz, eps, grad, red);
-  else
-    k_tv<3><<<nb, kVecThreads, 0, st>>>(x, nx, ny, nz, eps, grad, red);
-  return cudaGetLastError();
+  return launch_k(dim == 2 ? k_tv<2> : k_tv<3>, dim3(nb), dim3(kVecThreads), 0, st, 0, x, nx, ny,
+                  nz, eps, grad, red);
 }
 
 
@@ -1170,7 +1158,7 @@ template <int DIM>
 __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile,
                                                     unsigned char* smem) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
-  float* s_acc = adj_accumulate<DIM, false>(P, tile, 0, P.S, smem);
+  float* s_acc = adj_accumulate<DIM, false, kBatchAdjWarps>(P, tile, 0, P.S, smem);
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
   const float om = (float)(*P.omega);
   for (int p = threadIdx.x; p < kTilePixels; p += blockDim.x) {
@@ -1188,7 +1176,7 @@ __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kAdjThreads) k_batch_landweber(
+__global__ void __launch_bounds__(kBatchThreads) k_batch_landweber(
     const BatchFrame* __restrict__ frames, int nf, const int* __restrict__ pre, int n_iter,
     unsigned* state, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1245,13 +1233,13 @@ cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm) {
                              (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_landweber<2>,
-                                                         kAdjThreads, smem);
+                                                         kBatchThreads, smem);
   }
   e = cudaFuncSetAttribute(k_batch_landweber<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_landweber<3>,
-                                                       kAdjThreads, smem);
+                                                       kBatchThreads, smem);
 }
 
 cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_frames, const int* pre,
@@ -1261,9 +1249,9 @@ cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_fram
                   (void*)&err};
   if (dim == 2)
     return cudaLaunchCooperativeKernel((const void*)k_batch_landweber<2>, dim3(grid),
-                                       dim3(kAdjThreads), args, smem, st);
+                                       dim3(kBatchThreads), args, smem, st);
   return cudaLaunchCooperativeKernel((const void*)k_batch_landweber<3>, dim3(grid),
-                                     dim3(kAdjThreads), args, smem, st);
+                                     dim3(kBatchThreads), args, smem, st);
 }
 
 }  // namespace pa
