@@ -81,13 +81,13 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
   b->plans.assign(plans, plans + n_frames);
   Guard guard(b->device);
   // item counts per frame: forward (tile x sensor chunk), combine (sensor x
-  // sample block of kBatchThreads), adjoint (tile)
+  // block of 4 kBatchThreads samples), adjoint (tile)
   std::vector<int> pre(3 * (n_frames + 1), 0);
   int Lmax = 0, spc_max = 0;
   for (int f = 0; f < n_frames; ++f) {
     const pa_plan* p = plans[f];
     const int chunks = (p->S + p->fwd_spc - 1) / p->fwd_spc;
-    const int nk = (p->K + kBatchThreads - 1) / kBatchThreads;
+    const int nk = combine_kblocks(p->K, kBatchThreads, 4);
     pre[f + 1] = pre[f] + p->ntiles * chunks;
     pre[(n_frames + 1) + f + 1] = pre[(n_frames + 1) + f] + p->S * nk;
     pre[2 * (n_frames + 1) + f + 1] = pre[2 * (n_frames + 1) + f] + p->ntiles;
@@ -169,7 +169,7 @@ pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
     F.f.red = make_reduce(p, OP_SUM, nullptr, nullptr, nullptr);
     F.a = adjoint_params(p, x_dev[f], ADJ_LANDWEBER, b->d_omega + f, nonneg);
     F.fwd_chunks = (p->S + p->fwd_spc - 1) / p->fwd_spc;
-    F.n_kblk = (p->K + kBatchThreads - 1) / kBatchThreads;
+    F.n_kblk = combine_kblocks(p->K, kBatchThreads, 4);
     F.hist = b->d_hist + (size_t)f * (n_iter + 1);
   }
   // the graph is valid while the descriptors, the steps and n_iter stay the same

@@ -56,8 +56,8 @@ constexpr int kSkip = INT_MIN;
 // FP32 position within the window carries at most L/2 in magnitude.
 // ---------------------------------------------------------------------------
 struct __align__(16) TileRef {
-  int klo;      // first sample of the staged window (even) | kNear, or kSkip
-  float fref;   // u_ref - (klo & ~1) - 0.5 - L/2
+  int klo;      // first sample of the staged window (a multiple of 4) | kNear, or kSkip
+  float fref;   // u_ref - window_start(klo) - 0.5 - L/2
   float dref;   // |centre - sensor|
   float dref2;  // d_ref^2
   float ex2k;   // 2*kappa*(centre - sensor).x
@@ -132,6 +132,7 @@ struct FwdParams {
   const int* upper;       // [S][K + L]: at k + L, how many sorted tiles have klo <= k
   int S, K, L, ntiles;
   int spc;                // sensors per forward tile work item
+  int comb_spt;           // samples per combine thread: 4, or 1 when many windows cover a sample
   GridF g;
   float kappa, inv_kappa, half_inv_kappa, amp;
   int mode;
@@ -196,14 +197,20 @@ cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
 int adjoint_smem_bytes(int L);
 cudaError_t configure_kernels(int smem_adj, int smem_fwd);
 int forward_smem_bytes(int L, int spc);
-int forward_combine_blocks(int S, int K);
+int forward_combine_blocks(int S, int K, int spt);
+// sample blocks per sensor of the combine (and of the CGLS r update) when each
+// thread forms spt consecutive samples
+__host__ __device__ inline int combine_kblocks(int K, int threads, int spt) {
+  return (K + spt * threads - 1) / (spt * threads);
+}
 pa_status validate_grid(const pa_grid* g);
 
 // reductions and vector updates
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const double* alpha, int N, int S,
-                           int K, int Kp, int pad, const Reduce& red, int nblk_x, int nblk_r,
+                           int K, int Kp, int pad, const Reduce& red, int nblk_x,
                            cudaStream_t st);
+int cgls_r_blocks(int S, int K);
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
@@ -240,6 +247,7 @@ struct pa_plan {
   int Kp = 0;       // packed row length (even)
   int cluster = 1;  // adjoint CTAs per tile
   int fwd_spc = 32; // sensors per forward tile work item
+  int comb_spt = 4; // samples per combine thread (1 when many windows cover a sample)
 
   // device memory owned by the plan
   double* d_sensors = nullptr;

@@ -346,7 +346,7 @@ __global__ void k_build_table(TileRef* table, int2* krange,
       kr = make_int2(kSkip, kSkip);
     } else {
       long long kl = (long long)k0min - 2;
-      kl = kl & ~1LL;  // round down to even (16-byte aligned float2 window)
+      kl = kl & ~3LL;  // a multiple of 4: aligned float2 windows and 4-sample combine groups
       if ((long long)k0max - kl + 1 > (long long)L - 2) atomicOr(err, ERR_WINDOW);
       r.klo = (int)kl | near;
       r.fref = (float)(uref - (double)kl - 0.5 - 0.5 * (double)L);
@@ -397,27 +397,31 @@ cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const doub
 // mid = (r_k + r_{k+1})/2, slope = r_{k+1} - r_k, with r_{-1} = r_K = 0.
 // Linear interpolation at r_k + f (f in [0,1]) is then mid + (f - 1/2) slope.
 // ---------------------------------------------------------------------------
-__global__ void k_pack(const float* r, float2* packed, int S, int K,
-                       int Kp, int pad) {
-  const int64_t row = K + 1;
-  const int64_t total = (int64_t)S * row;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int s = (int)(idx / row);
-    const int k = (int)(idx % row) - 1;
-    const float* rs = r + (int64_t)s * K;
-    const float a = (k >= 0) ? rs[k] : 0.0f;
-    const float b = (k + 1 < K) ? rs[k + 1] : 0.0f;
-    packed[(int64_t)s * Kp + pad + k] = make_float2(0.5f * (a + b), b - a);
+__global__ void k_pack(const float* r, float2* packed, int S, int K, int Kp, int pad) {
+  // blockIdx.y = sensor; thread: entries k = k4 - 1 .. k4 + 2 of the row, k4 = 4 * index
+  const int s = blockIdx.y;
+  const int k4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (k4 > K) return;  // entries k in [-1, K)
+  const float* rs = r + (int64_t)s * K;
+  float2* row = packed + (int64_t)s * Kp + pad;
+  float v[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int k = k4 - 1 + j;  // r_{-1} = r_K = 0
+    v[j] = (k >= 0 && k < K) ? rs[k] : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = k4 - 1 + j;
+    if (k < K) row[k] = make_float2(0.5f * (v[j] + v[j + 1]), v[j + 1] - v[j]);
   }
 }
 
 cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
                         cudaStream_t st) {
-  const int64_t total = (int64_t)S * (K + 1);
   const int threads = 256;
-  const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 152 * 16);
-  return launch_k(k_pack, dim3(blocks), dim3(threads), 0, st, 0, r, packed, S, K, Kp, pad);
+  const dim3 grid((K + 1 + 4 * threads - 1) / (4 * threads), S, 1);
+  return launch_k(k_pack, grid, dim3(threads), 0, st, 0, r, packed, S, K, Kp, pad);
 }
 
 // ---------------------------------------------------------------------------
@@ -834,47 +838,73 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
   fwd_tile_block<DIM>(P, blockIdx.y, blockIdx.x, smem);
 }
 
-// One (sensor, block of blockDim samples) work item of the combine; nkblk =
-// sample blocks per sensor (for the in-kernel reduction's slot numbering).
-template <int MODE>
+// One (sensor, block of SPT blockDim samples) work item of the combine: p[s,k]
+// = sum of the windows covering k, taken in the sensor's sorted (by start)
+// order, which are the windows starting in (k - L, k].  SPT = 4: each thread
+// forms four consecutive samples k..k+3 (k a multiple of 4); window starts are
+// multiples of 4 and L a multiple of 16, so a window covers all four samples
+// or none and its slice is one aligned 16-byte load.  SPT = 1: one sample per
+// thread, so the 32 lanes of a warp span fewer samples than a window and read
+// the same windows (coalesced) — the better choice when many windows cover
+// each sample (large 3D grids).  nkblk = sample blocks per sensor (for the
+// in-kernel reduction's slot numbering).
+template <int MODE, int SPT>
 __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kblk, int nkblk) {
+  static_assert(SPT == 1 || SPT == 4, "1 or 4 samples per thread");
   __shared__ double s_red[32];
-  const int k = kblk * blockDim.x + threadIdx.x;
+  const int k = SPT * (kblk * blockDim.x + threadIdx.x);
   double part = 0.0;
   if (k < P.K) {
     const int* up = P.upper + (int64_t)s * (P.K + P.L);
     const int i0 = up[k], i1 = up[k + P.L];  // windows starting in (k - L, k]
     const int2* srt = P.sorted + (int64_t)s * P.ntiles;
     const float* ps = P.part + (int64_t)s * P.ntiles * P.L;
-    float v = 0.0f;
+    float v[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) v[j] = 0.0f;
+    auto add = [&](int2 a) {
+      const float* src = ps + (int64_t)a.x * P.L + (k - a.y);
+      if (SPT == 4) {
+        const float4 w = __ldcg(reinterpret_cast<const float4*>(src));
+        v[0] += w.x;
+        v[SPT > 1 ? 1 : 0] += w.y;
+        v[SPT > 2 ? 2 : 0] += w.z;
+        v[SPT > 3 ? 3 : 0] += w.w;
+      } else {
+        v[0] += __ldcg(src);
+      }
+    };
     int i = i0;
     for (; i + 4 <= i1; i += 4) {  // four independent loads in flight, summed in order
       const int2 a = srt[i], b = srt[i + 1], c = srt[i + 2], d = srt[i + 3];
-      const float va = __ldcg(ps + (int64_t)a.x * P.L + (k - a.y));
-      const float vb = __ldcg(ps + (int64_t)b.x * P.L + (k - b.y));
-      const float vc = __ldcg(ps + (int64_t)c.x * P.L + (k - c.y));
-      const float vd = __ldcg(ps + (int64_t)d.x * P.L + (k - d.y));
-      v += va;
-      v += vb;
-      v += vc;
-      v += vd;
+      add(a);
+      add(b);
+      add(c);
+      add(d);
     }
-    for (; i < i1; ++i) {
-      const int2 a = srt[i];
-      v += __ldcg(ps + (int64_t)a.x * P.L + (k - a.y));
-    }
-    v *= P.amp;
+    for (; i < i1; ++i) add(srt[i]);
     const int64_t o = (int64_t)s * P.K + k;
-    if (MODE == FWD_RESID) {
-      const float y = P.y_f16 ? __half2float(reinterpret_cast<const __half*>(P.y)[o])
-                              : reinterpret_cast<const float*>(P.y)[o];
-      const float rr = y - v;
-      P.out[o] = rr;
-      part = (double)rr * (double)rr;
-    } else {
-      P.out[o] = v;
-      part = (double)v * (double)v;
+    const int n = min(SPT, P.K - k);
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+      v[j] *= P.amp;
+      if (MODE == FWD_RESID && j < n) {
+        const float y = P.y_f16 ? __half2float(reinterpret_cast<const __half*>(P.y)[o + j])
+                                : reinterpret_cast<const float*>(P.y)[o + j];
+        v[j] = y - v[j];
+      }
     }
+    if (SPT == 4 && n == 4 && (P.K & 3) == 0) {
+      *reinterpret_cast<float4*>(P.out + o) =
+          make_float4(v[0], v[SPT > 1 ? 1 : 0], v[SPT > 2 ? 2 : 0], v[SPT > 3 ? 3 : 0]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < SPT; ++j)
+        if (j < n) P.out[o + j] = v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < SPT; ++j)
+      if (j < n) part += (double)v[j] * (double)v[j];
   }
   if (MODE != FWD_STORE) {
     const double t = block_sum(part, s_red, blockDim.x >> 5);
@@ -882,12 +912,12 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
   }
 }
 
-template <int MODE>
+template <int MODE, int SPT>
 __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P) {
-  combine_block<MODE>(P, blockIdx.y, blockIdx.x, gridDim.x);
+  combine_block<MODE, SPT>(P, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
-int forward_combine_blocks(int S, int K) { return S * ((K + kCombThreads - 1) / kCombThreads); }
+int forward_combine_blocks(int S, int K, int spt) { return S * combine_kblocks(K, kCombThreads, spt); }
 
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
   const int smem = forward_smem_bytes(p.L, p.spc);
@@ -895,10 +925,14 @@ cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
   const cudaError_t e = launch_k(dim == 2 ? k_fwd_tile<2> : k_fwd_tile<3>, grid1,
                                  dim3(kFwdThreads), smem, st, 0, p);
   if (e != cudaSuccess) return e;
-  const dim3 grid2((p.K + kCombThreads - 1) / kCombThreads, p.S, 1);
-  auto combine = p.mode == FWD_RESID ? k_fwd_combine<FWD_RESID>
-                 : p.mode == FWD_NORM ? k_fwd_combine<FWD_NORM>
-                                      : k_fwd_combine<FWD_STORE>;
+  const dim3 grid2(combine_kblocks(p.K, kCombThreads, p.comb_spt), p.S, 1);
+  auto combine = p.comb_spt == 4
+                     ? (p.mode == FWD_RESID ? k_fwd_combine<FWD_RESID, 4>
+                        : p.mode == FWD_NORM ? k_fwd_combine<FWD_NORM, 4>
+                                             : k_fwd_combine<FWD_STORE, 4>)
+                     : (p.mode == FWD_RESID ? k_fwd_combine<FWD_RESID, 1>
+                        : p.mode == FWD_NORM ? k_fwd_combine<FWD_NORM, 1>
+                                             : k_fwd_combine<FWD_STORE, 1>);
   return launch_k(combine, grid2, dim3(kCombThreads), 0, st, 0, p);
 }
 
@@ -930,7 +964,9 @@ cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
 constexpr int kVecThreads = 256;
 
 // CGLS: x += alpha p (first nblk_x blocks); r_out = r_in - alpha q, packed
-// residual and FP64 partials of ||r_out||^2 (remaining blocks, one partial each).
+// residual and FP64 partials of ||r_out||^2 (the remaining blocks: one partial
+// each, blockIdx.x - nblk_x = s * kblocks + sample block, four consecutive
+// samples per thread).
 __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     float* x, const float* pv, const float* r_in,
     float* r_out, const float* q, float2* packed,
@@ -944,30 +980,50 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
       x[i] = fmaf(alpha, pv[i], x[i]);
     return;
   }
+  const int kb = combine_kblocks(K, kVecThreads, 4);
   const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
-  const int64_t total = (int64_t)S * K;
+  const int s = b / kb;
+  const int k = 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
   double part = 0.0;
-  for (int64_t o = b * (int64_t)kVecThreads + threadIdx.x; o < total;
-       o += (int64_t)nb * kVecThreads) {
-    const int s = (int)(o / K), k = (int)(o % K);
-    const float rk = fmaf(-alpha, q[o], r_in[o]);
-    const float rn = (k + 1 < K) ? fmaf(-alpha, q[o + 1], r_in[o + 1]) : 0.0f;
-    r_out[o] = rk;
-    float2* row = packed + (int64_t)s * Kp + pad;
-    row[k] = make_float2(0.5f * (rk + rn), rn - rk);
-    if (k == 0) row[-1] = make_float2(0.5f * rk, rk);
-    part += (double)rk * (double)rk;
+  if (k < K) {
+    const int64_t o = (int64_t)s * K + k;
+    const int n = min(4, K - k);
+    float rk[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)  // rk[4] = the next group's first sample (0 past the row)
+      rk[j] = (j <= n && k + j < K) ? fmaf(-alpha, q[o + j], r_in[o + j]) : 0.0f;
+    float2* row = packed + (int64_t)s * Kp + pad + k;
+    if (n == 4 && (K & 3) == 0) {
+      *reinterpret_cast<float4*>(r_out + o) = make_float4(rk[0], rk[1], rk[2], rk[3]);
+      // (pad + k) and Kp are even: two 16-byte stores of two (mid, slope) each
+      reinterpret_cast<float4*>(row)[0] =
+          make_float4(0.5f * (rk[0] + rk[1]), rk[1] - rk[0], 0.5f * (rk[1] + rk[2]), rk[2] - rk[1]);
+      reinterpret_cast<float4*>(row)[1] =
+          make_float4(0.5f * (rk[2] + rk[3]), rk[3] - rk[2], 0.5f * (rk[3] + rk[4]), rk[4] - rk[3]);
+    } else {
+      for (int j = 0; j < n; ++j) {
+        r_out[o + j] = rk[j];
+        row[j] = make_float2(0.5f * (rk[j] + rk[j + 1]), rk[j + 1] - rk[j]);
+      }
+    }
+    if (k == 0) row[-1] = make_float2(0.5f * rk[0], rk[0]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < n) part += (double)rk[j] * (double)rk[j];
   }
   const double t = block_sum<kVecThreads / 32>(part, s_red);
   reduce_across_ctas<kVecThreads / 32>(red, t, b, nb, s_red);
 }
 
+// number of r blocks of k_cgls_xr for S x K traces
+int cgls_r_blocks(int S, int K) { return S * combine_kblocks(K, kVecThreads, 4); }
+
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const double* alpha, int N, int S,
-                           int K, int Kp, int pad, const Reduce& red, int nblk_x, int nblk_r,
+                           int K, int Kp, int pad, const Reduce& red, int nblk_x,
                            cudaStream_t st) {
-  return launch_k(k_cgls_xr, dim3(nblk_x + nblk_r), dim3(kVecThreads), 0, st, 0, x, pvec, r_in,
-                  r_out, q, packed, alpha, N, S, K, Kp, pad, red, nblk_x);
+  return launch_k(k_cgls_xr, dim3(nblk_x + cgls_r_blocks(S, K)), dim3(kVecThreads), 0, st, 0, x,
+                  pvec, r_in, r_out, q, packed, alpha, N, S, K, Kp, pad, red, nblk_x);
 }
 
 __global__ void k_scale(float* v, const float* w,
@@ -1198,7 +1254,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_landweber(
       FwdParams P = frames[f].f;
       P.red.out_sum = frames[f].hist + it;
       const int nk = frames[f].n_kblk;
-      combine_block<FWD_RESID>(P, li / nk, li % nk, nk);
+      combine_block<FWD_RESID, 4>(P, li / nk, li % nk, nk);
     }
     grid_barrier(state, nb, err, state + 3);
     if (it == n_iter) break;

@@ -326,6 +326,10 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     p->cluster = C;
     if (opts && opts->adj_cluster > 0) p->cluster = std::min(opts->adj_cluster, p->S);
     if (opts && opts->fwd_sensors_per_cta > 0) p->fwd_spc = opts->fwd_sensors_per_cta;
+    // the 4-sample combine reads 16-byte window slices per lane, and its warps span
+    // 128 samples; once more than 16 windows cover a sample on average, lanes of a
+    // warp mostly read different windows and one sample per lane (coalesced) wins
+    p->comb_spt = (int64_t)p->ntiles * p->L <= 16 * (int64_t)p->K ? 4 : 1;
   }
   const size_t smem_adj = (size_t)adjoint_smem_bytes(p->L);
   if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->L, p->fwd_spc) > 200 * 1024) {
@@ -355,7 +359,8 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   const size_t n_pix = (size_t)grid->nx * grid->ny * grid->nz;
   const size_t n_tr = (size_t)p->S * p->K;
   p->n_partials = (int)std::max<int64_t>(
-      {(int64_t)p->ntiles * p->cluster, (int64_t)forward_combine_blocks(p->S, p->K), 152 * 8, 1});
+      {(int64_t)p->ntiles * p->cluster, (int64_t)forward_combine_blocks(p->S, p->K, 1),
+       (int64_t)cgls_r_blocks(p->S, p->K), 152 * 8, 1});
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaStreamCreate failed");
@@ -487,6 +492,7 @@ FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode,
   f.L = p->L;
   f.ntiles = p->ntiles;
   f.spc = p->fwd_spc;
+  f.comb_spt = p->comb_spt;
   f.g = p->g;
   f.kappa = (float)(p->fs / p->c);
   f.inv_kappa = (float)(p->c / p->fs);

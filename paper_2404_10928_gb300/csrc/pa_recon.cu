@@ -191,8 +191,7 @@ pa_status enqueue_landweber(pa_plan* p, int n_iter, const void* y, float* x,
 pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa_recon_opts& o,
                        const Scalars& sc, Timing& t, cudaStream_t st) {
   const int N = p->grid.nx * p->grid.ny * p->grid.nz;
-  const int64_t SK = (int64_t)p->S * p->K;
-  const int nbx = vec_blocks_x(N), nbr = vec_blocks_r(SK);
+  const int nbx = vec_blocks_x(N);
   float* r_in = p->d_ra;
   float* r_out = p->d_rb;
   float* p_cur = p->d_pv;
@@ -219,8 +218,7 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
     // x += alpha p; r -= alpha q (packed for the adjoint); ||r||^2
     PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, sc.alpha + it, N, p->S,
                            p->K, p->Kp, p->pad,
-                           make_reduce(p, OP_SUM, sc.hist + it + 1, nullptr, nullptr), nbx, nbr,
-                           st));
+                           make_reduce(p, OP_SUM, sc.hist + it + 1, nullptr, nullptr), nbx, st));
     // s = A^T r; beta = ||s||^2 / gamma
     PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0,
                make_reduce(p, OP_BETA, sc.gamma + it + 1, sc.gamma + it, sc.beta + it), t, st));
