@@ -99,7 +99,7 @@ enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
 // stores its partial, the last CTA to arrive (decided by a counter) sums all
 // partials in index order and applies `op`.  Disabled when partials == nullptr.
 struct Reduce {
-  double* partials;      // one slot per CTA
+  float2* partials;      // one slot per CTA: a double-float (hi, lo) partial
   unsigned* counter;     // 0 before the launch; the last CTA resets it
   int op;                // ScalarOp
   double* out_sum;       // nullable

@@ -117,44 +117,85 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Deterministic FP64 block sum: xor-tree within warps, warps in index order.
-// nw = warps in the block; the result is valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* s_red, int nw) {
+// ---------------------------------------------------------------------------
+// Reductions in double-float arithmetic (an unevaluated FP32 pair hi + lo,
+// Dekker 1971; TwoSum of Knuth, TAOCP vol. 2, Sec. 4.2.2).  GB300's FP64 pipe
+// runs at 1/64 of the FP32 rate (about 64 cycles per warp instruction), so a
+// reduction carried in FP64 stalls the short kernels that finish one.  A pair
+// of FP32 numbers holds ~48 significant bits: every product is split exactly
+// (v*v = p + fma(v, v, -p)) and every addition keeps its rounding error, so a
+// sum keeps a relative error of order n * 2^-44 of the sum of the magnitudes of
+// its terms -- the accuracy class of an FP64 accumulation of FP32 products.  Only
+// the finished total is converted to FP64.  All operations use the _rn
+// intrinsics so that no FMA contraction breaks the error-free transforms, and
+// sums run in a fixed order (bitwise reproducible).
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_zero() { return DF{0.0f, 0.0f}; }
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));  // exact
+  const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, lo);
+  return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ DF df_prod(float a, float b) {  // a*b exactly, as hi + lo
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_sq(float v) { return df_prod(v, v); }
+__device__ __forceinline__ DF df_of(float v) { return DF{v, 0.0f}; }
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
+  return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// Deterministic block sum: xor-tree within warps, warps in index order.
+// nw = warps in the block; s_red holds >= nw pairs; the result is valid in
+// thread 0.
+__device__ __forceinline__ DF block_sum(DF v, DF* s_red, int nw) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
   if (lane == 0) s_red[warp] = v;
   __syncthreads();
-  double t = 0.0;
+  DF t = df_zero();
   if (threadIdx.x == 0)
-    for (int w = 0; w < nw; ++w) t += s_red[w];
+    for (int w = 0; w < nw; ++w) t = df_add(t, s_red[w]);
   __syncthreads();
   return t;
 }
 template <int NW>
-__device__ __forceinline__ double block_sum(double v, double* s_red) {
+__device__ __forceinline__ DF block_sum(DF v, DF* s_red) {
   return block_sum(v, s_red, NW);
 }
 
 // Finishes a Reduce inside the producing kernel (see Reduce).  `part` is the
 // CTA's partial, valid in thread 0; all threads of the CTA must call this.
 // bid / nblk: this CTA's slot and the number of CTAs (work items) reducing.
-__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part, int bid, int nblk,
-                                                   double* s_red) {
+__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, DF part, int bid, int nblk,
+                                                   DF* s_red) {
   __shared__ int s_last;
   const int nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
-    R.partials[bid] = part;
+    R.partials[bid] = make_float2(part.hi, part.lo);
     __threadfence();
     s_last = atomicAdd(R.counter, 1u) == (unsigned)nblk - 1u;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += __ldcg(R.partials + i);
-  const double t = block_sum(v, s_red, nw);
+  DF v = df_zero();
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    const float2 q = __ldcg(R.partials + i);
+    v = df_add(v, DF{q.x, q.y});
+  }
+  const DF tdf = block_sum(v, s_red, nw);
   if (threadIdx.x == 0) {
+    const double t = df_to_double(tdf);
     if (R.out_sum) *R.out_sum = R.post_scale != 0.0 ? t * R.post_scale : t;
     switch (R.op) {
       case OP_ALPHA:  // alpha = gamma / ||q||^2
@@ -174,8 +215,8 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part,
   __syncthreads();
 }
 template <int NW>
-__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part, int bid, int nblk,
-                                                   double* s_red) {
+__device__ __forceinline__ void reduce_across_ctas(const Reduce& R, DF part, int bid, int nblk,
+                                                   DF* s_red) {
   reduce_across_ctas(R, part, bid, nblk, s_red);
 }
 
@@ -183,12 +224,41 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, double part,
 // per-pixel geometry shared by A and A^T (identical FP32 arithmetic, so the two
 // kernels apply exactly the same matrix entries)
 // ---------------------------------------------------------------------------
+// Pixel p (0..1023) of a tile in row-major order (x fastest): the order of the
+// per-tile accumulators in shared memory and of the epilogues' image stores.
 template <int DIM>
-__device__ __forceinline__ void pixel_local(int p, int& lx, int& ly, int& lz) {
+__device__ __forceinline__ void pixel_rowmajor(int p, int& lx, int& ly, int& lz) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y;
   lx = p % TX;
   ly = (p / TX) % TY;
   lz = p / (TX * TY);
+}
+template <int DIM>
+__device__ __forceinline__ int rowmajor_index(int lx, int ly, int lz) {
+  return lx + Tile<DIM>::X * (ly + Tile<DIM>::Y * lz);
+}
+
+// Pixel p of a tile in compute order (threads take consecutive p): every 16
+// consecutive p (a half-warp) form a compact 4x4 (2D) or 4x2x2 (3D) block, and
+// every 32 an 8x4 or 4x4x2 block.  The arrivals of a half-warp then span a few
+// samples only (~11 at 0.1 mm, 2D), so its 8-byte window loads in the adjoint
+// hit distinct banks, and the forward's 4-byte window atomics of a warp stay
+// within 32 consecutive bins.  (A 32-pixel row spans up to ~85 samples and
+// costs several bank-conflict replays per access.)
+template <int DIM>
+__device__ __forceinline__ void pixel_local(int p, int& lx, int& ly, int& lz) {
+  const int j = p & 15, h = (p >> 4) & 1;
+  if (DIM == 2) {  // 32 x 32: p = [m:2][w:3][h:1][j:4]
+    const int w = (p >> 5) & 7, m = p >> 8;
+    lx = 8 * (w & 3) + 4 * h + (j & 3);
+    ly = 8 * m + 4 * (w >> 2) + (j >> 2);
+    lz = 0;
+  } else {  // 16 x 8 x 8: p = [w:5][h:1][j:4]
+    const int w = p >> 5;
+    lx = 4 * (w & 3) + (j & 3);
+    ly = 4 * ((w >> 2) & 1) + 2 * h + ((j >> 2) & 1);
+    lz = 2 * (w >> 3) + (j >> 3);
+  }
 }
 
 // offset of a pixel from the centre of its tile's in-grid pixels (an exact
@@ -597,7 +667,11 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
       if (lane == 0) mbar_arrive(&s_empty[slot]);
     }
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) s_acc[tid + m * 32 * NW] = acc[m];
+    for (int m = 0; m < PPT; ++m) {
+      int lx, ly, lz;
+      pixel_local<DIM>(tid + m * 32 * NW, lx, ly, lz);
+      s_acc[rowmajor_index<DIM>(lx, ly, lz)] = acc[m];
+    }
   }
   __syncthreads();
   if (tid == 0 && s_abort) {
@@ -616,7 +690,7 @@ template <int DIM, bool DC>
 __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double s_red[kAdjWarps + 1];
+  __shared__ DF s_red[kAdjWarps + 1];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
@@ -631,30 +705,36 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   const int per = (kTilePixels + C - 1) / C;
   const int p0 = rank * per, p1 = min(kTilePixels, p0 + per);
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
-  double part = 0.0;
+  DF part = df_zero();
   for (int p = p0 + tid; p < p1; p += kAdjThreads) {
+    // the C <= 8 remote loads are issued together, then summed in rank order
+    float part_q[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part_q[q] = q < C ? cluster.map_shared_rank(s_acc, q)[p] : 0.0f;
     float v = 0.0f;
-    for (int q = 0; q < C; ++q) v += cluster.map_shared_rank(s_acc, q)[p];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < C) v += part_q[q];
     int lx, ly, lz;
-    pixel_local<DIM>(p, lx, ly, lz);
+    pixel_rowmajor<DIM>(p, lx, ly, lz);
     const int gx = tx * TX + lx, gy = ty * TY + ly, gz = tz * TZ + lz;
     if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
       const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
       const float gval = P.amp * v;
       if (DC) {
-        part += (double)P.xin[i] * (double)v;
+        part = df_add(part, df_prod(P.xin[i], v));
       } else if (P.mode == ADJ_LANDWEBER) {
         float xv = fmaf((float)(*P.omega), gval, P.out[i]);
         if (P.nonneg) xv = fmaxf(xv, 0.0f);
         P.out[i] = xv;
       } else {
         P.out[i] = gval;
-        part += (double)gval * (double)gval;
+        part = df_add(part, df_sq(gval));
       }
     }
   }
   if (P.mode == ADJ_NORM || DC) {
-    const double t = block_sum<kAdjWarps + 1>(part, s_red);
+    const DF t = block_sum<kAdjWarps + 1>(part, s_red);
     reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
   }
   cluster.sync();
@@ -851,9 +931,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
 template <int MODE, int SPT>
 __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kblk, int nkblk) {
   static_assert(SPT == 1 || SPT == 4, "1 or 4 samples per thread");
-  __shared__ double s_red[32];
+  __shared__ DF s_red[32];
   const int k = SPT * (kblk * blockDim.x + threadIdx.x);
-  double part = 0.0;
+  DF part = df_zero();
   if (k < P.K) {
     const int* up = P.upper + (int64_t)s * (P.K + P.L);
     const int i0 = up[k], i1 = up[k + P.L];  // windows starting in (k - L, k]
@@ -904,10 +984,10 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
     }
 #pragma unroll
     for (int j = 0; j < SPT; ++j)
-      if (j < n) part += (double)v[j] * (double)v[j];
+      if (j < n) part = df_add(part, df_sq(v[j]));
   }
   if (MODE != FWD_STORE) {
-    const double t = block_sum(part, s_red, blockDim.x >> 5);
+    const DF t = block_sum(part, s_red, blockDim.x >> 5);
     reduce_across_ctas(P.red, t, s * nkblk + kblk, P.S * nkblk, s_red);
   }
 }
@@ -972,7 +1052,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     float* r_out, const float* q, float2* packed,
     const double* alpha_p, int N, int S, int K, int Kp, int pad, const Reduce red,
     int nblk_x) {
-  __shared__ double s_red[kVecThreads / 32];
+  __shared__ DF s_red[kVecThreads / 32];
   const float alpha = (float)(*alpha_p);
   if ((int)blockIdx.x < nblk_x) {
     for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < N;
@@ -984,7 +1064,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
   const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
   const int s = b / kb;
   const int k = 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
-  double part = 0.0;
+  DF part = df_zero();
   if (k < K) {
     const int64_t o = (int64_t)s * K + k;
     const int n = min(4, K - k);
@@ -1009,9 +1089,9 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     if (k == 0) row[-1] = make_float2(0.5f * rk[0], rk[0]);
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (j < n) part += (double)rk[j] * (double)rk[j];
+      if (j < n) part = df_add(part, df_sq(rk[j]));
   }
-  const double t = block_sum<kVecThreads / 32>(part, s_red);
+  const DF t = block_sum<kVecThreads / 32>(part, s_red);
   reduce_across_ctas<kVecThreads / 32>(red, t, b, nb, s_red);
 }
 
@@ -1052,12 +1132,12 @@ __global__ void k_fill(float* dst, float v, int64_t n) {
 
 __global__ void __launch_bounds__(kVecThreads) k_norm(const float* v, int64_t n,
                                                       const Reduce red) {
-  __shared__ double s_red[kVecThreads / 32];
-  double part = 0.0;
+  __shared__ DF s_red[kVecThreads / 32];
+  DF part = df_zero();
   for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kVecThreads)
-    part += (double)v[i] * (double)v[i];
-  const double t = block_sum<kVecThreads / 32>(part, s_red);
+    part = df_add(part, df_sq(v[i]));
+  const DF t = block_sum<kVecThreads / 32>(part, s_red);
   reduce_across_ctas<kVecThreads / 32>(red, t, blockIdx.x, gridDim.x, s_red);
 }
 
@@ -1111,16 +1191,16 @@ template <int DIM>
 __global__ void __launch_bounds__(kVecThreads) k_tv(const float* x, int nx, int ny,
                                                     int nz, float eps, float* grad,
                                                     const Reduce red) {
-  __shared__ double s_red[kVecThreads / 32];
+  __shared__ DF s_red[kVecThreads / 32];
   const float eps2 = eps * eps;
   const int64_t n = (int64_t)nx * ny * nz;
-  double part = 0.0;
+  DF part = df_zero();
   for (int64_t o = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; o < n;
        o += (int64_t)gridDim.x * kVecThreads) {
     const int i = (int)(o % nx), j = (int)((o / nx) % ny), l = (int)(o / ((int64_t)nx * ny));
     float ax, ay, az, m;
     tv_terms<DIM>(x, i, j, l, nx, ny, nz, eps2, ax, ay, az, m);
-    part += (double)m;
+    part = df_add(part, df_of(m));
     float g = -(ax + ay + az);
     float bx, by, bz, mm;
     if (i > 0) {
@@ -1137,7 +1217,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tv(const float* x, int nx, int 
     }
     grad[o] = g;
   }
-  const double t = block_sum<kVecThreads / 32>(part, s_red);
+  const DF t = block_sum<kVecThreads / 32>(part, s_red);
   reduce_across_ctas<kVecThreads / 32>(red, t, blockIdx.x, gridDim.x, s_red);
 }
 
@@ -1219,7 +1299,7 @@ __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile
   const float om = (float)(*P.omega);
   for (int p = threadIdx.x; p < kTilePixels; p += blockDim.x) {
     int lx, ly, lz;
-    pixel_local<DIM>(p, lx, ly, lz);
+    pixel_rowmajor<DIM>(p, lx, ly, lz);
     const int gx = tx * TX + lx, gy = ty * TY + ly, gz = tz * TZ + lz;
     if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
       const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;

@@ -534,7 +534,7 @@ AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* o
 
 Reduce make_reduce(const pa_plan* p, int op, double* out_sum, const double* other, double* out2) {
   Reduce r;
-  r.partials = p->d_partials;
+  r.partials = reinterpret_cast<float2*>(p->d_partials);  // 8-byte slots
   r.counter = p->d_counter;
   r.op = op;
   r.out_sum = out_sum;
