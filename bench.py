@@ -49,11 +49,11 @@ def cores():
 
 
 def cgls_launches(n_iter: int) -> int:
-    """Kernels of one CGLS reconstruction (A = tile gather + combine; every FP64
-    reduction is finished inside its producer): setup (A, pack, A^T) = 4, per
-    iteration (A with the fused direction update, x/r update, A^T) = 4, final
-    clamp = 1."""
-    return 4 + 4 * n_iter + 1
+    """Kernels of one CGLS reconstruction (A = tile gather + combine; every norm
+    is summed by the kernel that consumes it): setup (A, pack, A^T) = 4, per
+    iteration (A with the fused direction update, alpha + x/r update, A^T) = 4,
+    then the residual history and the final clamp = 2."""
+    return 4 + 4 * n_iter + 2
 
 
 def cgls_applications(n_iter: int) -> int:

@@ -89,7 +89,10 @@ struct GridF {
   float hdx, hdy, hdz;  // half spacings (FP32)
 };
 
-enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3 };
+// OP_STORE: the producer only stores its per-CTA partial (no fence, counter or
+// last-CTA sum); the kernel that needs the total sums the partials itself
+// (sum_partials), or k_hist does so after the iterations.
+enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3, OP_STORE = 4 };
 
 // kernel modes
 enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3 };
@@ -145,8 +148,27 @@ struct FwdParams {
   const float* s_in;
   const float* p_old;
   float* p_new;
-  const double* beta;
+  // beta = ||s||^2 / gamma_old, ||s||^2 summed by every CTA from the adjoint's
+  // n_s_parts partials; CTA (0, 0) records beta and gamma_new = ||s||^2
+  const float2* s_parts;
+  int n_s_parts;
+  const double* gamma_old;
+  double* beta;
+  double* gamma_new;
   int* err;
+};
+
+// Scalars of the CGLS vector step: alpha = gamma / delta, gamma = ||s||^2 and
+// delta = ||q||^2 summed by every CTA from the adjoint's and the combine's
+// partials; CTA 0 records the three.
+struct CglsAlpha {
+  const float2* q_parts;
+  int n_q_parts;
+  const float2* s_parts;
+  int n_s_parts;
+  double* alpha;
+  double* gamma;
+  double* delta;
 };
 
 // One frame of a batched reconstruction (see k_batch_landweber).
@@ -207,9 +229,13 @@ pa_status validate_grid(const pa_grid* g);
 
 // reductions and vector updates
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
-                           const float* q, float2* packed, const double* alpha, int N, int S,
+                           const float* q, float2* packed, const CglsAlpha& ca, int N, int S,
                            int K, int Kp, int pad, const Reduce& red, int nblk_x,
                            cudaStream_t st);
+// hist[r] = sum of row r of `parts` (row stride `stride`; n_first partials in
+// row 0, n_rest in the others), rows = n_iter + 1
+cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,
+                        double* hist, cudaStream_t st);
 int cgls_r_blocks(int S, int K);
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
@@ -260,6 +286,10 @@ struct pa_plan {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   int n_partials = 0;
+  float2* d_parts_q = nullptr;   // per-CTA partials of ||A p||^2 (CGLS combine)
+  float2* d_parts_s = nullptr;   // per-CTA partials of ||A^T r||^2 (CGLS adjoint)
+  float2* d_parts_h = nullptr;   // [rows][n_partials] partials of the residual history
+  int parts_h_rows = 0;
   unsigned* d_counter = nullptr;  // last-CTA counter of the fused reductions
   // reconstruction workspace (allocated on first use)
   float* d_ra = nullptr;

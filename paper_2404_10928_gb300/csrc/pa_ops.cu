@@ -178,6 +178,10 @@ __device__ __forceinline__ DF block_sum(DF v, DF* s_red) {
 // bid / nblk: this CTA's slot and the number of CTAs (work items) reducing.
 __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, DF part, int bid, int nblk,
                                                    DF* s_red) {
+  if (R.op == OP_STORE) {  // the consumer sums the partials
+    if (threadIdx.x == 0) R.partials[bid] = make_float2(part.hi, part.lo);
+    return;
+  }
   __shared__ int s_last;
   const int nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
@@ -218,6 +222,41 @@ template <int NW>
 __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, DF part, int bid, int nblk,
                                                    DF* s_red) {
   reduce_across_ctas(R, part, bid, nblk, s_red);
+}
+
+// Sum of n per-CTA partials written by an earlier kernel, in the order of
+// reduce_across_ctas (each thread its strided share, then block_sum), so every
+// CTA that calls it obtains the same bits.  All threads must call it; the
+// total is valid in thread 0.
+__device__ __forceinline__ DF sum_partials(const float2* parts, int n, DF* s_red) {
+  DF v = df_zero();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 q = __ldcg(parts + i);
+    v = df_add(v, DF{q.x, q.y});
+  }
+  return block_sum(v, s_red, blockDim.x >> 5);
+}
+
+// The same sum taken by one warp (lane-strided shares, then an xor tree; the
+// total in every lane), so the rest of the CTA keeps working meanwhile.  A
+// fixed order: every warp that calls it obtains the same bits.
+__device__ __forceinline__ DF warp_sum_partials(const float2* parts, int n) {
+  const int lane = threadIdx.x & 31;
+  DF v = df_zero();
+  for (int i0 = 0; i0 < n; i0 += 8 * 32) {  // 8 independent loads in flight per lane
+    float2 q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * 32 + lane;
+      q[j] = i < n ? __ldcg(parts + i) : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (i0 + j * 32 + lane < n) v = df_add(v, DF{q[j].x, q[j].y});
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -735,7 +774,19 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   }
   if (P.mode == ADJ_NORM || DC) {
     const DF t = block_sum<kAdjWarps + 1>(part, s_red);
-    reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
+    if (P.red.op == OP_STORE) {
+      // one partial per tile: rank 0 sums the cluster's C CTA totals in rank order
+      __shared__ DF s_cta;
+      if (tid == 0) s_cta = t;
+      cluster.sync();
+      if (rank == 0 && tid == 0) {
+        DF u = df_zero();
+        for (int q = 0; q < C; ++q) u = df_add(u, *cluster.map_shared_rank(&s_cta, q));
+        P.red.partials[tile] = make_float2(u.hi, u.lo);
+      }
+    } else {
+      reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
+    }
   }
   cluster.sync();
   (void)TZ;
@@ -798,7 +849,7 @@ __device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, floa
 // One (tile, sensor chunk) work item of the forward gather.  The first
 // kFwdThreads threads own four pixels each (two packed pairs); any further
 // threads of the block only help with the copies and barriers.
-template <int DIM>
+template <int DIM, bool DIR>
 __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int chunk,
                                                unsigned char* smem) {
   constexpr int PPT = kTilePixels / kFwdThreads;
@@ -821,19 +872,55 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   float2 ddx[2], ddy[2], ddz[2], cm[2], xs[2];
   float amax = 0.0f;
   int nonfinite = 0;
+  // CGLS direction p = s + beta p_old (stored once, by sensor chunk 0): s and
+  // p_old are loaded first; meanwhile warp 0 forms beta = ||s||^2 / gamma_old
+  // from the adjoint's per-tile partials
+  float sv[PPT], pv[PPT];
+  int64_t pix[PPT];
+  float beta = 0.0f;
+  if (DIR) {
+    __shared__ float s_beta;
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+      int lx, ly, lz;
+      pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
+      const bool in = owner && lx < nvx && ly < nvy && lz < nvz;
+      pix[m] = in ? ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)
+                  : -1;
+      sv[m] = in ? P.s_in[pix[m]] : 0.0f;
+      pv[m] = in ? P.p_old[pix[m]] : 0.0f;
+    }
+    if (warp == 0) {
+      const DF t = warp_sum_partials(P.s_parts, P.n_s_parts);
+      if (lane == 0) {
+        // the update runs in FP32, so beta is formed in FP32 from the leading
+        // parts (an FP64 division is a long chain on GB300's FP64 pipe); one
+        // CTA records the FP64 values
+        const double g_old = *P.gamma_old;
+        const float gof = (float)g_old;
+        s_beta = gof > 0.0f ? __fdiv_rn(t.hi, gof) : 0.0f;
+        if (tile == 0 && chunk == 0) {
+          const double g_new = df_to_double(t);
+          *P.beta = g_old > 0.0 ? g_new / g_old : 0.0;
+          *P.gamma_new = g_new;
+        }
+      }
+    }
+    __syncthreads();
+    beta = s_beta;
+  }
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
     int lx, ly, lz;
     pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
     float xv = 0.0f;
-    if (owner && lx < nvx && ly < nvy && lz < nvz) {
-      const int64_t i = ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx);
-      if (P.s_in) {  // CGLS direction p = s + beta p_old, stored once (sensor chunk 0)
-        xv = fmaf((float)(*P.beta), P.p_old[i], P.s_in[i]);
-        if (chunk == 0) P.p_new[i] = xv;
-      } else {
-        xv = P.x[i];
+    if (DIR) {
+      if (pix[m] >= 0) {
+        xv = fmaf(beta, pv[m], sv[m]);
+        if (chunk == 0) P.p_new[pix[m]] = xv;
       }
+    } else if (owner && lx < nvx && ly < nvy && lz < nvz) {
+      xv = P.x[((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)];
     }
     amax = fmaxf(amax, fabsf(xv));
     nonfinite |= !(fabsf(xv) <= 3.0e38f);
@@ -912,10 +999,11 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   __syncthreads();  // the block's shared memory is free for the next work item
 }
 
-template <int DIM>
+// DIR: the image is the CGLS direction s + beta p_old (P.s_in != nullptr)
+template <int DIM, bool DIR>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  fwd_tile_block<DIM>(P, blockIdx.y, blockIdx.x, smem);
+  fwd_tile_block<DIM, DIR>(P, blockIdx.y, blockIdx.x, smem);
 }
 
 // One (sensor, block of SPT blockDim samples) work item of the combine: p[s,k]
@@ -1002,8 +1090,10 @@ int forward_combine_blocks(int S, int K, int spt) { return S * combine_kblocks(K
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
   const int smem = forward_smem_bytes(p.L, p.spc);
   dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, 1);
-  const cudaError_t e = launch_k(dim == 2 ? k_fwd_tile<2> : k_fwd_tile<3>, grid1,
-                                 dim3(kFwdThreads), smem, st, 0, p);
+  const bool dir = p.s_in != nullptr;
+  auto tile_kernel = dim == 2 ? (dir ? k_fwd_tile<2, true> : k_fwd_tile<2, false>)
+                              : (dir ? k_fwd_tile<3, true> : k_fwd_tile<3, false>);
+  const cudaError_t e = launch_k(tile_kernel, grid1, dim3(kFwdThreads), smem, st, 0, p);
   if (e != cudaSuccess) return e;
   const dim3 grid2(combine_kblocks(p.K, kCombThreads, p.comb_spt), p.S, 1);
   auto combine = p.comb_spt == 4
@@ -1032,10 +1122,17 @@ cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
   if ((e = cudaFuncSetAttribute(k_adjoint<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_adj)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_fwd_tile<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_fwd)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_fwd_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd);
+  if ((e = cudaFuncSetAttribute(k_fwd_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_fwd)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_fwd_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_fwd)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_fwd_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_fwd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1050,28 +1147,54 @@ constexpr int kVecThreads = 256;
 __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     float* x, const float* pv, const float* r_in,
     float* r_out, const float* q, float2* packed,
-    const double* alpha_p, int N, int S, int K, int Kp, int pad, const Reduce red,
+    const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red,
     int nblk_x) {
   __shared__ DF s_red[kVecThreads / 32];
-  const float alpha = (float)(*alpha_p);
-  if ((int)blockIdx.x < nblk_x) {
+  __shared__ float s_alpha;
+  // this thread's operands are loaded first; meanwhile warp 0 forms
+  // alpha = gamma / ||q||^2 from the combine's and the adjoint's partials
+  const bool xblk = (int)blockIdx.x < nblk_x;
+  const int kb = combine_kblocks(K, kVecThreads, 4);
+  const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
+  const int s = xblk ? 0 : b / kb;
+  const int k = xblk ? K : 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
+  const int64_t o = (int64_t)s * K + k;
+  const int n = min(4, K - k);
+  float qv[5], rv[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {  // sample 4 = the next group's first (0 past the row)
+    const bool use = k < K && j <= n && k + j < K;
+    qv[j] = use ? q[o + j] : 0.0f;
+    rv[j] = use ? r_in[o + j] : 0.0f;
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    const DF d = warp_sum_partials(ca.q_parts, ca.n_q_parts);
+    const DF g = warp_sum_partials(ca.s_parts, ca.n_s_parts);
+    if (threadIdx.x == 0) {
+      // alpha in FP32 from the leading parts (the update runs in FP32); CTA 0
+      // records the FP64 values
+      s_alpha = d.hi > 0.0f ? __fdiv_rn(g.hi, d.hi) : 0.0f;
+      if (blockIdx.x == 0) {
+        const double delta = df_to_double(d), gamma = df_to_double(g);
+        *ca.alpha = delta > 0.0 ? gamma / delta : 0.0;
+        *ca.gamma = gamma;
+        *ca.delta = delta;
+      }
+    }
+  }
+  __syncthreads();
+  const float alpha = s_alpha;
+  if (xblk) {
     for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < N;
          i += (int64_t)nblk_x * kVecThreads)
       x[i] = fmaf(alpha, pv[i], x[i]);
     return;
   }
-  const int kb = combine_kblocks(K, kVecThreads, 4);
-  const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
-  const int s = b / kb;
-  const int k = 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
   DF part = df_zero();
   if (k < K) {
-    const int64_t o = (int64_t)s * K + k;
-    const int n = min(4, K - k);
     float rk[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j)  // rk[4] = the next group's first sample (0 past the row)
-      rk[j] = (j <= n && k + j < K) ? fmaf(-alpha, q[o + j], r_in[o + j]) : 0.0f;
+    for (int j = 0; j < 5; ++j) rk[j] = fmaf(-alpha, qv[j], rv[j]);
     float2* row = packed + (int64_t)s * Kp + pad + k;
     if (n == 4 && (K & 3) == 0) {
       *reinterpret_cast<float4*>(r_out + o) = make_float4(rk[0], rk[1], rk[2], rk[3]);
@@ -1099,11 +1222,27 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
 int cgls_r_blocks(int S, int K) { return S * combine_kblocks(K, kVecThreads, 4); }
 
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
-                           const float* q, float2* packed, const double* alpha, int N, int S,
+                           const float* q, float2* packed, const CglsAlpha& ca, int N, int S,
                            int K, int Kp, int pad, const Reduce& red, int nblk_x,
                            cudaStream_t st) {
   return launch_k(k_cgls_xr, dim3(nblk_x + cgls_r_blocks(S, K)), dim3(kVecThreads), 0, st, 0, x,
-                  pvec, r_in, r_out, q, packed, alpha, N, S, K, Kp, pad, red, nblk_x);
+                  pvec, r_in, r_out, q, packed, ca, N, S, K, Kp, pad, red, nblk_x);
+}
+
+// The residual history of a reconstruction: one CTA per iteration sums that
+// iteration's partials (stored by the producing kernels with OP_STORE).
+__global__ void __launch_bounds__(kVecThreads) k_hist(const float2* parts, int stride,
+                                                     int n_first, int n_rest, double* hist) {
+  __shared__ DF s_red[kVecThreads / 32];
+  const int row = blockIdx.x;
+  const DF t = sum_partials(parts + (int64_t)row * stride, row == 0 ? n_first : n_rest, s_red);
+  if (threadIdx.x == 0) hist[row] = df_to_double(t);
+}
+
+cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,
+                        double* hist, cudaStream_t st) {
+  return launch_k(k_hist, dim3(rows), dim3(kVecThreads), 0, st, 0, parts, stride, n_first,
+                  n_rest, hist);
 }
 
 __global__ void k_scale(float* v, const float* w,
@@ -1259,11 +1398,16 @@ __device__ __forceinline__ void grid_barrier(unsigned* st, unsigned nblocks, int
       __threadfence();
       atomicAdd(st + 1, 1u);
     } else {
+      // bounded: after kWaitLimitNs, or as soon as an earlier wait of the launch
+      // has given up (ERR_WAIT_TIMEOUT latched), stop waiting
       const uint64_t t0 = global_ns();
       for (uint32_t it = 1; *gen == g; ++it) {
-        if ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) {
-          atomicOr(err, ERR_WAIT_TIMEOUT);
-          break;
+        if ((it & 255u) == 0u) {
+          if (*(volatile int*)err & ERR_WAIT_TIMEOUT) break;
+          if (global_ns() - t0 > kWaitLimitNs) {
+            atomicOr(err, ERR_WAIT_TIMEOUT);
+            break;
+          }
         }
       }
     }
@@ -1325,7 +1469,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_landweber(
       const int f = frame_of(pf, nf, gi);
       const int li = gi - pf[f];
       const int chunks = frames[f].fwd_chunks;
-      fwd_tile_block<DIM>(frames[f].f, li / chunks, li % chunks, smem);
+      fwd_tile_block<DIM, false>(frames[f].f, li / chunks, li % chunks, smem);
     }
     grid_barrier(state, nb, err, state + 2);
     for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {

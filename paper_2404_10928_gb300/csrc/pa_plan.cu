@@ -136,7 +136,7 @@ static void free_plan(pa_plan* p) {
   }
   p->graphs.clear();
   void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
-                  p->d_packed, p->d_err, p->d_partials,
+                  p->d_packed, p->d_err, p->d_partials, p->d_parts_q, p->d_parts_s, p->d_parts_h,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
                   p->d_scal,    p->d_counter,
                   p->d_yhost,   p->d_xhost};
@@ -376,6 +376,8 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
       (st = dev_alloc(p, &p->d_packed, (size_t)p->S * p->Kp)) != PA_OK ||
       (st = dev_alloc(p, &p->d_err, 1)) != PA_OK ||
       (st = dev_alloc(p, &p->d_partials, (size_t)p->n_partials)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_parts_q, (size_t)p->n_partials)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_parts_s, (size_t)p->n_partials)) != PA_OK ||
       (st = dev_alloc(p, &p->d_counter, 4)) != PA_OK) {
     free_plan(p);
     return st;

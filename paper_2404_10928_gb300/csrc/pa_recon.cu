@@ -76,6 +76,18 @@ pa_status ensure_workspace(pa_plan* p, int n_iter) {
   PA_TRY(alloc_once(p, &p->d_pv, N));
   PA_TRY(alloc_once(p, &p->d_pb, N));
   PA_TRY(alloc_once(p, &p->d_sv, N));
+  if (p->parts_h_rows < n_iter + 1) {
+    drop_graphs(p);  // graphs hold pointers into the old rows
+    if (p->d_parts_h) {
+      PA_CUDA(cudaDeviceSynchronize());
+      cudaFree(p->d_parts_h);
+      p->bytes -= (int64_t)p->parts_h_rows * p->n_partials * (int64_t)sizeof(float2);
+      p->d_parts_h = nullptr;
+    }
+    const int rows = std::max(n_iter + 1, 65);
+    PA_TRY(alloc_once(p, &p->d_parts_h, (size_t)rows * p->n_partials));
+    p->parts_h_rows = rows;
+  }
   const int need = scalar_count(n_iter);
   if (p->scal_cap < need) {
     drop_graphs(p);  // graphs hold pointers into the old records
@@ -113,8 +125,21 @@ struct DirUpdate {
   const float* s = nullptr;
   const float* p_old = nullptr;
   float* p_new = nullptr;
-  const double* beta = nullptr;
+  const float2* s_parts = nullptr;  // partials of ||s||^2 (the adjoint's)
+  int n_s_parts = 0;
+  const double* gamma_old = nullptr;
+  double* beta = nullptr;           // records
+  double* gamma_new = nullptr;
 };
+
+// A reduction whose per-CTA partials are only stored (into `parts`); the
+// consumer sums them (OP_STORE).
+Reduce stored(float2* parts) {
+  Reduce r{};
+  r.op = OP_STORE;
+  r.partials = parts;
+  return r;
+}
 
 pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, const Reduce& red,
               Timing& t, cudaStream_t st, const DirUpdate& du = DirUpdate()) {
@@ -124,7 +149,11 @@ pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, c
   f.s_in = du.s;
   f.p_old = du.p_old;
   f.p_new = du.p_new;
+  f.s_parts = du.s_parts;
+  f.n_s_parts = du.n_s_parts;
+  f.gamma_old = du.gamma_old;
   f.beta = du.beta;
+  f.gamma_new = du.gamma_new;
   PA_CUDA(launch_forward(p->dim, f, st));
   PA_TRY(mark(t, true, st));
   return PA_OK;
@@ -177,14 +206,16 @@ pa_status enqueue_landweber(pa_plan* p, int n_iter, const void* y, float* x,
     omega = sc.inv_lam;
   }
   const Reduce none{};
+  const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
   for (int it = 0; it <= n_iter; ++it) {
-    // r = y - A x and ||r||^2
-    PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y, make_reduce(p, OP_SUM, sc.hist + it, nullptr, nullptr),
-               t, st));
+    // r = y - A x; the partials of ||r||^2 go to history row it
+    PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y, stored(p->d_parts_h + (size_t)it * p->n_partials), t,
+               st));
     if (it == n_iter) break;
     PA_CUDA(launch_pack(p->d_ra, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
     PA_TRY(adj(p, x, ADJ_LANDWEBER, omega, o.nonneg, none, t, st));  // x = max(0, x + w A^T r)
   }
+  PA_CUDA(launch_hist(p->d_parts_h, p->n_partials, n_comb, n_comb, n_iter + 1, sc.hist, st));
   return PA_OK;
 }
 
@@ -196,35 +227,53 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
   float* r_out = p->d_rb;
   float* p_cur = p->d_pv;
   float* p_prev = p->d_pb;
-  // r = y - A x0; s = A^T r; p = s; gamma = ||s||^2
-  PA_TRY(fwd(p, x, r_in, FWD_RESID, y, make_reduce(p, OP_SUM, sc.hist, nullptr, nullptr), t, st));
+  // Every norm is reduced by its consumer: a producer stores one partial per CTA
+  // (OP_STORE), the next kernel that needs the total sums them itself, and the
+  // residual history is summed once after the loop (launch_hist).
+  const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
+  const int n_adj = p->ntiles;  // the adjoint stores one partial per tile (per cluster)
+  const int n_xr = cgls_r_blocks(p->S, p->K);
+  float2* hist_row = p->d_parts_h;
+  // r = y - A x0; s = A^T r; p = s (||r||^2 -> history row 0, ||s||^2 -> parts_s)
+  PA_TRY(fwd(p, x, r_in, FWD_RESID, y, stored(hist_row), t, st));
   PA_CUDA(launch_pack(r_in, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, make_reduce(p, OP_SUM, sc.gamma, nullptr, nullptr),
-             t, st));
+  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
   for (int it = 0; it < n_iter; ++it) {
-    // p = s + beta p (fused into the gather from the second iteration on);
-    // q = A p; alpha = gamma / ||q||^2
-    const Reduce ra = make_reduce(p, OP_ALPHA, sc.delta + it, sc.gamma + it, sc.alpha + it);
+    // p = s + beta p with beta = ||s||^2 / gamma (fused into the gather from the
+    // second iteration on); q = A p (||q||^2 -> parts_q)
     if (it == 0) {
-      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, ra, t, st));
+      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
     } else {
       DirUpdate du;
       du.s = p->d_sv;
       du.p_old = p_prev;
       du.p_new = p_cur;
+      du.s_parts = p->d_parts_s;
+      du.n_s_parts = n_adj;
+      du.gamma_old = sc.gamma + it - 1;
       du.beta = sc.beta + it - 1;
-      PA_TRY(fwd(p, nullptr, p->d_q, FWD_NORM, nullptr, ra, t, st, du));
+      du.gamma_new = sc.gamma + it;
+      PA_TRY(fwd(p, nullptr, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st, du));
     }
-    // x += alpha p; r -= alpha q (packed for the adjoint); ||r||^2
-    PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, sc.alpha + it, N, p->S,
-                           p->K, p->Kp, p->pad,
-                           make_reduce(p, OP_SUM, sc.hist + it + 1, nullptr, nullptr), nbx, st));
-    // s = A^T r; beta = ||s||^2 / gamma
-    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0,
-               make_reduce(p, OP_BETA, sc.gamma + it + 1, sc.gamma + it, sc.beta + it), t, st));
+    // alpha = gamma / ||q||^2; x += alpha p; r -= alpha q (packed for the
+    // adjoint); ||r||^2 -> history row it + 1
+    CglsAlpha ca;
+    ca.q_parts = p->d_parts_q;
+    ca.n_q_parts = n_comb;
+    ca.s_parts = p->d_parts_s;
+    ca.n_s_parts = n_adj;
+    ca.alpha = sc.alpha + it;
+    ca.gamma = sc.gamma + it;
+    ca.delta = sc.delta + it;
+    PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, ca, N, p->S, p->K, p->Kp,
+                           p->pad, stored(hist_row + (size_t)(it + 1) * p->n_partials), nbx,
+                           st));
+    // s = A^T r (||s||^2 -> parts_s)
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
     std::swap(r_in, r_out);
     std::swap(p_cur, p_prev);
   }
+  PA_CUDA(launch_hist(p->d_parts_h, p->n_partials, n_comb, n_xr, n_iter + 1, sc.hist, st));
   if (o.nonneg) PA_CUDA(launch_clamp(x, N, st));
   return PA_OK;
 }
