@@ -814,9 +814,27 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
 // k, in a fixed order (by window start), plus the residual / norm epilogue.
 // ---------------------------------------------------------------------------
+// Each (tile, sensor) window is kept as kFwdCopies copies, kFwdCopyPad words
+// apart in bank alignment (copy c starts c (L + kFwdCopyPad) words after copy
+// 0, i.e. 8 banks further): a thread deposits into the copy chosen by its place
+// in its half-warp's 4x4 pixel block (fwd_copy), so pixels on a common row,
+// column or diagonal of the block -- the likeliest to share a sample bin --
+// update different banks instead of replaying one atomic.  The flush adds the
+// copies (exact integer sums), so results do not depend on the split.
+constexpr int kFwdCopies = 4;
+constexpr int kFwdCopyPad = 8;
+__host__ __device__ inline int fwd_copy_stride(int L) { return L + kFwdCopyPad; }
+
 int forward_smem_bytes(int L, int spc) {
-  return spc * (int)sizeof(TileRef2) + 2 * kFwdSB * L * (int)sizeof(int);
+  return spc * (int)sizeof(TileRef2) +
+         2 * kFwdSB * kFwdCopies * fwd_copy_stride(L) * (int)sizeof(int);
 }
+
+// Copy index of compute-order pixel p: a 4x4 Latin square over the half-warp
+// block position j = p & 15 (x = j & 3, y = j >> 2) whose rows, columns and
+// both diagonals hold all four copies:
+//   0 1 2 3 / 2 3 0 1 / 3 2 1 0 / 1 0 3 2
+__device__ __forceinline__ int fwd_copy(int p) { return (0xB11B4EE4u >> (2 * (p & 15))) & 3; }
 
 constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
 
@@ -940,7 +958,9 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     else
       refs[i].klo = kSkip;
   }
-  for (int i = tid; i < 2 * kFwdSB * L; i += nt) win[i] = 0;
+  const int CS = fwd_copy_stride(L);           // words per window copy
+  const int WS = kFwdCopies * CS;              // words per (tile, sensor) window
+  for (int i = tid; i < 2 * kFwdSB * WS; i += nt) win[i] = 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if (lane == 0) s_max[warp] = amax;
@@ -952,14 +972,15 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   for (int h = 0; h < 2; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
   const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
 
-  const uint32_t win_u32 = smem_u32(win);
+  // this thread's copy of every window (all four of its pixels share it)
+  const uint32_t win_u32 = smem_u32(win) + 4u * (uint32_t)(fwd_copy(tid) * CS);
   for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
-    int* wb = win + buf * kFwdSB * L;
+    int* wb = win + buf * kFwdSB * WS;
     const int nsb = min(kFwdSB, ns - g0);
     if (owner && xscale > 0.0f) {
-      uint32_t base = magic_base(win_u32 + (uint32_t)(buf * kFwdSB * L + L / 2) * 4u, 2);
+      uint32_t base = magic_base(win_u32 + (uint32_t)(buf * kFwdSB * WS + L / 2) * 4u, 2);
 #pragma unroll 1
-      for (int sb = 0; sb < nsb; ++sb, base += 4u * (uint32_t)L) {
+      for (int sb = 0; sb < nsb; ++sb, base += 4u * (uint32_t)WS) {
         const TileRef2 r = refs[g0 + sb];
         if (r.klo == kSkip) continue;
         const float2 dlo = f2(r.dlo);
@@ -985,13 +1006,21 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
         const float u = !finite ? __int_as_float(0x7fc00000)
                         : (xscale > 0.0f ? __fdividef(xmax, kFixedScale * refs[g0 + warp].dlo)
                                          : 0.0f);
-        int4* src = reinterpret_cast<int4*>(wb + warp * L);
+        int4* src = reinterpret_cast<int4*>(wb + warp * WS);
         float4* dst = reinterpret_cast<float4*>(
             P.part + ((int64_t)(s0 + g0 + warp) * P.ntiles + tile) * L);
         for (int k4 = lane; k4 < L / 4; k4 += 32) {
-          const int4 v = src[k4];
+          int4 v = make_int4(0, 0, 0, 0);
+#pragma unroll
+          for (int c = 0; c < kFwdCopies; ++c) {
+            const int4 w = src[c * (CS / 4) + k4];
+            v.x += w.x;
+            v.y += w.y;
+            v.z += w.z;
+            v.w += w.w;
+            src[c * (CS / 4) + k4] = make_int4(0, 0, 0, 0);
+          }
           dst[k4] = make_float4((float)v.x * u, (float)v.y * u, (float)v.z * u, (float)v.w * u);
-          src[k4] = make_int4(0, 0, 0, 0);
         }
       }
     }
@@ -1151,7 +1180,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     int nblk_x) {
   __shared__ DF s_red[kVecThreads / 32];
   __shared__ float s_alpha;
-  // this thread's operands are loaded first; meanwhile warp 0 forms
+  // this thread's operands are loaded first, then the CTA forms
   // alpha = gamma / ||q||^2 from the combine's and the adjoint's partials
   const bool xblk = (int)blockIdx.x < nblk_x;
   const int kb = combine_kblocks(K, kVecThreads, 4);
@@ -1167,10 +1196,34 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     qv[j] = use ? q[o + j] : 0.0f;
     rv[j] = use ? r_in[o + j] : 0.0f;
   }
-  if ((threadIdx.x >> 5) == 0) {
-    const DF d = warp_sum_partials(ca.q_parts, ca.n_q_parts);
-    const DF g = warp_sum_partials(ca.s_parts, ca.n_s_parts);
+  {  // every warp takes a share of the partials (one round of loads), warps in order
+    DF d = df_zero(), g = df_zero();
+    for (int i = threadIdx.x; i < ca.n_q_parts; i += kVecThreads) {
+      const float2 v = __ldcg(ca.q_parts + i);
+      d = df_add(d, DF{v.x, v.y});
+    }
+    for (int i = threadIdx.x; i < ca.n_s_parts; i += kVecThreads) {
+      const float2 v = __ldcg(ca.s_parts + i);
+      g = df_add(g, DF{v.x, v.y});
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      d = df_add(d, df_shfl_xor(d, sh));
+      g = df_add(g, df_shfl_xor(g, sh));
+    }
+    __shared__ DF s_dg[2][kVecThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+      s_dg[0][threadIdx.x >> 5] = d;
+      s_dg[1][threadIdx.x >> 5] = g;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      d = df_zero();
+      g = df_zero();
+      for (int w = 0; w < kVecThreads / 32; ++w) {
+        d = df_add(d, s_dg[0][w]);
+        g = df_add(g, s_dg[1][w]);
+      }
       // alpha in FP32 from the leading parts (the update runs in FP32); CTA 0
       // records the FP64 values
       s_alpha = d.hi > 0.0f ? __fdiv_rn(g.hi, d.hi) : 0.0f;
@@ -1456,7 +1509,7 @@ __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBatchThreads) k_batch_landweber(
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
     const BatchFrame* __restrict__ frames, int nf, const int* __restrict__ pre, int n_iter,
     unsigned* state, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
