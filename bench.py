@@ -503,6 +503,37 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(kind: str) -> int:
+    """Small fixed workload for ncu captures of the gather kernels: one plan (the
+    256x256 ring with 8 CTAs per adjoint cluster and 16 sensors per forward CTA,
+    or a 64^3 planar array with 2 and 64), then A on a dense random image and
+    A^T on random traces, three times each.  Prints nothing."""
+    import torch
+
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Plan
+
+    torch.cuda.set_device(0)
+    if kind == "2d":
+        prob = ph.ring_vessels()
+        plan = Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=16)
+    else:
+        prob = ph.planar_vessel_tree(n=64)
+        plan = Plan.from_problem(prob, adj_cluster=2, fwd_sensors_per_cta=64)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(plan.n_pixels, device="cuda", generator=g)
+    y = torch.randn(plan.n_sensors * plan.n_samples, device="cuda", generator=g)
+    p = torch.empty_like(y)
+    z = torch.empty_like(x)
+    for _ in range(3):
+        plan.forward(x, out=p)
+        plan.adjoint(y, out=z)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -512,7 +543,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
+    ap.add_argument("--profile-case", choices=["2d", "3d"],
+                    help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
