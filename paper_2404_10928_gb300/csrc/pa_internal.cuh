@@ -230,8 +230,7 @@ pa_status validate_grid(const pa_grid* g);
 // reductions and vector updates
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const CglsAlpha& ca, int N, int S,
-                           int K, int Kp, int pad, const Reduce& red, int nblk_x,
-                           cudaStream_t st);
+                           int K, int Kp, int pad, const Reduce& red, cudaStream_t st);
 // hist[r] = sum of row r of `parts` (row stride `stride`; n_first partials in
 // row 0, n_rest in the others), rows = n_iter + 1
 cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,

@@ -1176,19 +1176,31 @@ constexpr int kVecThreads = 256;
 __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     float* x, const float* pv, const float* r_in,
     float* r_out, const float* q, float2* packed,
-    const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red,
-    int nblk_x) {
+    const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red) {
   __shared__ DF s_red[kVecThreads / 32];
   __shared__ float s_alpha;
-  // this thread's operands are loaded first, then the CTA forms
-  // alpha = gamma / ||q||^2 from the combine's and the adjoint's partials
-  const bool xblk = (int)blockIdx.x < nblk_x;
+  // CTA b owns samples 4 (j kVecThreads + thread) .. + 3 of sensor s (b = s kb + j)
+  // and the image slice [b chunk, (b + 1) chunk): one wave of S kb CTAs
   const int kb = combine_kblocks(K, kVecThreads, 4);
-  const int b = blockIdx.x - nblk_x, nb = gridDim.x - nblk_x;
-  const int s = xblk ? 0 : b / kb;
-  const int k = xblk ? K : 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
+  const int b = blockIdx.x, nb = gridDim.x;
+  const int s = b / kb;
+  const int k = 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
   const int64_t o = (int64_t)s * K + k;
   const int n = min(4, K - k);
+  const int64_t chunk = ((int64_t)N + nb - 1) / nb;
+  const int64_t x0 = b * chunk, x1 = min((int64_t)N, x0 + chunk);
+  // alpha = gamma / ||q||^2 from the combine's and the adjoint's partials: the
+  // partials are loaded first (their chain is the longest), then this thread's
+  // operands, and every warp takes a share of the partials, warps in order
+  DF d = df_zero(), g = df_zero();
+  for (int i = threadIdx.x; i < ca.n_q_parts; i += kVecThreads) {
+    const float2 v = __ldcg(ca.q_parts + i);
+    d = df_add(d, DF{v.x, v.y});
+  }
+  for (int i = threadIdx.x; i < ca.n_s_parts; i += kVecThreads) {
+    const float2 v = __ldcg(ca.s_parts + i);
+    g = df_add(g, DF{v.x, v.y});
+  }
   float qv[5], rv[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {  // sample 4 = the next group's first (0 past the row)
@@ -1196,53 +1208,41 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     qv[j] = use ? q[o + j] : 0.0f;
     rv[j] = use ? r_in[o + j] : 0.0f;
   }
-  {  // every warp takes a share of the partials (one round of loads), warps in order
-    DF d = df_zero(), g = df_zero();
-    for (int i = threadIdx.x; i < ca.n_q_parts; i += kVecThreads) {
-      const float2 v = __ldcg(ca.q_parts + i);
-      d = df_add(d, DF{v.x, v.y});
-    }
-    for (int i = threadIdx.x; i < ca.n_s_parts; i += kVecThreads) {
-      const float2 v = __ldcg(ca.s_parts + i);
-      g = df_add(g, DF{v.x, v.y});
-    }
+  const int64_t xi = x0 + threadIdx.x;
+  const float xv0 = xi < x1 ? x[xi] : 0.0f, pv0 = xi < x1 ? pv[xi] : 0.0f;
 #pragma unroll
-    for (int sh = 16; sh > 0; sh >>= 1) {
-      d = df_add(d, df_shfl_xor(d, sh));
-      g = df_add(g, df_shfl_xor(g, sh));
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    d = df_add(d, df_shfl_xor(d, sh));
+    g = df_add(g, df_shfl_xor(g, sh));
+  }
+  __shared__ DF s_dg[2][kVecThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    s_dg[0][threadIdx.x >> 5] = d;
+    s_dg[1][threadIdx.x >> 5] = g;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    d = df_zero();
+    g = df_zero();
+    for (int w = 0; w < kVecThreads / 32; ++w) {
+      d = df_add(d, s_dg[0][w]);
+      g = df_add(g, s_dg[1][w]);
     }
-    __shared__ DF s_dg[2][kVecThreads / 32];
-    if ((threadIdx.x & 31) == 0) {
-      s_dg[0][threadIdx.x >> 5] = d;
-      s_dg[1][threadIdx.x >> 5] = g;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      d = df_zero();
-      g = df_zero();
-      for (int w = 0; w < kVecThreads / 32; ++w) {
-        d = df_add(d, s_dg[0][w]);
-        g = df_add(g, s_dg[1][w]);
-      }
-      // alpha in FP32 from the leading parts (the update runs in FP32); CTA 0
-      // records the FP64 values
-      s_alpha = d.hi > 0.0f ? __fdiv_rn(g.hi, d.hi) : 0.0f;
-      if (blockIdx.x == 0) {
-        const double delta = df_to_double(d), gamma = df_to_double(g);
-        *ca.alpha = delta > 0.0 ? gamma / delta : 0.0;
-        *ca.gamma = gamma;
-        *ca.delta = delta;
-      }
+    // alpha in FP32 from the leading parts (the update runs in FP32); CTA 0
+    // records the FP64 values
+    s_alpha = d.hi > 0.0f ? __fdiv_rn(g.hi, d.hi) : 0.0f;
+    if (blockIdx.x == 0) {
+      const double delta = df_to_double(d), gamma = df_to_double(g);
+      *ca.alpha = delta > 0.0 ? gamma / delta : 0.0;
+      *ca.gamma = gamma;
+      *ca.delta = delta;
     }
   }
   __syncthreads();
   const float alpha = s_alpha;
-  if (xblk) {
-    for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < N;
-         i += (int64_t)nblk_x * kVecThreads)
-      x[i] = fmaf(alpha, pv[i], x[i]);
-    return;
-  }
+  // x += alpha p over this CTA's image slice
+  if (xi < x1) x[xi] = fmaf(alpha, pv0, xv0);
+  for (int64_t i = xi + kVecThreads; i < x1; i += kVecThreads) x[i] = fmaf(alpha, pv[i], x[i]);
   DF part = df_zero();
   if (k < K) {
     float rk[5];
@@ -1276,10 +1276,9 @@ int cgls_r_blocks(int S, int K) { return S * combine_kblocks(K, kVecThreads, 4);
 
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const CglsAlpha& ca, int N, int S,
-                           int K, int Kp, int pad, const Reduce& red, int nblk_x,
-                           cudaStream_t st) {
-  return launch_k(k_cgls_xr, dim3(nblk_x + cgls_r_blocks(S, K)), dim3(kVecThreads), 0, st, 0, x,
-                  pvec, r_in, r_out, q, packed, ca, N, S, K, Kp, pad, red, nblk_x);
+                           int K, int Kp, int pad, const Reduce& red, cudaStream_t st) {
+  return launch_k(k_cgls_xr, dim3(cgls_r_blocks(S, K)), dim3(kVecThreads), 0, st, 0, x, pvec,
+                  r_in, r_out, q, packed, ca, N, S, K, Kp, pad, red);
 }
 
 // The residual history of a reconstruction: one CTA per iteration sums that

@@ -169,7 +169,6 @@ pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg,
   return PA_OK;
 }
 
-int vec_blocks_x(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 4)); }
 int vec_blocks_r(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
 // v <- A^T A v / ||A^T A v||, n_pow times, from v0 (NULL = ones).  Afterwards
@@ -222,7 +221,6 @@ pa_status enqueue_landweber(pa_plan* p, int n_iter, const void* y, float* x,
 pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa_recon_opts& o,
                        const Scalars& sc, Timing& t, cudaStream_t st) {
   const int N = p->grid.nx * p->grid.ny * p->grid.nz;
-  const int nbx = vec_blocks_x(N);
   float* r_in = p->d_ra;
   float* r_out = p->d_rb;
   float* p_cur = p->d_pv;
@@ -266,8 +264,7 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
     ca.gamma = sc.gamma + it;
     ca.delta = sc.delta + it;
     PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, ca, N, p->S, p->K, p->Kp,
-                           p->pad, stored(hist_row + (size_t)(it + 1) * p->n_partials), nbx,
-                           st));
+                           p->pad, stored(hist_row + (size_t)(it + 1) * p->n_partials), st));
     // s = A^T r (||s||^2 -> parts_s)
     PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
     std::swap(r_in, r_out);
