@@ -160,6 +160,25 @@ pa_status pa_forward(pa_plan *plan, const float *x_dev, float *p_dev, pa_stream 
  * p_dev: [S][K] float32; x_dev: [N] float32, fully overwritten. */
 pa_status pa_adjoint(pa_plan *plan, const float *p_dev, float *x_dev, pa_stream stream);
 
+/* Trace filters of pa_backproject. */
+typedef enum { PA_BP_NONE = 0, PA_BP_UBP = 1 } pa_bp_filter;
+
+/* Back-projection reconstruction: the "BP" against which Sec. 4 (Experiment 1,
+ * Table 2) times the iterative reconstruction, one delay-and-sum pass over
+ * filtered traces,
+ *     x = A^T b,   b = F(p).
+ * filter PA_BP_NONE: b = p (x = A^T p, as pa_adjoint).  PA_BP_UBP: the
+ * universal back-projection term b(t) = 2 p(t) - 2 t dp/dt (Xu and Wang, Phys.
+ * Rev. E 71, 016706, 2005) at t_k = t0 + k/fs with the central difference
+ * dp/dt = fs (p[k+1] - p[k-1]) / 2 and p[-1] = p[K] = 0:
+ *     b[k] = 2 p[k] - (t0 fs + k) (p[k+1] - p[k-1]).
+ * (The paper calls its BP "filtered back-projection" without giving the
+ * filter; UBP is the standard time-domain one.)  The back-projection keeps the
+ * 1/d weight of A^T.  p_dev: [S][K] float32; x_dev: [N] float32, fully
+ * overwritten.  Other filter values return PA_ERR_INVALID_ARG. */
+pa_status pa_backproject(pa_plan *plan, const float *p_dev, int filter, float *x_dev,
+                         pa_stream stream);
+
 /* Largest eigenvalue of A^T A by n_iter power-iteration steps from v0_dev ([N]
  * float32, NULL = ones).  Blocks; *sigma2 receives the estimate. */
 pa_status pa_power_iteration(pa_plan *plan, int n_iter, const float *v0_dev, double *sigma2,

@@ -21,6 +21,9 @@ What is computed, and where it comes from:
 * ``power_iteration``: largest eigenvalue of A^T A (step size for Landweber).
 * ``tv`` / ``tv_grad``: smoothed isotropic total variation (the TV term of
   Eq. 8 with Psi' = identity).
+* ``ubp_filter`` / ``backproject``: the back-projection reconstruction timed
+  against the iterative one in Sec. 4 (Experiment 1, Table 2), with the
+  universal back-projection trace filter (a reading: the paper names no filter).
 
 Readings where the paper is silent are listed in the design doc; each function
 names the one it uses.  Parity status: every function here is pinned by a
@@ -145,6 +148,33 @@ def adjoint(geo: Geometry, p, c=None) -> np.ndarray:
     g = np.empty(geo.n_pixels)
     _load().oracle_adjoint(*geo._args(c), _ptr(p), _ptr(g))
     return g
+
+
+def ubp_filter(p, t0: float, fs: float) -> np.ndarray:
+    """Universal back-projection term b(t) = 2 p(t) - 2 t dp/dt (Xu and Wang,
+    Phys. Rev. E 71, 016706, 2005), the filter of the paper's "filtered
+    back-projection" (Sec. 4, Experiment 1; the paper does not give one), at the
+    sample times t_k = t0 + k/fs, with dp/dt taken as the central difference
+    fs (p[k+1] - p[k-1]) / 2 and zero traces before sample 0 and after K-1.
+    p: [S][K]; returns [S][K] float64."""
+    p = _f64(p)
+    s, k = p.shape
+    padded = np.zeros((s, k + 2))
+    padded[:, 1:-1] = p
+    dpdt = fs * (padded[:, 2:] - padded[:, :-2]) / 2.0
+    t = t0 + np.arange(k) / fs
+    return 2.0 * p - 2.0 * t[None, :] * dpdt
+
+
+def backproject(geo: Geometry, p, filter: str = "ubp") -> np.ndarray:
+    """Back-projection reconstruction x = A^T F(p) (the "BP" of Table 2):
+    F = ubp_filter ("ubp") or the identity ("none"), then the adjoint."""
+    p = _f64(p).reshape(geo.n_sensors, geo.n_samples)
+    if filter == "ubp":
+        p = ubp_filter(p, geo.t0, geo.fs)
+    elif filter != "none":
+        raise ValueError(filter)
+    return adjoint(geo, p)
 
 
 def dc(geo: Geometry, x, g, c=None) -> float:

@@ -25,6 +25,8 @@ PA_ERR_UNSUPPORTED = 7
 
 PA_LANDWEBER = 0
 PA_CGLS = 1
+PA_BP_NONE = 0
+PA_BP_UBP = 1
 PA_F32 = 0
 PA_F16 = 1
 
@@ -67,6 +69,7 @@ SIGNATURES = {
     "pa_plan_query": (c_int, [_P, ctypes.POINTER(pa_plan_info)]),
     "pa_forward": (c_int, [_P, c_void_p, c_void_p, _STREAM]),
     "pa_adjoint": (c_int, [_P, c_void_p, c_void_p, _STREAM]),
+    "pa_backproject": (c_int, [_P, c_void_p, c_int, c_void_p, _STREAM]),
     "pa_power_iteration": (c_int, [_P, c_int, c_void_p, _DP, _STREAM]),
     "pa_reconstruct": (c_int, [_P, c_int, c_int, c_void_p, c_void_p,
                                ctypes.POINTER(pa_recon_opts), _STREAM]),

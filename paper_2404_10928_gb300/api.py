@@ -13,9 +13,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PA_CGLS, PA_F16, PA_F32, PA_LANDWEBER, check
+from ._lib import PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_LANDWEBER, check
 
 METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS}
+BP_FILTERS = {"none": PA_BP_NONE, "ubp": PA_BP_UBP}
 
 
 def _stream_handle(device: torch.device) -> int:
@@ -126,6 +127,20 @@ class Plan:
         self._check_tensor(out, self.n_pixels, "out")
         check(self._lib.pa_adjoint(self._h, p.data_ptr(), out.data_ptr(),
                                    _stream_handle(self.device)), "pa_adjoint")
+        return out
+
+    def backproject(self, p: torch.Tensor, filter: str = "ubp",
+                    out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """x = A^T F(p): back-projection of [S][K] traces, F = "ubp" (universal
+        back-projection term 2p - 2t dp/dt) or "none" (see ``pa_backproject``)."""
+        self._check_tensor(p, self.n_sensors * self.n_samples, "p")
+        if filter not in BP_FILTERS:
+            raise ValueError(f"filter must be one of {sorted(BP_FILTERS)}")
+        if out is None:
+            out = torch.empty(self.n_pixels, device=self.device, dtype=torch.float32)
+        self._check_tensor(out, self.n_pixels, "out")
+        check(self._lib.pa_backproject(self._h, p.data_ptr(), BP_FILTERS[filter], out.data_ptr(),
+                                       _stream_handle(self.device)), "pa_backproject")
         return out
 
     def dc(self, x: torch.Tensor, g: torch.Tensor, out: Optional[torch.Tensor] = None):

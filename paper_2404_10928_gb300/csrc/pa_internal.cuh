@@ -214,6 +214,8 @@ cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const doub
                                double t0fs, int K, int L, double hmin, int* err, cudaStream_t st);
 cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
                         cudaStream_t st);
+cudaError_t launch_bp_filter(const float* p, float2* packed, int S, int K, int Kp, int pad,
+                             float t0fs, cudaStream_t st);
 cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st);
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
 int adjoint_smem_bytes(int L);

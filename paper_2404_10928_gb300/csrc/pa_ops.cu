@@ -526,6 +526,45 @@ __global__ void k_pack(const float* r, float2* packed, int S, int K, int Kp, int
   }
 }
 
+// Back-projection trace filter (universal back-projection term, see
+// pa_backproject): b[k] = 2 p[k] - (t0 fs + k) (p[k+1] - p[k-1]), p[-1] = p[K] =
+// 0, written straight into the packed (mid, slope) rows the adjoint reads, with
+// b[-1] = b[K] = 0 as in k_pack.  Thread layout as in k_pack: entries
+// k = k4 - 1 .. k4 + 2 of row blockIdx.y.
+__global__ void k_bp_filter(const float* p, float2* packed, int S, int K, int Kp, int pad,
+                            float t0fs) {
+  const int s = blockIdx.y;
+  const int k4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (k4 > K) return;
+  const float* ps = p + (int64_t)s * K;
+  float2* row = packed + (int64_t)s * Kp + pad;
+  float pv[7];  // p[k4 - 2 .. k4 + 4]
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const int k = k4 - 2 + j;
+    pv[j] = (k >= 0 && k < K) ? ps[k] : 0.0f;
+  }
+  float bv[5];  // b[k4 - 1 .. k4 + 3]
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int k = k4 - 1 + j;
+    bv[j] = (k >= 0 && k < K) ? fmaf(-(t0fs + (float)k), pv[j + 2] - pv[j], 2.0f * pv[j + 1])
+                              : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = k4 - 1 + j;
+    if (k < K) row[k] = make_float2(0.5f * (bv[j] + bv[j + 1]), bv[j + 1] - bv[j]);
+  }
+}
+
+cudaError_t launch_bp_filter(const float* p, float2* packed, int S, int K, int Kp, int pad,
+                             float t0fs, cudaStream_t st) {
+  const int threads = 256;
+  const dim3 grid((K + 1 + 4 * threads - 1) / (4 * threads), S);
+  return launch_k(k_bp_filter, grid, dim3(threads), 0, st, 0, p, packed, S, K, Kp, pad, t0fs);
+}
+
 cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
                         cudaStream_t st) {
   const int threads = 256;

@@ -574,6 +574,28 @@ pa_status pa_adjoint(pa_plan* plan, const float* p_dev, float* x_dev, pa_stream 
   return PA_OK;
 }
 
+pa_status pa_backproject(pa_plan* plan, const float* p_dev, int filter, float* x_dev,
+                         pa_stream stream) {
+  if (!plan || !x_dev || !p_dev) {
+    set_error("pa_backproject: NULL argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  if (filter != PA_BP_NONE && filter != PA_BP_UBP) {
+    set_error("pa_backproject: unknown filter %d", filter);
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (filter == PA_BP_UBP)
+    PA_CUDA(launch_bp_filter(p_dev, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad,
+                             (float)(plan->t0 * plan->fs), st));
+  else
+    PA_CUDA(launch_pack(p_dev, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad, st));
+  AdjParams a = adjoint_params(plan, x_dev, ADJ_STORE, nullptr, 0);
+  PA_CUDA(launch_adjoint(plan->dim, a, plan->cluster, plan->ntiles, st));
+  return PA_OK;
+}
+
 pa_status pa_dc(pa_plan* plan, const float* x_dev, const float* g_dev, double* dc_dev,
                 pa_stream stream) {
   if (!plan || !x_dev || !g_dev || !dc_dev) {

@@ -144,3 +144,36 @@ def test_autotuned_plan_matches_default(torch_cuda, tmp_path):
             fwd_sensors_per_cta=best["fwd_sensors_per_cta"]) as b:
         assert torch.equal(a.forward(xt), b.forward(xt))
         assert rel_l2(a.adjoint(yt).cpu().numpy(), b.adjoint(yt).cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["linear64-disks", "ragged-37x53-ring13-k301", "t0-amp-33x20",
+                                  "3d-20x17x12-planar"])
+@pytest.mark.parametrize("filt", ["ubp", "none"])
+def test_backproject_matches_oracle(torch_cuda, name, filt):
+    # back-projection (Sec. 4, Experiment 1): A^T of the filtered traces
+    torch = torch_cuda
+    prob = CASES[name]
+    geo = orc.Geometry.of(prob)
+    x, y = _inputs(prob, seed=13)
+    p = f32(orc.forward(geo, x))  # traces with the structure of a measurement
+    with _plan(prob) as plan:
+        b_gpu = plan.backproject(torch.tensor(p, dtype=torch.float32, device="cuda"), filt)
+        torch.cuda.synchronize()
+        plan.sync_status()
+        b_gpu = b_gpu.cpu().numpy()
+    b_ref = orc.backproject(geo, p, filt)
+    assert rel_l2(b_gpu, b_ref) <= OP_TOL, rel_l2(b_gpu, b_ref)
+
+
+def test_backproject_full_size_ring(torch_cuda):
+    torch = torch_cuda
+    prob = ph.ring_vessels()
+    geo = orc.Geometry.of(prob)
+    p = f32(orc.forward(geo, f32(prob.x_true)))
+    with _plan(prob) as plan:
+        b_gpu = plan.backproject(torch.tensor(p, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        plan.sync_status()
+        b_gpu = b_gpu.cpu().numpy()
+    b_ref = orc.backproject(geo, p, "ubp")
+    assert rel_l2(b_gpu, b_ref) <= OP_TOL, rel_l2(b_gpu, b_ref)

@@ -253,3 +253,43 @@ def test_monotone_residual_landweber():
     _, hist = orc.landweber(geo, y, 25, omega=1.0 / lam)
     assert np.all(np.diff(hist) <= 1e-12 * hist[0])
     assert hist[-1] < 0.5 * hist[0]
+
+
+def test_ubp_filter_hand_values():
+    # worked by hand from b(t) = 2 p(t) - 2 t dp/dt, dp/dt = fs (p[k+1] - p[k-1]) / 2,
+    # p[-1] = p[K] = 0:  p = (1, 2, 4)
+    #   t0 = 0, fs = 1:   dp/dt = (1, 1.5, -1),  t = (0, 1, 2)     -> b = (2, 1, 12)
+    #   t0 = 0.5, fs = 2: dp/dt = (2, 3, -2),    t = (0.5, 1, 1.5) -> b = (0, -2, 14)
+    p = np.array([[1.0, 2.0, 4.0]])
+    assert np.allclose(orc.ubp_filter(p, 0.0, 1.0), [[2.0, 1.0, 12.0]], rtol=0, atol=1e-14)
+    assert np.allclose(orc.ubp_filter(p, 0.5, 2.0), [[0.0, -2.0, 14.0]], rtol=0, atol=1e-14)
+
+
+def test_ubp_filter_quadratic_closed_form():
+    # a central difference is exact on a quadratic: for p[k] = a + b k + c k^2 the
+    # interior derivative is fs (b + 2 c k), so the filter is the polynomial
+    # 2 (a + b k + c k^2) - 2 (t0 fs + k)(b + 2 c k) away from the two ends
+    a, b, c, fs, t0, K = 0.3, -1.7, 0.05, 40e6, 2.5e-8, 64
+    k = np.arange(K, dtype=np.float64)
+    p = (a + b * k + c * k * k)[None, :]
+    got = orc.ubp_filter(p, t0, fs)[0]
+    expect = 2 * (a + b * k + c * k * k) - 2 * (t0 * fs + k) * (b + 2 * c * k)
+    assert np.allclose(got[1:-1], expect[1:-1], rtol=1e-12, atol=1e-12)
+    # the ends see the zero extension: dp/dt = fs p[1] / 2 and -fs p[K-2] / 2
+    assert np.isclose(got[0], 2 * p[0, 0] - 2 * t0 * fs * p[0, 1] / 2, rtol=1e-12)
+    assert np.isclose(got[-1], 2 * p[0, -1] + 2 * (t0 * fs + K - 1) * p[0, -2] / 2, rtol=1e-12)
+
+
+def test_backproject_is_adjoint_of_filtered_traces():
+    # <BP(p), x> = <F(p), A x>: the back-projection is the adjoint (an independent
+    # loop, pinned above) applied to the filtered traces
+    prob = ph.custom(2, (21, 17), (1e-4, 1e-4), ph.ring_sensors(7, 3e-3), 180, seed=11,
+                     t0=2 / ph.SAMPLE_RATE)
+    geo = orc.Geometry.of(prob)
+    rng = np.random.default_rng(12)
+    p = rng.standard_normal((prob.n_sensors, prob.n_samples))
+    x = rng.standard_normal(prob.n_pixels)
+    lhs = float(np.dot(orc.backproject(geo, p, "ubp"), x))
+    rhs = float(np.sum(orc.ubp_filter(p, geo.t0, geo.fs) * orc.forward(geo, x)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+    assert np.array_equal(orc.backproject(geo, p, "none"), orc.adjoint(geo, p))
