@@ -324,6 +324,56 @@ def bench_bp_vs_ir(torch, plan, prob, y, x_ir, ir_ms: float, reps: int = 20) -> 
             "timing": f"median of {reps}, CUDA events (warm L2)"}
 
 
+def bench_dense(torch, hbm_gbs: float, reps: int = 10) -> dict:
+    """The paper's own method at the paper's size (Sec. 4, Experiment 2, Table 4):
+    the 6144 x 16384 measurement matrix of a 128x128 frame assembled dense and
+    applied with matrix-vector products, in FP64 (the paper's precision) and in
+    FP32, against the matrix-free A and A^T on the same geometry."""
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Plan
+    prob = ph.dense_paper_size()
+    plan = Plan.from_problem(prob)
+    rows, cols = prob.n_sensors * prob.n_samples, prob.n_pixels
+    out = {"workload": "128x128 at 0.1 mm, 48-sensor ring R=10 mm, 128 samples at 10 MHz: "
+                       "M = 6144 x 16384 (the matrix size of the paper's Table 4)",
+           "paper_k40c_fp64_s": {"Mx": 7.8, "MTr": 6.4,
+                                 "note": "Table 4 as printed (Tesla K40c, FP64, MATLAB/mex)"}}
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        m = torch.empty((rows, cols), dtype=dt, device="cuda")
+        plan.dense_assemble(dt, out=m)
+        t_asm = _events_time(torch, lambda: plan.dense_assemble(dt, out=m), 3)
+        v = torch.rand(cols, dtype=dt, device="cuda", generator=g)
+        w = torch.rand(rows, dtype=dt, device="cuda", generator=g)
+        yo = torch.empty(rows, dtype=dt, device="cuda")
+        xo = torch.empty(cols, dtype=dt, device="cuda")
+        plan.dense_matvec(m, v, out=yo)
+        plan.dense_matvec(m, w, transpose=True, out=xo)
+        t_mv = _events_time(torch, lambda: plan.dense_matvec(m, v, out=yo), reps)
+        t_mtv = _events_time(torch, lambda: plan.dense_matvec(m, w, transpose=True, out=xo),
+                             reps)
+        nbytes = rows * cols * m.element_size()
+        out[name] = {"assemble_ms": t_asm * 1e3, "Mx_ms": t_mv * 1e3, "MTr_ms": t_mtv * 1e3,
+                     "Mx_gbs": nbytes / t_mv / 1e9, "MTr_gbs": nbytes / t_mtv / 1e9,
+                     "Mx_frac_hbm": nbytes / t_mv / 1e9 / hbm_gbs,
+                     "MTr_frac_hbm": nbytes / t_mtv / 1e9 / hbm_gbs,
+                     "Mx_tflops": 2 * rows * cols / t_mv / 1e12}
+        del m
+        torch.cuda.empty_cache()
+    x = torch.rand(cols, device="cuda", generator=g)
+    r = torch.rand(rows, device="cuda", generator=g)
+    p = torch.empty(rows, device="cuda")
+    z = torch.empty(cols, device="cuda")
+    plan.forward(x, out=p)
+    plan.adjoint(r, out=z)
+    out["matrix_free_fp32"] = {"A_ms": _events_time(torch, lambda: plan.forward(x, out=p), reps) * 1e3,
+                               "AT_ms": _events_time(torch, lambda: plan.adjoint(r, out=z), reps) * 1e3}
+    out["hbm_peak_gbs"] = hbm_gbs
+    out["timing"] = f"median of {reps}, CUDA events; M is larger than L2, so every product streams it from HBM"
+    plan.close()
+    return out
+
+
 def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
     """3D workload: 128^3 voxels at 0.2 mm, 32x32 planar array (0.8 mm pitch,
     5 mm from the volume), 1024 samples; A and A^T rates, a 30-iteration CGLS
@@ -474,6 +524,8 @@ def run_gpu(args):
         peak = (torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * sm_max
                 * 1e6 / 1e12)
         extra["volume3d"] = bench_volume(torch, tuner, peak)
+        hbm = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
+        extra["dense_paper_size"] = bench_dense(torch, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

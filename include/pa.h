@@ -63,7 +63,7 @@ typedef enum {
 } pa_status;
 
 typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1 } pa_method;
-typedef enum { PA_F32 = 0, PA_F16 = 1 } pa_dtype;
+typedef enum { PA_F32 = 0, PA_F16 = 1, PA_F64 = 2 } pa_dtype;
 
 /* Regular grid of pixel centres (Sec. 3.4: r_ij, the Cartesian pixel
  * coordinates of Eq. 6-7).  dim is 2 or 3; nx, ny, nz >= 1 (nz == 1 for 2D);
@@ -178,6 +178,25 @@ typedef enum { PA_BP_NONE = 0, PA_BP_UBP = 1 } pa_bp_filter;
  * overwritten.  Other filter values return PA_ERR_INVALID_ARG. */
 pa_status pa_backproject(pa_plan *plan, const float *p_dev, int filter, float *x_dev,
                          pa_stream stream);
+
+/* Dense-matrix mode: the paper's own method (Sec. 4, Experiment 2, Table 4)
+ * keeps the discretised Eq. 6 as a dense matrix (kn, 6144 x 16384 in FP64 for
+ * a 128 x 128 frame) and applies it with matrix-vector products; these two
+ * calls reproduce it on the plan's geometry, for comparison with the
+ * matrix-free pa_forward / pa_adjoint.
+ * pa_dense_assemble writes the matrix of A,
+ *     M[s*K + k][i] = amp * h(u_is - k) / d_is,
+ * row-major [S*K][N], into m_dev (caller-allocated, S*K*N entries of dtype
+ * PA_F64 or PA_F32).  Entries are evaluated in FP64 (rounded once for PA_F32);
+ * only the two taps of each (pixel, sensor) pair are non-zero.
+ * pa_dense_matvec computes out = M v (transpose = 0; v [N], out [S*K]) or
+ * out = M^T v (transpose = 1; v [S*K], out [N]) in dtype arithmetic for such a
+ * matrix (vectors of the same dtype, device memory).  Sums run in a fixed
+ * order.  The first transposed call allocates the plan's partial buffer
+ * (ceil(S*K/128) * N * 8 bytes): make it outside stream capture. */
+pa_status pa_dense_assemble(pa_plan *plan, int dtype, void *m_dev, pa_stream stream);
+pa_status pa_dense_matvec(pa_plan *plan, int dtype, const void *m_dev, int transpose,
+                          const void *v_dev, void *out_dev, pa_stream stream);
 
 /* Largest eigenvalue of A^T A by n_iter power-iteration steps from v0_dev ([N]
  * float32, NULL = ones).  Blocks; *sigma2 receives the estimate. */

@@ -29,6 +29,7 @@ PA_BP_NONE = 0
 PA_BP_UBP = 1
 PA_F32 = 0
 PA_F16 = 1
+PA_F64 = 2
 
 
 class pa_grid(ctypes.Structure):
@@ -70,6 +71,8 @@ SIGNATURES = {
     "pa_forward": (c_int, [_P, c_void_p, c_void_p, _STREAM]),
     "pa_adjoint": (c_int, [_P, c_void_p, c_void_p, _STREAM]),
     "pa_backproject": (c_int, [_P, c_void_p, c_int, c_void_p, _STREAM]),
+    "pa_dense_assemble": (c_int, [_P, c_int, c_void_p, _STREAM]),
+    "pa_dense_matvec": (c_int, [_P, c_int, c_void_p, c_int, c_void_p, c_void_p, _STREAM]),
     "pa_power_iteration": (c_int, [_P, c_int, c_void_p, _DP, _STREAM]),
     "pa_reconstruct": (c_int, [_P, c_int, c_int, c_void_p, c_void_p,
                                ctypes.POINTER(pa_recon_opts), _STREAM]),

@@ -13,10 +13,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_LANDWEBER, check
+from ._lib import PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_F64, PA_LANDWEBER, check
 
 METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS}
 BP_FILTERS = {"none": PA_BP_NONE, "ubp": PA_BP_UBP}
+_DENSE_DTYPES = {torch.float64: PA_F64, torch.float32: PA_F32}
 
 
 def _stream_handle(device: torch.device) -> int:
@@ -141,6 +142,39 @@ class Plan:
         self._check_tensor(out, self.n_pixels, "out")
         check(self._lib.pa_backproject(self._h, p.data_ptr(), BP_FILTERS[filter], out.data_ptr(),
                                        _stream_handle(self.device)), "pa_backproject")
+        return out
+
+    # -- dense-matrix mode (see pa_dense_assemble / pa_dense_matvec) ---------
+    def dense_assemble(self, dtype: torch.dtype = torch.float64,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The matrix of A, [S*K][N] row-major, in float64 or float32."""
+        code = _DENSE_DTYPES.get(dtype)
+        if code is None:
+            raise ValueError("dtype must be torch.float64 or torch.float32")
+        rows, cols = self.n_sensors * self.n_samples, self.n_pixels
+        if out is None:
+            out = torch.empty((rows, cols), dtype=dtype, device=self.device)
+        self._check_tensor(out, rows * cols, "out", dtype)
+        check(self._lib.pa_dense_assemble(self._h, code, out.data_ptr(),
+                                          _stream_handle(self.device)), "pa_dense_assemble")
+        return out
+
+    def dense_matvec(self, m: torch.Tensor, v: torch.Tensor, transpose: bool = False,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """M v ([N] -> [S*K]) or M^T v ([S*K] -> [N]) for an assembled matrix."""
+        code = _DENSE_DTYPES.get(m.dtype)
+        if code is None:
+            raise ValueError("m must be float64 or float32")
+        rows, cols = self.n_sensors * self.n_samples, self.n_pixels
+        self._check_tensor(m, rows * cols, "m", m.dtype)
+        n_in, n_out = (rows, cols) if transpose else (cols, rows)
+        self._check_tensor(v, n_in, "v", m.dtype)
+        if out is None:
+            out = torch.empty(n_out, dtype=m.dtype, device=self.device)
+        self._check_tensor(out, n_out, "out", m.dtype)
+        check(self._lib.pa_dense_matvec(self._h, code, m.data_ptr(), int(bool(transpose)),
+                                        v.data_ptr(), out.data_ptr(), _stream_handle(self.device)),
+              "pa_dense_matvec")
         return out
 
     def dc(self, x: torch.Tensor, g: torch.Tensor, out: Optional[torch.Tensor] = None):

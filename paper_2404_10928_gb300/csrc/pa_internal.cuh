@@ -9,6 +9,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pa.h"
@@ -32,6 +33,20 @@ pa_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
     pa_status s_ = (call);            \
     if (s_ != PA_OK) return s_;       \
   } while (0)
+
+// Makes a plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 // device error bits (latched in plan->d_err)
 enum : int {
@@ -291,6 +306,7 @@ struct pa_plan {
   float2* d_parts_s = nullptr;   // per-CTA partials of ||A^T r||^2 (CGLS adjoint)
   float2* d_parts_h = nullptr;   // [rows][n_partials] partials of the residual history
   int parts_h_rows = 0;
+  void* d_dense_part = nullptr;  // dense-matrix mode: per-row-chunk partials of M^T v
   unsigned* d_counter = nullptr;  // last-CTA counter of the fused reductions
   // reconstruction workspace (allocated on first use)
   float* d_ra = nullptr;

@@ -25,19 +25,6 @@ pa_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
   return PA_ERR_CUDA;
 }
 
-// Makes the plan's device current for the duration of a call.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 template <typename T>
 static pa_status dev_alloc(pa_plan* p, T** ptr, size_t count) {
@@ -137,6 +124,7 @@ static void free_plan(pa_plan* p) {
   p->graphs.clear();
   void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
                   p->d_packed, p->d_err, p->d_partials, p->d_parts_q, p->d_parts_s, p->d_parts_h,
+                  p->d_dense_part,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
                   p->d_scal,    p->d_counter,
                   p->d_yhost,   p->d_xhost};

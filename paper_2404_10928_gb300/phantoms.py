@@ -305,6 +305,20 @@ def planar_vessel_tree(seed: int = 1005, n: int = 128) -> Problem:
                    extra={"method": "cgls", "n_iter": 30})
 
 
+def dense_paper_size(seed: int = 1006) -> Problem:
+    """The size of the paper's dense measurement matrix (Sec. 4, Table 4:
+    6144 x 16384): a 128x128 frame at 0.1 mm and 6144 = 48 sensors x 128
+    samples -- a 48-element ring of radius 10 mm sampled at 10 MHz (the paper
+    does not give the split); Bezier vessel phantom."""
+    rng = np.random.default_rng(seed)
+    shape, spacing = (128, 128, 1), (1e-4, 1e-4, 1e-4)
+    origin = centred_origin(shape, spacing)
+    sensors = ring_sensors(48, 10e-3)
+    x = vessel_phantom(shape, spacing, origin, rng)
+    return Problem(2, shape, spacing, origin, sensors, SOUND_SPEED, 10e6, 128, x_true=x,
+                   name="2d-128x128-ring48-k128-10MHz-dense")
+
+
 def custom(dim: int, shape: Sequence[int], spacing: Sequence[float], sensors: np.ndarray,
            n_samples: int, seed: int, c: float = SOUND_SPEED, fs: float = SAMPLE_RATE,
            density: float = 0.3, t0: float = 0.0, amp_scale: float = 1.0) -> Problem:
