@@ -62,7 +62,7 @@ typedef enum {
   PA_ERR_UNSUPPORTED = 7    /* valid request this build does not handle */
 } pa_status;
 
-typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1 } pa_method;
+typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1, PA_FISTA = 2 } pa_method;
 typedef enum { PA_F32 = 0, PA_F16 = 1, PA_F64 = 2 } pa_dtype;
 
 /* Regular grid of pixel centres (Sec. 3.4: r_ij, the Cartesian pixel
@@ -98,15 +98,20 @@ typedef struct {
 /* Reconstruction settings (fill with pa_recon_opts_default first).
  *   omega        Landweber step.  <= 0: 1/sigma^2 with sigma^2 = largest
  *                eigenvalue of A^T A from power_iters power-iteration steps.
+ *                FISTA: the step tau; <= 0: 1/(2 sigma^2 + 8 tv_weight/tv_eps)
+ *                (the inverse Lipschitz bound of the smooth part, 2D).
  *   nonneg       1: x >= 0 (Landweber: projection every step; CGLS: once at the
- *                end, after the unconstrained iterations).
+ *                end, after the unconstrained iterations; FISTA: inside the
+ *                proximal step).
  *   power_iters  steps of the power iteration when omega <= 0 (default 50).
  *   power_v0_dev start vector [N] float32 on the device, or NULL for all ones.
  *   residual_history_host  NULL, or n_iter+1 doubles receiving ||y - A x_n||^2
  *                for n = 0..n_iter; when given, the call waits for the stream.
  *   use_graph    1: the iteration is captured once as a CUDA graph and replayed.
  *   kernel_timing 1: CUDA events bracket every A and A^T gather launch; read the
- *                totals with pa_plan_kernel_times after the stream finished. */
+ *                totals with pa_plan_kernel_times after the stream finished.
+ *   l1_weight, tv_weight, tv_eps  FISTA only: the alpha and beta of Eq. 8 and the
+ *                smoothing of its TV term (defaults 0, 0, 1e-4). */
 typedef struct {
   double omega;
   int nonneg;
@@ -115,6 +120,9 @@ typedef struct {
   double *residual_history_host;
   int use_graph;
   int kernel_timing;
+  double l1_weight;
+  double tv_weight;
+  double tv_eps;
 } pa_recon_opts;
 
 /* Facts about a plan (sizes, tiling, memory), for logging and benchmarks. */
@@ -222,7 +230,16 @@ pa_status pa_dc(pa_plan *plan, const float *x_dev, const float *g_dev, double *d
 pa_status pa_tv(pa_plan *plan, const float *x_dev, double eps, double *tv_dev, float *grad_dev,
                 pa_stream stream);
 
-/* Iterative reconstruction minimising ||A x - y||^2 (Eq. 8 data term).
+/* Iterative reconstruction.  PA_LANDWEBER and PA_CGLS minimise ||A x - y||^2
+ * (the data term of Eq. 8).  PA_FISTA minimises the full objective of Eq. 8
+ * with Phi = A and Psi' = identity,
+ *     F(x) = ||A x - y||^2 + l1_weight ||x||_1 + tv_weight TV_eps(x)
+ * (TV_eps as in pa_tv), by the fast iterative shrinkage-thresholding
+ * algorithm (Beck and Teboulle, SIAM J. Imaging Sci. 2, 183, 2009): a gradient
+ * step on the smooth part at the extrapolated point z, the proximal step of
+ * the L1 term (soft threshold; with nonneg, max(0, v - tau l1_weight)), then
+ * z = x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1}).  Its residual history holds
+ * ||y - A z_n||^2 for n < n_iter and ||y - A x_n||^2 last.
  * y_dev: [S][K] measured traces in the plan's y_dtype; x_dev: [N] float32, in:
  * start image x_0, out: result.  n_iter >= 0.  opts may be NULL (defaults). */
 pa_status pa_reconstruct(pa_plan *plan, pa_method method, int n_iter, const void *y_dev,

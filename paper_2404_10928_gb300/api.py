@@ -13,9 +13,10 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_F64, PA_LANDWEBER, check
+from ._lib import (PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_F64, PA_FISTA,
+                   PA_LANDWEBER, check)
 
-METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS}
+METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS, "fista": PA_FISTA}
 BP_FILTERS = {"none": PA_BP_NONE, "ubp": PA_BP_UBP}
 _DENSE_DTYPES = {torch.float64: PA_F64, torch.float32: PA_F32}
 
@@ -208,9 +209,13 @@ class Plan:
               "pa_power_iteration")
         return out.value
 
-    def _opts(self, omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing):
+    def _opts(self, omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing,
+              l1=0.0, tv=0.0, tv_eps=1e-4):
         o = _lib.pa_recon_opts()
         self._lib.pa_recon_opts_default(ctypes.byref(o))
+        o.l1_weight = float(l1)
+        o.tv_weight = float(tv)
+        o.tv_eps = float(tv_eps)
         o.omega = float(omega)
         o.nonneg = int(bool(nonneg))
         o.power_iters = int(power_iters)
@@ -225,8 +230,10 @@ class Plan:
                     x0: Optional[torch.Tensor] = None, omega: float = 0.0, nonneg: bool = True,
                     power_iters: int = 50, power_v0: Optional[torch.Tensor] = None,
                     history: bool = False, use_graph: bool = True, kernel_timing: bool = False,
-                    out: Optional[torch.Tensor] = None):
-        """Minimise ||A x - y||^2 (Landweber with projection, or CGLS + final clamp).
+                    out: Optional[torch.Tensor] = None, l1: float = 0.0, tv: float = 0.0,
+                    tv_eps: float = 1e-4):
+        """Minimise ||A x - y||^2 (Landweber with projection, or CGLS + final clamp),
+        or with method "fista" ||A x - y||^2 + l1 ||x||_1 + tv TV_eps(x) (Eq. 8).
 
         Returns x (and the residual history ||y - A x_n||^2, n = 0..n_iter, when
         ``history`` is set).  ``out`` (if given) is used in place: its contents
@@ -242,7 +249,8 @@ class Plan:
         if power_v0 is not None:
             self._check_tensor(power_v0, self.n_pixels, "power_v0")
         hist = np.zeros(n_iter + 1) if history else None
-        o = self._opts(omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing)
+        o = self._opts(omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing,
+                       l1, tv, tv_eps)
         check(self._lib.pa_reconstruct(self._h, METHODS[method], int(n_iter), y.data_ptr(),
                                        out.data_ptr(), ctypes.byref(o),
                                        _stream_handle(self.device)), "pa_reconstruct")

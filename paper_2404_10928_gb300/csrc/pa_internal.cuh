@@ -110,7 +110,7 @@ struct GridF {
 enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3, OP_STORE = 4 };
 
 // kernel modes
-enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3 };
+enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3, ADJ_FISTA = 4 };
 enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
 
 // Cross-CTA FP64 reduction finished inside the producing kernel: every CTA
@@ -140,6 +140,12 @@ struct AdjParams {
   Reduce red;             // ||out||^2 (ADJ_NORM)
   int* err;
   int sensors_per_rank;
+  // ADJ_FISTA (out = x_k, updated in place; omega = the step tau): with g =
+  // A^T r, r = y - A z, v = z + tau (2 g - tv_beta tvg), x_new = prox(v), and
+  // z = x_new + mu (x_new - x_k), both in place
+  float* z;
+  const float* tvg;       // gradient of TV_eps at z
+  float l1, tv_beta, mu;
 };
 
 struct FwdParams {
@@ -257,6 +263,8 @@ cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
+// *tau = 1 / (2 / *inv_lam + c_tv): the FISTA step from the power iteration
+cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
 cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
@@ -327,7 +335,8 @@ struct pa_plan {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> fwd_ev, adj_ev;  // pairs (start, stop)
   };
-  std::map<std::tuple<int, int, const void*, float*, double, int, int, const float*, int>,
+  std::map<std::tuple<int, int, const void*, float*, double, int, int, const float*, int, double,
+                      double, double>,
            GraphEntry>
       graphs;
   GraphEntry direct;                 // timing events of runs without a graph

@@ -805,6 +805,17 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
         float xv = fmaf((float)(*P.omega), gval, P.out[i]);
         if (P.nonneg) xv = fmaxf(xv, 0.0f);
         P.out[i] = xv;
+      } else if (P.mode == ADJ_FISTA) {
+        // gradient step on ||A z - y||^2 + beta TV(z) at z, proximal step of
+        // tau l1 ||.||_1 (and x >= 0), then the extrapolation
+        const float tau = (float)(*P.omega);
+        const float zi = P.z[i];
+        const float v = fmaf(tau, fmaf(2.0f, gval, -P.tv_beta * P.tvg[i]), zi);
+        const float thr = tau * P.l1;
+        const float xn = P.nonneg ? fmaxf(v - thr, 0.0f) : copysignf(fmaxf(fabsf(v) - thr, 0.0f), v);
+        const float xo = P.out[i];
+        P.out[i] = xn;
+        P.z[i] = fmaf(P.mu, xn - xo, xn);
       } else {
         P.out[i] = gval;
         part = df_add(part, df_sq(gval));
@@ -1384,6 +1395,14 @@ cudaError_t launch_clamp(float* x, int N, cudaStream_t st) {
 }
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st) {
   return launch_k(k_set_scalar, dim3(1), dim3(1), 0, st, 0, dst, value);
+}
+
+__global__ void k_fista_tau(double* tau, const double* inv_lam, double c_tv) {
+  const double il = *inv_lam;
+  *tau = il > 0.0 ? 1.0 / (2.0 / il + c_tv) : 0.0;
+}
+cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st) {
+  return launch_k(k_fista_tau, dim3(1), dim3(1), 0, st, 0, tau, inv_lam, c_tv);
 }
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
   return launch_k(k_fill, dim3(vec_blocks(n)), dim3(kVecThreads), 0, st, 0, dst, value, n);

@@ -200,6 +200,9 @@ void pa_recon_opts_default(pa_recon_opts* o) {
   o->residual_history_host = nullptr;
   o->use_graph = 1;
   o->kernel_timing = 0;
+  o->l1_weight = 0.0;
+  o->tv_weight = 0.0;
+  o->tv_eps = 1e-4;
 }
 
 pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors,

@@ -2,6 +2,7 @@
 // all-device sequence of kernels (scalars stay in device memory, no host
 // synchronisation inside the loop) that is captured once as a CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <utility>
 
@@ -275,10 +276,55 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
   return PA_OK;
 }
 
+// FISTA on F(x) = ||A x - y||^2 + alpha ||x||_1 + beta TV_eps(x) (Eq. 8 with
+// Phi = A, Psi' = I): per iteration r = y - A z (||r||^2 -> history), the TV
+// gradient at z, then A^T r with the proximal step and the extrapolation in the
+// adjoint's epilogue.  The momentum weights (t_k - 1)/t_{k+1} depend on k only
+// and are baked into the launches.
+pa_status enqueue_fista(pa_plan* p, int n_iter, const void* y, float* x, const pa_recon_opts& o,
+                        const Scalars& sc, Timing& t, cudaStream_t st) {
+  const int N = p->grid.nx * p->grid.ny * p->grid.nz;
+  if (o.omega > 0.0) {
+    PA_CUDA(launch_set_scalar(sc.omega, o.omega, st));
+  } else {
+    PA_TRY(enqueue_power(p, o.power_iters > 0 ? o.power_iters : 50, o.power_v0_dev, sc, t, st));
+    PA_CUDA(launch_fista_tau(sc.omega, sc.inv_lam, 8.0 * o.tv_weight / o.tv_eps, st));
+  }
+  float* z = p->d_pv;
+  float* tvg = p->d_sv;
+  PA_CUDA(cudaMemcpyAsync(z, x, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
+  double tk = 1.0;
+  for (int it = 0; it < n_iter; ++it) {
+    PA_TRY(fwd(p, z, p->d_ra, FWD_RESID, y, stored(p->d_parts_h + (size_t)it * p->n_partials), t,
+               st));
+    PA_CUDA(launch_pack(p->d_ra, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+    if (o.tv_weight != 0.0)
+      PA_CUDA(launch_tv(p->dim, z, p->grid.nx, p->grid.ny, p->grid.nz, (float)o.tv_eps, tvg,
+                        stored(p->d_parts_q), st));
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * tk * tk));
+    AdjParams a = adjoint_params(p, x, ADJ_FISTA, sc.omega, o.nonneg);
+    a.z = z;
+    a.tvg = o.tv_weight != 0.0 ? tvg : z;  // unused when tv_beta = 0
+    a.l1 = (float)o.l1_weight;
+    a.tv_beta = (float)o.tv_weight;
+    a.mu = (float)((tk - 1.0) / tn);
+    PA_TRY(mark(t, false, st));
+    PA_CUDA(launch_adjoint(p->dim, a, p->cluster, p->ntiles, st));
+    PA_TRY(mark(t, false, st));
+    tk = tn;
+  }
+  PA_TRY(fwd(p, x, p->d_ra, FWD_RESID, y,
+             stored(p->d_parts_h + (size_t)n_iter * p->n_partials), t, st));
+  PA_CUDA(launch_hist(p->d_parts_h, p->n_partials, n_comb, n_comb, n_iter + 1, sc.hist, st));
+  return PA_OK;
+}
+
 pa_status enqueue_recon(pa_plan* p, pa_method method, int n_iter, const void* y, float* x,
                         const pa_recon_opts& o, Timing& t, cudaStream_t st) {
   const Scalars sc = scalars(p, n_iter);
   if (method == PA_LANDWEBER) return enqueue_landweber(p, n_iter, y, x, o, sc, t, st);
+  if (method == PA_FISTA) return enqueue_fista(p, n_iter, y, x, o, sc, t, st);
   return enqueue_cgls(p, n_iter, y, x, o, sc, t, st);
 }
 
@@ -323,14 +369,16 @@ pa_status pa_power_iteration(pa_plan* plan, int n_iter, const float* v0_dev, dou
 pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void* y_dev,
                          float* x_dev, const pa_recon_opts* opts, pa_stream stream) {
   if (!plan || !y_dev || !x_dev || n_iter < 0 ||
-      (method != PA_LANDWEBER && method != PA_CGLS)) {
+      (method != PA_LANDWEBER && method != PA_CGLS && method != PA_FISTA)) {
     set_error("pa_reconstruct: invalid argument");
     return PA_ERR_INVALID_ARG;
   }
   pa_recon_opts o;
   pa_recon_opts_default(&o);
   if (opts) o = *opts;
-  if (!std::isfinite(o.omega) || o.power_iters < 0) {
+  if (!std::isfinite(o.omega) || o.power_iters < 0 || !std::isfinite(o.l1_weight) ||
+      o.l1_weight < 0.0 || !std::isfinite(o.tv_weight) || o.tv_weight < 0.0 ||
+      !(o.tv_eps > 0.0) || !std::isfinite(o.tv_eps)) {
     set_error("pa_reconstruct: invalid options");
     return PA_ERR_INVALID_ARG;
   }
@@ -342,7 +390,8 @@ pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void
 
   if (o.use_graph) {
     const auto key = std::make_tuple((int)method, n_iter, y_dev, x_dev, o.omega, o.nonneg,
-                                     o.power_iters, o.power_v0_dev, o.kernel_timing);
+                                     o.power_iters, o.power_v0_dev, o.kernel_timing,
+                                     o.l1_weight, o.tv_weight, o.tv_eps);
     auto it = plan->graphs.find(key);
     if (it == plan->graphs.end()) {
       pa_plan::GraphEntry entry;

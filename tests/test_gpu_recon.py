@@ -180,3 +180,39 @@ def test_cgls_3d_small(torch_cuda):
     assert np.max(np.abs(gh30 - h30)) <= 5e-3 * h30[0]
     assert np.all(np.diff(gh30) <= 1e-7 * gh30[0])
     assert rel_l2(g30, prob.x_true) <= 2.0 * rel_l2(x30, prob.x_true)
+
+
+@pytest.mark.parametrize("alpha_rel,beta_rel,nonneg", [(0.02, 0.0, True), (0.02, 0.05, True),
+                                                       (0.01, 0.05, False)])
+def test_fista_full_objective(torch_cuda, disks, alpha_rel, beta_rel, nonneg):
+    """30 FISTA steps on the full objective of Eq. 8 (data, L1 and smoothed TV)."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    eps = 1e-2
+    alpha = alpha_rel * float(np.abs(orc.adjoint(geo, y)).max())
+    beta = beta_rel * lam * eps  # TV curvature 8 beta / eps: 0.4 of the data term's 2 lam
+    tau = 1.0 / (2.0 * lam + 8.0 * beta / eps)
+    x_ref, h_ref = orc.fista(geo, y, 30, tau, alpha, beta, eps, nonneg=nonneg)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "fista", 30, omega=tau, nonneg=nonneg,
+                                history=True, l1=alpha, tv=beta, tv_eps=eps)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL, atol=RECON_TOL * h_ref[0])
+    if nonneg:
+        assert x.min() >= 0.0
+
+
+def test_fista_default_step_from_power_iteration(torch_cuda, disks):
+    # omega <= 0: tau = 1 / (2 sigma^2 + 8 beta / eps), sigma^2 from the power iteration
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    eps, beta = 1e-2, 0.05 * lam * 1e-2
+    alpha = 0.02 * float(np.abs(orc.adjoint(geo, y)).max())
+    tau = 1.0 / (2.0 * lam + 8.0 * beta / eps)
+    x_ref, _ = orc.fista(geo, y, 20, tau, alpha, beta, eps)
+    with _plan(prob) as plan:
+        x = plan.reconstruct(_dev(torch, y), "fista", 20, omega=0.0, power_iters=50,
+                             power_v0=_dev(torch, v0), l1=alpha, tv=beta, tv_eps=eps)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)

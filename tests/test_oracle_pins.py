@@ -293,3 +293,66 @@ def test_backproject_is_adjoint_of_filtered_traces():
     rhs = float(np.sum(orc.ubp_filter(p, geo.t0, geo.fs) * orc.forward(geo, x)))
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
     assert np.array_equal(orc.backproject(geo, p, "none"), orc.adjoint(geo, p))
+
+
+def _tiny_fista_problem(seed):
+    prob = ph.custom(2, (5, 4), (1e-4, 1e-4), ph.ring_sensors(6, 1.5e-3), 70, seed=seed)
+    geo = orc.Geometry.of(prob)
+    m = orc.matrix(geo)
+    sigma2 = float(np.linalg.svd(m, compute_uv=False)[0] ** 2)
+    return prob, geo, m, sigma2
+
+
+def test_fista_unregularised_reaches_lstsq():
+    # alpha = beta = 0, no projection: FISTA minimises ||A x - y||^2
+    prob, geo, m, sigma2 = _tiny_fista_problem(31)
+    rng = np.random.default_rng(32)
+    y = m @ rng.uniform(0.2, 1.0, prob.n_pixels) + 0.01 * rng.standard_normal(m.shape[0])
+    x, hist = orc.fista(geo, y, 4000, tau=1.0 / (2.0 * sigma2), nonneg=False)
+    ref = np.linalg.lstsq(m, y, rcond=None)[0]
+    assert np.allclose(x, ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+    assert hist[-1] <= hist[0]
+
+
+def test_fista_meets_the_optimality_conditions():
+    # minimiser of ||A x - y||^2 + alpha ||x||_1 + beta TV_eps(x) over x >= 0: with
+    # G the gradient of the smooth part, G_i + alpha = 0 where x_i > 0 and
+    # G_i + alpha >= 0 where x_i = 0 (KKT)
+    prob, geo, m, sigma2 = _tiny_fista_problem(33)
+    rng = np.random.default_rng(34)
+    truth = np.where(rng.uniform(size=prob.n_pixels) < 0.5, rng.uniform(0.5, 1.0, prob.n_pixels), 0.0)
+    y = m @ truth + 0.02 * rng.standard_normal(m.shape[0])
+    # beta such that the TV term's curvature bound 8 beta / eps is half the data
+    # term's 2 sigma^2: both terms shape the minimiser
+    alpha, eps = 0.05 * np.abs(m.T @ y).max(), 1e-2
+    beta = 0.125 * sigma2 * eps
+    tau = 1.0 / (2.0 * sigma2 + 8.0 * beta / eps)
+    x, _ = orc.fista(geo, y, 20000, tau, alpha, beta, eps)
+    nx, ny, _ = prob.shape
+    g = -2.0 * m.T @ (y - m @ x) + beta * orc.tv_grad(x.reshape(ny, nx), eps).ravel()
+    scale = alpha + np.abs(g).max()
+    active = x > 1e-12 * np.abs(x).max()
+    assert active.any() and (~active).any()  # both cases are exercised
+    assert np.all(np.abs(g[active] + alpha) <= 1e-6 * scale)
+    assert np.all(g[~active] + alpha >= -1e-6 * scale)
+
+
+def test_fista_momentum_beats_plain_shrinkage():
+    # the extrapolation is what makes FISTA O(1/k^2): after a few dozen steps on
+    # an ill-conditioned problem its objective is below that of the same
+    # proximal steps without momentum (ISTA)
+    prob, geo, m, sigma2 = _tiny_fista_problem(35)
+    rng = np.random.default_rng(36)
+    y = m @ rng.uniform(0.0, 1.0, prob.n_pixels)
+    tau, alpha = 1.0 / (2.0 * sigma2), 1e-3 * np.abs(m.T @ y).max()
+
+    def objective(x):
+        return float(np.sum((m @ x - y) ** 2) + alpha * np.abs(x).sum())
+
+    f_star = objective(orc.fista(geo, y, 20000, tau, alpha)[0])
+    x_f, _ = orc.fista(geo, y, 40, tau, alpha)
+    x_i = np.zeros(prob.n_pixels)  # ISTA: the same step, no extrapolation
+    for _ in range(40):
+        v = x_i - tau * (-2.0 * m.T @ (y - m @ x_i))
+        x_i = np.maximum(v - tau * alpha, 0.0)
+    assert objective(x_f) - f_star < 0.5 * (objective(x_i) - f_star)
