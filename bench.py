@@ -56,6 +56,30 @@ def cgls_launches(n_iter: int) -> int:
     return 4 + 4 * n_iter + 2
 
 
+def max_over_ranks(dist, device, value: float) -> float:
+    """The largest of every rank's `value` (the job's clock is its slowest
+    rank); the value itself when not distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed per second of the job's clock (weak scaling:
+    every rank processes units_per_rank)."""
+    return units_per_rank * world / seconds
+
+
+def frame_noise(shape, rank: int) -> np.ndarray:
+    """Each rank reconstructs its own frame: the benchmark geometry with its own
+    noise draw (frames are independent, so they shard across ranks with no
+    exchange)."""
+    return np.random.default_rng(2003 + rank).standard_normal(shape)
+
+
 def cgls_applications(n_iter: int) -> int:
     return 2 + 2 * n_iter
 
@@ -461,7 +485,7 @@ def run_gpu(args):
 
     prob = ph.ring_vessels(seed=1002)
     # each rank reconstructs its own frame (same geometry, its own noise draw)
-    noise = np.random.default_rng(2003 + rank).standard_normal(prob.noise_unit.shape)
+    noise = frame_noise(prob.noise_unit.shape, rank)
     from paper_2404_10928_gb300.autotune import Autotuner
     tuner = Autotuner(os.path.join(ROOT, "gpurun_out", f"autotune_rank{rank}.json"))
     tuned = tuner.best(prob)
@@ -511,14 +535,10 @@ def run_gpu(args):
             dist.barrier()
         t_wall = time.perf_counter() - t_wall
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, dev, sum(step_ms))
     apps = cgls_applications(N_ITER)
-    pairs_all = prob.pairs * apps * args.steps * world
-    value = pairs_all / (total_ms * 1e-3)
+    pairs_rank = prob.pairs * apps * args.steps
+    value = whole_job_rate(pairs_rank, world, total_ms * 1e-3)
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     y_pin = torch.empty(y_host.shape, dtype=torch.float32).pin_memory()
@@ -533,12 +553,8 @@ def run_gpu(args):
     for _ in range(args.steps):
         x_np[:] = 0
         plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)
-    e2e_t = time.perf_counter() - e2e_t
-    if dist:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = pairs_all / e2e_t
+    e2e_t = max_over_ranks(dist, dev, time.perf_counter() - e2e_t)
+    e2e_value = whole_job_rate(pairs_rank, world, e2e_t)
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
