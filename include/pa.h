@@ -206,6 +206,25 @@ pa_status pa_dense_assemble(pa_plan *plan, int dtype, void *m_dev, pa_stream str
 pa_status pa_dense_matvec(pa_plan *plan, int dtype, const void *m_dev, int transpose,
                           const void *v_dev, void *out_dev, pa_stream stream);
 
+/* Frequency-domain model (Eq. 7, the alternative system model of Sec. 3.4):
+ *     K(m,n)_i = i c k_n exp(-i k_n |r_i - r_m|) / |r_i - r_m|,  k_n = 2 pi f_n / c,
+ * at n_freq frequencies f_n = f0 + n df (the paper gives q_n frequency samples
+ * without their values).  pa_freq_forward: P[m][n] = amp sum_i K(m,n)_i x_i;
+ * x_dev [N] float32, p_dev [S][n_freq][2] float32 (re, im), fully overwritten.
+ * pa_freq_adjoint: its adjoint for the real inner product Re sum conj(P) Q,
+ *     x_i = amp / d_im sum_{m,n} c k_n Im(exp(i k_n d_im) P[m][n]);
+ * p_dev [S][n_freq][2], x_dev [N], fully overwritten.  Arithmetic is FP32 with
+ * the phase split into an FP64 per-(tile, sensor) part and an FP32 per-pixel
+ * difference, which bounds the phase error by about 2 pi f_max |pixel - tile
+ * centre| / c * 2^-24.  1 <= n_freq <= 65536 (the adjoint stages n_freq complex
+ * values in shared memory: at most 25600); f0, df >= 0.  The first call, or a
+ * call needing more workspace than earlier ones, allocates the plan's
+ * workspace: make it outside stream capture. */
+pa_status pa_freq_forward(pa_plan *plan, int n_freq, double f0, double df, const float *x_dev,
+                          float *p_dev, pa_stream stream);
+pa_status pa_freq_adjoint(pa_plan *plan, int n_freq, double f0, double df, const float *p_dev,
+                          float *x_dev, pa_stream stream);
+
 /* Largest eigenvalue of A^T A by n_iter power-iteration steps from v0_dev ([N]
  * float32, NULL = ones).  Blocks; *sigma2 receives the estimate. */
 pa_status pa_power_iteration(pa_plan *plan, int n_iter, const float *v0_dev, double *sigma2,

@@ -21,6 +21,8 @@ What is computed, and where it comes from:
 * ``power_iteration``: largest eigenvalue of A^T A (step size for Landweber).
 * ``tv`` / ``tv_grad``: smoothed isotropic total variation (the TV term of
   Eq. 8 with Psi' = identity).
+* ``freq_forward`` / ``freq_adjoint``: the frequency-domain measurement matrix
+  of Eq. 7 applied to an image, and its adjoint (own loops).
 * ``fista``: the full objective of Eq. 8 (data term, L1 and smoothed TV) by
   FISTA with a fixed step.
 * ``ubp_filter`` / ``backproject``: the back-projection reconstruction timed
@@ -76,6 +78,13 @@ def _load():
             lib.oracle_dc.restype = ctypes.c_double
             lib.oracle_dc_flip_bound.argtypes = geo + [dp, dp, ctypes.c_double]
             lib.oracle_dc_flip_bound.restype = ctypes.c_double
+            fgeo = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                    ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                    ctypes.c_double, ctypes.c_double]
+            for name in ("oracle_freq_forward", "oracle_freq_adjoint"):
+                fn = getattr(lib, name)
+                fn.argtypes = fgeo + [dp, dp]
+                fn.restype = None
             lib.oracle_min_distance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.oracle_min_distance.restype = ctypes.c_double
@@ -149,6 +158,31 @@ def adjoint(geo: Geometry, p, c=None) -> np.ndarray:
     p = _f64(p).reshape(geo.n_sensors, geo.n_samples)
     g = np.empty(geo.n_pixels)
     _load().oracle_adjoint(*geo._args(c), _ptr(p), _ptr(g))
+    return g
+
+
+def _freq_args(geo: Geometry, q: int, f0: float, df: float):
+    nx, ny, nz = geo.shape
+    return (geo.dim, nx, ny, nz, _ptr(geo.spacing), _ptr(geo.origin), _ptr(geo.sensors),
+            geo.n_sensors, geo.c, geo.amp, int(q), float(f0), float(df))
+
+
+def freq_forward(geo: Geometry, x, q: int, f0: float, df: float) -> np.ndarray:
+    """The frequency-domain model of Eq. 7: P[m][n] = amp sum_i x_i i c k_n
+    exp(-i k_n d_im) / d_im at f_n = f0 + n df (a reading: the paper gives q_n
+    frequency samples without their values).  Returns complex [S][q]."""
+    x = _f64(x).ravel()
+    p = np.empty((geo.n_sensors, q, 2))
+    _load().oracle_freq_forward(*_freq_args(geo, q, f0, df), _ptr(x), _ptr(p))
+    return p[..., 0] + 1j * p[..., 1]
+
+
+def freq_adjoint(geo: Geometry, p, q: int, f0: float, df: float) -> np.ndarray:
+    """Adjoint of freq_forward for the real inner product Re sum conj(P) Q."""
+    p = np.asarray(p, dtype=np.complex128).reshape(geo.n_sensors, q)
+    pp = np.ascontiguousarray(np.stack([p.real, p.imag], axis=-1))
+    g = np.empty(geo.n_pixels)
+    _load().oracle_freq_adjoint(*_freq_args(geo, q, f0, df), _ptr(pp), _ptr(g))
     return g
 
 

@@ -229,3 +229,74 @@ double oracle_min_distance(int dim, int nx, int ny, int nz, const double *spacin
   }
   return best;
 }
+
+/*
+ * Frequency-domain measurement matrix (Eq. 7):
+ *   K(m,n)_i = i c k_n exp(-i k_n |r_i - r_m|) / |r_i - r_m|,  k_n = 2 pi f_n / c,
+ * at the frequencies f_n = f0 + n df, n = 0..q-1.  The forward map of a real
+ * image is P[m][n] = amp sum_i K(m,n)_i x_i, stored as [S][q][2] (re, im).
+ * The phase is reduced in cycles (f_n d / c minus its integer part) before the
+ * trigonometric functions, so it keeps FP64 accuracy at large k d.
+ */
+void oracle_freq_forward(int dim, int nx, int ny, int nz, const double *spacing,
+                         const double *origin, const double *sensors, int n_sensors, double c,
+                         double amp, int q, double f0, double df, const double *x, double *p) {
+  long n_pix = (long)nx * ny * nz;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < n_sensors; ++s) {
+    const double *rs = sensors + (long)s * dim;
+    for (int n = 0; n < q; ++n) {
+      double fn = f0 + (double)n * df;
+      double kn = 2.0 * M_PI * fn / c;
+      double re = 0.0, im = 0.0;
+      for (long i = 0; i < n_pix; ++i) {
+        if (x[i] == 0.0) continue;
+        double pos[3];
+        pixel_position(i, nx, ny, spacing, origin, pos);
+        double d = distance(dim, pos, rs);
+        double cyc = fn * d / c;
+        cyc -= floor(cyc);
+        double ph = 2.0 * M_PI * cyc; /* k_n d modulo 2 pi */
+        /* i c k_n exp(-i ph) = c k_n (sin ph + i cos ph) */
+        re += x[i] * sin(ph) / d;
+        im += x[i] * cos(ph) / d;
+      }
+      p[((long)s * q + n) * 2 + 0] = amp * c * kn * re;
+      p[((long)s * q + n) * 2 + 1] = amp * c * kn * im;
+    }
+  }
+}
+
+/*
+ * Its adjoint for the real inner product <P, Q> = Re sum conj(P) Q:
+ *   g_i = amp sum_{m,n} Re( conj(K(m,n)_i) P[m][n] )
+ *       = amp sum_{m,n} c k_n Im( exp(i k_n d_im) P[m][n] ) / d_im.
+ * Written as its own loop over pixels.
+ */
+void oracle_freq_adjoint(int dim, int nx, int ny, int nz, const double *spacing,
+                         const double *origin, const double *sensors, int n_sensors, double c,
+                         double amp, int q, double f0, double df, const double *p, double *g) {
+  long n_pix = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < n_pix; ++i) {
+    double pos[3];
+    pixel_position(i, nx, ny, spacing, origin, pos);
+    double acc = 0.0;
+    for (int s = 0; s < n_sensors; ++s) {
+      double d = distance(dim, pos, sensors + (long)s * dim);
+      double v = 0.0;
+      for (int n = 0; n < q; ++n) {
+        double fn = f0 + (double)n * df;
+        double kn = 2.0 * M_PI * fn / c;
+        double cyc = fn * d / c;
+        cyc -= floor(cyc);
+        double ph = 2.0 * M_PI * cyc;
+        double pr = p[((long)s * q + n) * 2 + 0], pi = p[((long)s * q + n) * 2 + 1];
+        /* Im((cos ph + i sin ph)(pr + i pi)) = cos ph pi + sin ph pr */
+        v += c * kn * (cos(ph) * pi + sin(ph) * pr);
+      }
+      acc += v / d;
+    }
+    g[i] = amp * acc;
+  }
+}

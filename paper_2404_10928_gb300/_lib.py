@@ -74,6 +74,8 @@ SIGNATURES = {
     "pa_adjoint": (c_int, [_P, c_void_p, c_void_p, _STREAM]),
     "pa_backproject": (c_int, [_P, c_void_p, c_int, c_void_p, _STREAM]),
     "pa_dense_assemble": (c_int, [_P, c_int, c_void_p, _STREAM]),
+    "pa_freq_forward": (c_int, [_P, c_int, c_double, c_double, c_void_p, c_void_p, _STREAM]),
+    "pa_freq_adjoint": (c_int, [_P, c_int, c_double, c_double, c_void_p, c_void_p, _STREAM]),
     "pa_dense_matvec": (c_int, [_P, c_int, c_void_p, c_int, c_void_p, c_void_p, _STREAM]),
     "pa_power_iteration": (c_int, [_P, c_int, c_void_p, _DP, _STREAM]),
     "pa_reconstruct": (c_int, [_P, c_int, c_int, c_void_p, c_void_p,

@@ -145,6 +145,35 @@ class Plan:
                                        _stream_handle(self.device)), "pa_backproject")
         return out
 
+    # -- frequency-domain model (Eq. 7; see pa_freq_forward / pa_freq_adjoint) --
+    def freq_forward(self, x: torch.Tensor, n_freq: int, f0: float, df: float,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """P = K x: [N] image -> [S][n_freq] complex64 spectra at f0 + n df."""
+        self._check_tensor(x, self.n_pixels, "x")
+        if out is None:
+            out = torch.empty((self.n_sensors, n_freq), dtype=torch.complex64, device=self.device)
+        if out.dtype != torch.complex64 or not out.is_contiguous() or \
+                out.numel() != self.n_sensors * n_freq or out.device != self.device:
+            raise ValueError("out must be a contiguous complex64 [S][n_freq] tensor on the device")
+        check(self._lib.pa_freq_forward(self._h, int(n_freq), float(f0), float(df), x.data_ptr(),
+                                        out.data_ptr(), _stream_handle(self.device)),
+              "pa_freq_forward")
+        return out
+
+    def freq_adjoint(self, p: torch.Tensor, n_freq: int, f0: float, df: float,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """x = K^H p (real part): [S][n_freq] complex64 -> [N] image."""
+        if p.dtype != torch.complex64 or not p.is_contiguous() or \
+                p.numel() != self.n_sensors * n_freq or p.device != self.device:
+            raise ValueError("p must be a contiguous complex64 [S][n_freq] tensor on the device")
+        if out is None:
+            out = torch.empty(self.n_pixels, dtype=torch.float32, device=self.device)
+        self._check_tensor(out, self.n_pixels, "out")
+        check(self._lib.pa_freq_adjoint(self._h, int(n_freq), float(f0), float(df), p.data_ptr(),
+                                        out.data_ptr(), _stream_handle(self.device)),
+              "pa_freq_adjoint")
+        return out
+
     # -- dense-matrix mode (see pa_dense_assemble / pa_dense_matvec) ---------
     def dense_assemble(self, dtype: torch.dtype = torch.float64,
                        out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -9,8 +9,11 @@ RECON_TOL = 1e-4  # after a full reconstruction
 
 
 def rel_l2(a, b) -> float:
-    a = np.asarray(a, dtype=np.float64).ravel()
-    b = np.asarray(b, dtype=np.float64).ravel()
+    """||a - b|| / ||b|| (complex arrays compare as complex)."""
+    cplx = np.iscomplexobj(a) or np.iscomplexobj(b)
+    dt = np.complex128 if cplx else np.float64
+    a = np.asarray(a, dtype=dt).ravel()
+    b = np.asarray(b, dtype=dt).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 

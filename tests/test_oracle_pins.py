@@ -356,3 +356,28 @@ def test_fista_momentum_beats_plain_shrinkage():
         v = x_i - tau * (-2.0 * m.T @ (y - m @ x_i))
         x_i = np.maximum(v - tau * alpha, 0.0)
     assert objective(x_f) - f_star < 0.5 * (objective(x_i) - f_star)
+
+
+def test_freq_single_pixel_hand_values():
+    # Eq. 7 for one pixel 3 mm from the sensor, c = 1500 m/s, amp = 1:
+    #   f = 1 MHz:    f d / c = 2 cycles, exp(-i k d) = 1,  P = i c k / d = i 2 pi f / d
+    #   f = 1.125 MHz: 2.25 cycles, exp(-i k d) = -i,    P = c k / d = 2 pi f / d (real)
+    geo = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                       np.array([[0.0, 3e-3]]), 1500.0, 40e6, 16)
+    p = orc.freq_forward(geo, np.ones(1), 2, 1.0e6, 0.125e6)[0]
+    two_pi_over_d = 2 * np.pi / 3e-3
+    assert abs(p[0] - 1j * two_pi_over_d * 1.0e6) <= 1e-9 * two_pi_over_d * 1e6
+    assert abs(p[1] - two_pi_over_d * 1.125e6) <= 1e-9 * two_pi_over_d * 1e6
+
+
+def test_freq_adjoint_identity():
+    # <K x, P> = <x, K^H P> between the two independently written loops
+    prob = ph.custom(2, (9, 7), (1e-4, 1e-4), ph.ring_sensors(5, 2e-3), 50, seed=41)
+    geo = orc.Geometry.of(prob)
+    rng = np.random.default_rng(42)
+    x = rng.standard_normal(prob.n_pixels)
+    q = 11
+    pq = rng.standard_normal((5, q)) + 1j * rng.standard_normal((5, q))
+    lhs = float(np.real(np.sum(np.conj(orc.freq_forward(geo, x, q, 0.5e6, 1.7e6)) * pq)))
+    rhs = float(np.dot(x, orc.freq_adjoint(geo, pq, q, 0.5e6, 1.7e6)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
