@@ -424,6 +424,36 @@ def bench_dense(torch, hbm_gbs: float, reps: int = 10) -> dict:
     return out
 
 
+def bench_freq(torch, peak_tflops: float, reps: int = 5) -> dict:
+    """The frequency-domain model of Eq. 7 on the 256^2 ring geometry at 256
+    frequencies (78 kHz steps up to 20 MHz): forward and adjoint rates in
+    pixel-sensor-frequency terms.  Each term costs one complex multiply (the
+    phase recurrence) and one complex-by-real accumulate: 10 flop."""
+    from paper_2404_10928_gb300 import phantoms as ph
+    from paper_2404_10928_gb300.api import Plan
+    prob = ph.ring_vessels()
+    q, f0, df = 256, 78125.0, 78125.0
+    plan = Plan.from_problem(prob)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(prob.n_pixels, device="cuda", generator=g)
+    p = torch.empty((prob.n_sensors, q), dtype=torch.complex64, device="cuda")
+    z = torch.empty(prob.n_pixels, device="cuda")
+    plan.freq_forward(x, q, f0, df, out=p)
+    plan.freq_adjoint(p, q, f0, df, out=z)
+    t_f = _events_time(torch, lambda: plan.freq_forward(x, q, f0, df, out=p), reps)
+    t_a = _events_time(torch, lambda: plan.freq_adjoint(p, q, f0, df, out=z), reps)
+    plan.close()
+    terms = prob.pairs * q
+    return {"workload": "256x256 at 0.1 mm, 256-sensor ring R=20 mm, 256 frequencies "
+                        "78 kHz..20 MHz",
+            "terms_per_application": terms,
+            "forward_ms": t_f * 1e3, "adjoint_ms": t_a * 1e3,
+            "forward_terms_per_s": terms / t_f, "adjoint_terms_per_s": terms / t_a,
+            "forward_frac_fp32": terms * 10 / t_f / 1e12 / peak_tflops,
+            "adjoint_frac_fp32": terms * 10 / t_a / 1e12 / peak_tflops,
+            "timing": f"median of {reps}, CUDA events"}
+
+
 def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
     """3D workload: 128^3 voxels at 0.2 mm, 32x32 planar array (0.8 mm pitch,
     5 mm from the volume), 1024 samples; A and A^T rates, a 30-iteration CGLS
@@ -568,6 +598,7 @@ def run_gpu(args):
         extra["volume3d"] = bench_volume(torch, tuner, peak)
         hbm = json.load(open(pk)).get("hbm_gbs", 6800.0) if os.path.exists(pk) else 6800.0
         extra["dense_paper_size"] = bench_dense(torch, hbm)
+        extra["frequency_domain"] = bench_freq(torch, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

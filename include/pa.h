@@ -216,8 +216,8 @@ pa_status pa_dense_matvec(pa_plan *plan, int dtype, const void *m_dev, int trans
  * p_dev [S][n_freq][2], x_dev [N], fully overwritten.  Arithmetic is FP32 with
  * the phase split into an FP64 per-(tile, sensor) part and an FP32 per-pixel
  * difference, which bounds the phase error by about 2 pi f_max |pixel - tile
- * centre| / c * 2^-24.  1 <= n_freq <= 65536 (the adjoint stages n_freq complex
- * values in shared memory: at most 25600); f0, df >= 0.  The first call, or a
+ * centre| / c * 2^-24.  1 <= n_freq <= 20480 (both stage n_freq complex values
+ * per sensor in shared memory); f0, df >= 0.  The first call, or a
  * call needing more workspace than earlier ones, allocates the plan's
  * workspace: make it outside stream capture. */
 pa_status pa_freq_forward(pa_plan *plan, int n_freq, double f0, double df, const float *x_dev,

@@ -40,7 +40,7 @@ struct FreqParams {
   int S, Q, dim;
   int nx, ny, nz, ntx, nty, ntz;
   double dx, dy, dz, ox, oy, oz;
-  double c, f0, df, amp;
+  double c, inv_c, f0, df, amp;
   const float* x;         // forward: [N]
   float2* part;           // forward: [S][ntiles][Q]
   const float2* p;        // adjoint: [S][Q]
@@ -142,9 +142,10 @@ __global__ void __launch_bounds__(kFreqThreads) k_freq_adjoint(const FreqParams 
     double ex, ey, ez, dref;
     tile_ref<DIM>(P, t, s, ex, ey, ez, dref);
     __syncthreads();  // the previous sensor's B is consumed
+    const double a = dref * P.inv_c;  // cycles per Hz at the tile centre
     for (int n = threadIdx.x; n < P.Q; n += kFreqThreads) {
       const double fn = P.f0 + n * P.df;
-      double cyc = fn * dref / P.c;
+      double cyc = fn * a;
       cyc -= floor(cyc);
       const float2 R = expm2pi((float)cyc);         // exp(-i k_n d_ref)
       const float2 pv = P.p[(int64_t)s * P.Q + n];
@@ -199,6 +200,8 @@ __global__ void __launch_bounds__(kFreqThreads) k_freq_adjoint_sum(const FreqPar
 template <int DIM>
 __global__ void __launch_bounds__(kFreqThreads) k_freq_forward(const FreqParams P) {
   __shared__ float2 sacc[kFreqBlock][kFreqThreads + 1];
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* sR = reinterpret_cast<float2*>(smem);  // [Q]: exp(-i k_n d_ref) of the sensor
   const int tile = blockIdx.y, chunk = blockIdx.x;
   const TileGeo<DIM> t = tile_geo<DIM>(P, tile);
   const int s0 = chunk * kFreqSensors, s1 = min(P.S, s0 + kFreqSensors);
@@ -218,6 +221,16 @@ __global__ void __launch_bounds__(kFreqThreads) k_freq_forward(const FreqParams 
   for (int s = s0; s < s1; ++s) {
     double ex, ey, ez, dref;
     tile_ref<DIM>(P, t, s, ex, ey, ez, dref);
+    {  // the centre's phase for every frequency, reduced in FP64, by all threads
+      const double cph = dref * P.inv_c;
+      __syncthreads();  // the previous sensor's sR is consumed
+      for (int n = threadIdx.x; n < P.Q; n += kFreqThreads) {
+        double cyc = (P.f0 + n * P.df) * cph;
+        cyc -= floor(cyc);
+        sR[n] = expm2pi((float)cyc);
+      }
+      __syncthreads();
+    }
     const float exf = (float)ex, eyf = (float)ey, ezf = (float)ez, dreff = (float)dref;
     float a[kFreqPPT], dt[kFreqPPT];
     float2 W[kFreqPPT];
@@ -264,13 +277,8 @@ __global__ void __launch_bounds__(kFreqThreads) k_freq_forward(const FreqParams 
         v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
       }
       const int n = n0 + j;
-      if (part == 0 && n < P.Q) {
-        const double fn = P.f0 + n * P.df;
-        double cyc = fn * dref / P.c;
-        cyc -= floor(cyc);
-        const float2 R = expm2pi((float)cyc);
-        P.part[((int64_t)s * (P.ntx * P.nty * P.ntz) + tile) * P.Q + n] = cmul(R, v);
-      }
+      if (part == 0 && n < P.Q)
+        P.part[((int64_t)s * (P.ntx * P.nty * P.ntz) + tile) * P.Q + n] = cmul(sR[n], v);
       __syncthreads();  // sacc is reused by the next block
     }
   }
@@ -309,6 +317,7 @@ FreqParams freq_params(const pa_plan* p, int Q, double f0, double df) {
   f.oy = p->grid.origin[1];
   f.oz = p->grid.origin[2];
   f.c = p->c;
+  f.inv_c = 1.0 / p->c;
   f.f0 = f0;
   f.df = df;
   f.amp = p->amp;
@@ -342,8 +351,8 @@ pa_status check_freq(const pa_plan* p, int Q, double f0, double df, const void* 
     set_error("%s: NULL argument", who);
     return PA_ERR_INVALID_ARG;
   }
-  if (Q < 1 || Q > 65536 || !std::isfinite(f0) || !std::isfinite(df) || f0 < 0.0 || df < 0.0) {
-    set_error("%s: need 1 <= n_freq <= 65536 and finite f0, df >= 0", who);
+  if (Q < 1 || Q > 20480 || !std::isfinite(f0) || !std::isfinite(df) || f0 < 0.0 || df < 0.0) {
+    set_error("%s: need 1 <= n_freq <= 20480 and finite f0, df >= 0", who);
     return PA_ERR_INVALID_ARG;
   }
   return PA_OK;
@@ -367,11 +376,15 @@ pa_status pa_freq_forward(pa_plan* plan, int n_freq, double f0, double df, const
   f.part = static_cast<float2*>(plan->d_freq);
   f.out = reinterpret_cast<float2*>(p_dev);
   cudaStream_t st = (cudaStream_t)stream;
+  const size_t smem = (size_t)n_freq * sizeof(float2);
+  if (smem > 160 * 1024) {
+    set_error("pa_freq_forward: n_freq %d needs more shared memory than a CTA has", n_freq);
+    return PA_ERR_UNSUPPORTED;
+  }
+  auto kernel = plan->dim == 2 ? k_freq_forward<2> : k_freq_forward<3>;
+  PA_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid(f.n_chunks, plan->ntiles);
-  if (plan->dim == 2)
-    k_freq_forward<2><<<grid, kFreqThreads, 0, st>>>(f);
-  else
-    k_freq_forward<3><<<grid, kFreqThreads, 0, st>>>(f);
+  kernel<<<grid, kFreqThreads, smem, st>>>(f);
   PA_CUDA(cudaGetLastError());
   const int64_t n_out = (int64_t)plan->S * n_freq;
   k_freq_combine<<<(unsigned)((n_out + kFreqThreads - 1) / kFreqThreads), kFreqThreads, 0, st>>>(
