@@ -661,16 +661,44 @@ def run_gpu(args):
 
 
 def run_profile_case(kind: str) -> int:
-    """Small fixed workload for ncu captures of the gather kernels: one plan (the
+    """Small fixed workloads for ncu captures.  "2d" / "3d": one plan (the
     256x256 ring with 8 CTAs per adjoint cluster and 16 sensors per forward CTA,
     or a 64^3 planar array with 2 and 64), then A on a dense random image and
-    A^T on random traces, three times each.  Prints nothing."""
+    A^T on random traces, three times each.  "dense": the 6144 x 16384 matrix
+    (FP64 and FP32), M x and M^T r twice each.  "freq": the frequency-domain
+    model on the 256x256 ring at 256 frequencies, forward and adjoint twice
+    each.  Prints nothing."""
     import torch
 
     from paper_2404_10928_gb300 import phantoms as ph
     from paper_2404_10928_gb300.api import Plan
 
     torch.cuda.set_device(0)
+    if kind == "dense":
+        prob = ph.dense_paper_size()
+        with Plan.from_problem(prob) as plan:
+            rows, cols = prob.n_sensors * prob.n_samples, prob.n_pixels
+            for dt in (torch.float64, torch.float32):
+                m = plan.dense_assemble(dt)
+                v = torch.rand(cols, dtype=dt, device="cuda")
+                w = torch.rand(rows, dtype=dt, device="cuda")
+                for _ in range(2):
+                    plan.dense_matvec(m, v)
+                    plan.dense_matvec(m, w, transpose=True)
+                torch.cuda.synchronize()
+                del m
+            plan.sync_status()
+        return 0
+    if kind == "freq":
+        prob = ph.ring_vessels()
+        with Plan.from_problem(prob) as plan:
+            x = torch.rand(prob.n_pixels, device="cuda")
+            for _ in range(2):
+                p = plan.freq_forward(x, 256, 78125.0, 78125.0)
+                plan.freq_adjoint(p, 256, 78125.0, 78125.0)
+            torch.cuda.synchronize()
+            plan.sync_status()
+        return 0
     if kind == "2d":
         prob = ph.ring_vessels()
         plan = Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=16)
@@ -700,7 +728,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
-    ap.add_argument("--profile-case", choices=["2d", "3d"],
+    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq"],
                     help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
