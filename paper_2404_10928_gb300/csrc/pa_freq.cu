@@ -261,13 +261,15 @@ __global__ void __launch_bounds__(kFreqThreads) k_freq_forward(const FreqParams 
 #pragma unroll
       for (int j = 0; j < kFreqBlock; ++j) sacc[j][threadIdx.x] = sum[j];
       __syncthreads();
-      // frequency j = thread / 16 summed by 16 threads (16 values each), then
+      // frequency j = thread / 16 summed by 16 threads (16 values each, lane
+      // `part` taking the threads part, part + 16, ...: consecutive lanes read
+      // consecutive entries, so a half-warp's loads fill distinct banks), then
       // a fixed xor tree over those 16 lanes
       const int j = threadIdx.x >> 4, part = threadIdx.x & 15;
       float2 v = make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int q = 0; q < kFreqThreads / 16; ++q) {
-        const float2 w = sacc[j][part * (kFreqThreads / 16) + q];
+        const float2 w = sacc[j][q * 16 + part];
         v.x += w.x;
         v.y += w.y;
       }
