@@ -93,7 +93,9 @@ struct __align__(16) TileRef2 {
   float2 ex2k, ey2k, ez2k, dref2, dref, fref;
   int klo;
   float dlo;
-  int pad0, pad1;
+  // forward only: window copy of each lane (2 bits per lane; lanes 0-15 in
+  // copy_lo, 16-31 in copy_hi); zero where unused
+  unsigned copy_lo, copy_hi;
 };
 static_assert(sizeof(TileRef2) == 64, "TileRef2 must be 64 bytes");
 static_assert(sizeof(TileRef) == 32, "TileRef must be 32 bytes");
@@ -150,6 +152,7 @@ struct AdjParams {
 
 struct FwdParams {
   const TileRef* table;   // [ntiles][S]
+  const unsigned long long* copies;  // [ntiles][S]: window copy of each lane, 2 bits per lane
   const float* x;         // [N]
   float* part;            // [S][ntiles][L] window of each (tile, sensor) pair
   const int2* sorted;     // [S][ntiles]: (tile, klo) of the pairs that are not skipped, by klo
@@ -233,6 +236,8 @@ constexpr int kCombThreads = 256;            // samples per combine CTA
 cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const double* sensors_dev,
                                int S, const pa_grid& grid, const GridF& g, double kappa,
                                double t0fs, int K, int L, double hmin, int* err, cudaStream_t st);
+cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, const double* sensors_dev, int S,
+                              const pa_grid& grid, const GridF& g, double kappa, cudaStream_t st);
 cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
                         cudaStream_t st);
 cudaError_t launch_bp_filter(const float* p, float2* packed, int S, int K, int Kp, int pad,
@@ -302,6 +307,7 @@ struct pa_plan {
   // device memory owned by the plan
   double* d_sensors = nullptr;
   pa::TileRef* d_table = nullptr;
+  unsigned long long* d_fwd_copies = nullptr;  // [ntiles][S] forward window copy per lane
   int2* d_krange = nullptr;
   float* d_part = nullptr;    // forward window partials [S][ntiles][L]
   int2* d_sorted = nullptr;   // [S][ntiles]

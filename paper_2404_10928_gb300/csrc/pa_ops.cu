@@ -391,7 +391,7 @@ __device__ __forceinline__ TileRef2 expand_ref(const TileRef& r) {
   e.fref = f2(r.fref);
   e.klo = r.klo;
   e.dlo = r.dlo;
-  e.pad0 = e.pad1 = 0;
+  e.copy_lo = e.copy_hi = 0;
   return e;
 }
 
@@ -864,27 +864,100 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
 // k, in a fixed order (by window start), plus the residual / norm epilogue.
 // ---------------------------------------------------------------------------
-// Each (tile, sensor) window is kept as kFwdCopies copies, kFwdCopyPad words
-// apart in bank alignment (copy c starts c (L + kFwdCopyPad) words after copy
-// 0, i.e. 8 banks further): a thread deposits into the copy chosen by its place
-// in its half-warp's 4x4 pixel block (fwd_copy), so pixels on a common row,
-// column or diagonal of the block -- the likeliest to share a sample bin --
-// update different banks instead of replaying one atomic.  The flush adds the
-// copies (exact integer sums), so results do not depend on the split.
+// Each (tile, sensor) window is kept as kFwdCopies copies, copy c starting
+// c * CS words in, with CS = 12 (mod 32): the copies of one bin lie 12 banks
+// apart.  A warp's shared-memory atomic takes as many passes as the largest
+// number of its lanes that fall into one bank, whether or not their addresses
+// agree, and the 32 pixels of a warp fall into ~25 sample bins.  Each lane
+// therefore deposits into the copy the per-(tile, sensor) table `copies`
+// assigns to it (k_fwd_copies), chosen so that the lanes' bins spread across
+// the banks.  The flush adds the copies (exact integer sums), so results do
+// not depend on the assignment.
 constexpr int kFwdCopies = 4;
-constexpr int kFwdCopyPad = 8;
-__host__ __device__ inline int fwd_copy_stride(int L) { return L + kFwdCopyPad; }
+constexpr int kFwdCopyRes = 12;  // copy stride mod 32 (a multiple of 4: 16-byte aligned copies)
+__host__ __device__ inline int fwd_copy_stride(int L) { return L + ((kFwdCopyRes - L) & 31); }
 
 int forward_smem_bytes(int L, int spc) {
   return spc * (int)sizeof(TileRef2) +
          2 * kFwdSB * kFwdCopies * fwd_copy_stride(L) * (int)sizeof(int);
 }
 
-// Copy index of compute-order pixel p: a 4x4 Latin square over the half-warp
-// block position j = p & 15 (x = j & 3, y = j >> 2) whose rows, columns and
-// both diagonals hold all four copies:
-//   0 1 2 3 / 2 3 0 1 / 3 2 1 0 / 1 0 3 2
-__device__ __forceinline__ int fwd_copy(int p) { return (0xB11B4EE4u >> (2 * (p & 15))) & 3; }
+// Copy assignment of the forward windows.  One warp per (tile, sensor) pair;
+// lane r holds the sample bins of pixel row r (compute-order pixels 32 r ..
+// 32 r + 31: thread lane l of warp r % 8 deposits pixel 32 r + l), so every
+// warp atomic of the gather is one row.  Lanes l = 0..31 in turn take the copy
+// c whose bank (bin + c kFwdCopyRes) mod 32 minimises, summed over the 32
+// rows, the squared number of lanes already assigned to that bank (ties to
+// the lower copy).  Bins come from FP32 distances: an occasional bin off by
+// one costs at most a bank conflict.  Output: copies[tile * S + s], 2 bits per
+// lane.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies,
+                                                    const double* sensors, int S, int nx, int ny,
+                                                    int nz, double dx, double dy, double dz,
+                                                    double ox, double oy, double oz, int ntx,
+                                                    int nty, int ntz, float kappa) {
+  __shared__ unsigned char s_load[8][32][33];  // per warp and row: lanes per bank
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t total = (int64_t)ntx * nty * ntz * S;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned char* ld = s_load[wib][lane];
+  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < total;
+       idx += wstride) {
+    const int t = (int)(idx / S), s = (int)(idx % S);
+    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
+    const int nvx = min(TX, nx - tx * TX), nvy = min(TY, ny - ty * TY), nvz = min(TZ, nz - tz * TZ);
+    // tile corner relative to the sensor
+    const float cx = (float)(ox + tx * TX * dx - sensors[(int64_t)s * DIM]);
+    const float cy = (float)(oy + ty * TY * dy - sensors[(int64_t)s * DIM + 1]);
+    const float cz = DIM == 3 ? (float)(oz + tz * TZ * dz - sensors[(int64_t)s * DIM + 2]) : 0.0f;
+    int bins[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      int lx, ly, lz;
+      pixel_local<DIM>(32 * lane + l, lx, ly, lz);
+      const float ex = cx + (float)min(lx, nvx - 1) * (float)dx;
+      const float ey = cy + (float)min(ly, nvy - 1) * (float)dy;
+      const float ez = cz + (float)min(lz, nvz - 1) * (float)dz;
+      bins[l] = (int)floorf(kappa * sqrtf(ex * ex + ey * ey + ez * ez));
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b) ld[b] = 0;
+    unsigned lo = 0, hi = 0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      int best = 0;
+      unsigned best_sc = 0xffffffffu;
+#pragma unroll
+      for (int c = 0; c < kFwdCopies; ++c) {
+        const unsigned v = ld[(bins[l] + c * kFwdCopyRes) & 31];
+        const unsigned sc = __reduce_add_sync(0xffffffffu, v * v);
+        if (sc < best_sc) {
+          best_sc = sc;
+          best = c;
+        }
+      }
+      ++ld[(bins[l] + best * kFwdCopyRes) & 31];
+      if (l < 16)
+        lo |= (unsigned)best << (2 * l);
+      else
+        hi |= (unsigned)best << (2 * (l - 16));
+    }
+    if (lane == 0) copies[idx] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, const double* sensors_dev, int S,
+                              const pa_grid& grid, const GridF& g, double kappa, cudaStream_t st) {
+  const int64_t warps = (int64_t)g.ntx * g.nty * g.ntz * S;
+  const int blocks = (int)std::min<int64_t>((warps + 7) / 8, 65535);
+  auto kernel = dim == 2 ? k_fwd_copies<2> : k_fwd_copies<3>;
+  return launch_k(kernel, dim3(blocks), dim3(256), 0, st, 0, copies, sensors_dev, S, grid.nx,
+                  grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.origin[0], grid.origin[1],
+                  grid.origin[2], g.ntx, g.nty, g.ntz, (float)kappa);
+}
 
 constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
 
@@ -1003,10 +1076,17 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   }
   for (int i = tid; i < ns; i += nt) {
     const TileRef r = P.table[(int64_t)tile * P.S + s0 + i];
-    if (r.klo != kSkip)
-      refs[i] = expand_ref(r);
-    else
+    if (r.klo != kSkip) {
+      TileRef2 e = expand_ref(r);
+      if (P.copies) {
+        const unsigned long long c = P.copies[(int64_t)tile * P.S + s0 + i];
+        e.copy_lo = (unsigned)c;
+        e.copy_hi = (unsigned)(c >> 32);
+      }
+      refs[i] = e;
+    } else {
       refs[i].klo = kSkip;
+    }
   }
   const int CS = fwd_copy_stride(L);           // words per window copy
   const int WS = kFwdCopies * CS;              // words per (tile, sensor) window
@@ -1022,8 +1102,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   for (int h = 0; h < 2; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
   const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
 
-  // this thread's copy of every window (all four of its pixels share it)
-  const uint32_t win_u32 = smem_u32(win) + 4u * (uint32_t)(fwd_copy(tid) * CS);
+  // copy 0 of the windows; lane l deposits into copy c(l) of each sensor's
+  // table entry, c(l) * CS words further
+  const uint32_t win_u32 = smem_u32(win);
+  const bool copy_hi = lane >= 16;
+  const int copy_sh = 2 * (lane & 15);
+  const uint32_t copy_bytes = 4u * (uint32_t)CS;
   for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
     int* wb = win + buf * kFwdSB * WS;
     const int nsb = min(kFwdSB, ns - g0);
@@ -1034,15 +1118,17 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
         const TileRef2 r = refs[g0 + sb];
         if (r.klo == kSkip) continue;
         const float2 dlo = f2(r.dlo);
+        const uint32_t cbase =
+            base + (((copy_hi ? r.copy_hi : r.copy_lo) >> copy_sh) & 3u) * copy_bytes;
         if (r.klo & kNear) {
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            fwd_pair2<DIM, true>(r, base, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
+            fwd_pair2<DIM, true>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
                                  inv_kappa, hik);
         } else {
 #pragma unroll
           for (int h = 0; h < 2; ++h)
-            fwd_pair2<DIM, false>(r, base, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
+            fwd_pair2<DIM, false>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
                                   inv_kappa, hik);
         }
       }

@@ -54,6 +54,8 @@ static pa_status build_table(pa_plan* p) {
   PA_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->cap_stream));
   PA_CUDA(launch_build_table(p->dim, p->d_table, p->d_krange, p->d_sensors, p->S, p->grid, p->g,
                              kappa, p->t0 * p->fs, p->K, p->L, hmin, p->d_err, p->cap_stream));
+  PA_CUDA(launch_fwd_copies(p->dim, p->d_fwd_copies, p->d_sensors, p->S, p->grid, p->g, kappa,
+                            p->cap_stream));
   int err = 0;
   PA_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->cap_stream));
   PA_CUDA(cudaStreamSynchronize(p->cap_stream));
@@ -122,7 +124,7 @@ static void free_plan(pa_plan* p) {
     for (auto ev : kv.second.adj_ev) cudaEventDestroy(ev);
   }
   p->graphs.clear();
-  void* ptrs[] = {p->d_sensors, p->d_table, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
+  void* ptrs[] = {p->d_sensors, p->d_table, p->d_fwd_copies, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
                   p->d_packed, p->d_err, p->d_partials, p->d_parts_q, p->d_parts_s, p->d_parts_h,
                   p->d_dense_part, p->d_freq,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
@@ -360,6 +362,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   }
   if ((st = dev_alloc(p, &p->d_sensors, p->sensors.size())) != PA_OK ||
       (st = dev_alloc(p, &p->d_table, n_tab)) != PA_OK ||
+      (st = dev_alloc(p, &p->d_fwd_copies, n_tab)) != PA_OK ||
       (st = dev_alloc(p, &p->d_krange, n_tab)) != PA_OK ||
       (st = dev_alloc(p, &p->d_part, n_tab * p->L)) != PA_OK ||
       (st = dev_alloc(p, &p->d_sorted, n_tab)) != PA_OK ||
@@ -476,6 +479,7 @@ namespace pa {
 FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode, const void* y) {
   FwdParams f{};
   f.table = p->d_table;
+  f.copies = p->d_fwd_copies;
   f.x = x;
   f.part = p->d_part;
   f.sorted = p->d_sorted;
