@@ -201,7 +201,9 @@ pa_status pa_backproject(pa_plan *plan, const float *p_dev, int filter, float *x
  * out = M^T v (transpose = 1; v [S*K], out [N]) in dtype arithmetic for such a
  * matrix (vectors of the same dtype, device memory).  Sums run in a fixed
  * order.  The first transposed call allocates the plan's partial buffer
- * (ceil(S*K/128) * N * 8 bytes): make it outside stream capture. */
+ * (ceil(S*K/128) * N * 8 bytes, plus ceil(N/256) counters): make it outside
+ * stream capture.  Transposed products on one plan must not overlap in time
+ * (they share that buffer). */
 pa_status pa_dense_assemble(pa_plan *plan, int dtype, void *m_dev, pa_stream stream);
 pa_status pa_dense_matvec(pa_plan *plan, int dtype, const void *m_dev, int transpose,
                           const void *v_dev, void *out_dev, pa_stream stream);

@@ -65,33 +65,43 @@ __device__ __forceinline__ T block_sum_t(T v, T* s_red) {
 }
 
 // out[r] = sum_j m[r][j] v[j]: one CTA per row, each thread a strided share
-// (one 16-byte load per step where the row is 16-byte aligned), then a fixed
-// tree.
+// (16-byte loads, four in flight, where the row is 16-byte aligned; summed in
+// the order of the plain strided loop), then a fixed tree.
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads) k_dense_mv(const T* m, const T* v, T* out,
-                                                            int64_t cols) {
+                                                            int64_t cols, int vec) {
   __shared__ T s_red[kDenseThreads / 32];
   constexpr int VW = 16 / sizeof(T);
+  using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
   const T* row = m + blockIdx.x * cols;
   T acc = 0;
-  const bool vec = (cols % VW) == 0;
+  auto dot = [&](const V& a, const V& b) {
+    if constexpr (sizeof(T) == 8) {
+      acc = fma(a.x, b.x, acc);
+      acc = fma(a.y, b.y, acc);
+    } else {
+      acc = fmaf(a.x, b.x, acc);
+      acc = fmaf(a.y, b.y, acc);
+      acc = fmaf(a.z, b.z, acc);
+      acc = fmaf(a.w, b.w, acc);
+    }
+  };
   if (vec) {
-    using V = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
     const V* rv = reinterpret_cast<const V*>(row);
     const V* vv = reinterpret_cast<const V*>(v);
-    for (int64_t j = threadIdx.x; j < cols / VW; j += kDenseThreads) {
-      const V a = __ldcs(rv + j);
-      const V b = __ldg(vv + j);
-      if constexpr (sizeof(T) == 8) {
-        acc = fma(a.x, b.x, acc);
-        acc = fma(a.y, b.y, acc);
-      } else {
-        acc = fmaf(a.x, b.x, acc);
-        acc = fmaf(a.y, b.y, acc);
-        acc = fmaf(a.z, b.z, acc);
-        acc = fmaf(a.w, b.w, acc);
+    const int64_t n = cols / VW;
+    int64_t j = threadIdx.x;
+    for (; j + 3 * kDenseThreads < n; j += 4 * kDenseThreads) {
+      V a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = __ldcs(rv + j + u * kDenseThreads);
+        b[u] = __ldg(vv + j + u * kDenseThreads);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dot(a[u], b[u]);
     }
+    for (; j < n; j += kDenseThreads) dot(__ldcs(rv + j), __ldg(vv + j));
   } else {
     for (int64_t j = threadIdx.x; j < cols; j += kDenseThreads) acc += row[j] * v[j];
   }
@@ -99,29 +109,48 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_mv(const T* m, const T*
   if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
-// part[chunk][c] = sum over the chunk's rows r (in order) of m[r][c] v[r]: a
-// thread per column (consecutive threads, consecutive columns: coalesced rows)
+// M^T r.  CTA (x, y) takes columns [256 x, 256 x + 256), one per thread
+// (consecutive threads, consecutive columns: every row segment a CTA reads is
+// contiguous), and rows [128 y, 128 y + 128): part[y][c] = sum over those rows
+// r, in order, of m[r][c] v[r].  The last CTA of each column block to finish
+// (a counter per block, reset by that CTA) then forms out[c] = sum over chunks
+// y, in order, of part[y][c] (eight chunk partials in flight): the same sums
+// in the same order, whichever CTA is last.
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads) k_dense_mtv(const T* m, const T* v, T* part,
-                                                             int64_t rows, int64_t cols) {
+                                                             T* out, unsigned* counters,
+                                                             int64_t rows, int64_t cols,
+                                                             int nchunks) {
+  __shared__ bool s_last;
   const int64_t c = blockIdx.x * (int64_t)kDenseThreads + threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.y * kRowsPerChunk;
   const int64_t r1 = min(rows, r0 + kRowsPerChunk);
-  if (c >= cols) return;
-  T acc = 0;
-  for (int64_t r = r0; r < r1; ++r) acc += __ldcs(m + r * cols + c) * __ldg(v + r);
-  part[(int64_t)blockIdx.y * cols + c] = acc;
-}
-
-// out[c] = sum over chunks, in chunk order
-template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) k_dense_mtv_sum(const T* part, T* out,
-                                                                 int nchunks, int64_t cols) {
-  const int64_t c = blockIdx.x * (int64_t)kDenseThreads + threadIdx.x;
-  if (c >= cols) return;
-  T acc = 0;
-  for (int q = 0; q < nchunks; ++q) acc += part[(int64_t)q * cols + c];
-  out[c] = acc;
+  if (c < cols) {
+    T acc = 0;
+    for (int64_t r = r0; r < r1; ++r) acc += __ldcs(m + r * cols + c) * __ldg(v + r);
+    part[(int64_t)blockIdx.y * cols + c] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    s_last = atomicAdd(&counters[blockIdx.x], 1u) == (unsigned)(nchunks - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (c < cols) {
+    T acc = 0;
+    int q = 0;
+    for (; q + 8 <= nchunks; q += 8) {
+      T w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) w[u] = __ldcg(part + (int64_t)(q + u) * cols + c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += w[u];
+    }
+    for (; q < nchunks; ++q) acc += __ldcg(part + (int64_t)q * cols + c);
+    out[c] = acc;
+  }
+  if (threadIdx.x == 0) counters[blockIdx.x] = 0;  // ready for the next product
 }
 
 template <typename T>
@@ -140,20 +169,21 @@ cudaError_t assemble(const pa_plan* p, T* m, cudaStream_t st) {
 
 template <typename T>
 cudaError_t matvec(pa_plan* p, const T* m, int transpose, const T* v, T* out, cudaStream_t st) {
+  constexpr int VW = 16 / sizeof(T);
   const int64_t rows = (int64_t)p->S * p->K;
   const int64_t cols = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
   if (!transpose) {
-    k_dense_mv<T><<<(unsigned)rows, kDenseThreads, 0, st>>>(m, v, out, cols);
+    // 16-byte vectors need 16-byte aligned rows and v
+    const int vec = (reinterpret_cast<uintptr_t>(m) & 15) == 0 && cols % VW == 0 &&
+                    (reinterpret_cast<uintptr_t>(v) & 15) == 0;
+    k_dense_mv<T><<<(unsigned)rows, kDenseThreads, 0, st>>>(m, v, out, cols, vec);
     return cudaGetLastError();
   }
   const int nchunks = (int)((rows + kRowsPerChunk - 1) / kRowsPerChunk);
-  T* part = reinterpret_cast<T*>(p->d_dense_part);
   const dim3 grid((unsigned)((cols + kDenseThreads - 1) / kDenseThreads), (unsigned)nchunks);
-  k_dense_mtv<T><<<grid, kDenseThreads, 0, st>>>(m, v, part, rows, cols);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_dense_mtv_sum<T><<<(unsigned)((cols + kDenseThreads - 1) / kDenseThreads), kDenseThreads, 0,
-                       st>>>(part, out, nchunks, cols);
+  T* part = reinterpret_cast<T*>(p->d_dense_part);
+  k_dense_mtv<T><<<grid, kDenseThreads, 0, st>>>(m, v, part, out, p->d_dense_cnt, rows, cols,
+                                                 nchunks);
   return cudaGetLastError();
 }
 
@@ -169,7 +199,8 @@ pa_status check_dense_args(const pa_plan* p, int dtype, const void* a, const voi
   }
   const int64_t rows = (int64_t)p->S * p->K;
   const int64_t cols = (int64_t)p->grid.nx * p->grid.ny * p->grid.nz;
-  if (rows > INT_MAX || rows * cols > (int64_t)1 << 40) {
+  if (rows > INT_MAX || rows * cols > (int64_t)1 << 40 ||
+      (rows + kRowsPerChunk - 1) / kRowsPerChunk > 65535) {
     set_error("%s: matrix too large (%lld x %lld)", who, (long long)rows, (long long)cols);
     return PA_ERR_UNSUPPORTED;
   }
@@ -206,14 +237,20 @@ pa_status pa_dense_matvec(pa_plan* plan, int dtype, const void* m_dev, int trans
     const int64_t rows = (int64_t)plan->S * plan->K;
     const int64_t cols = (int64_t)plan->grid.nx * plan->grid.ny * plan->grid.nz;
     const size_t bytes = (size_t)((rows + kRowsPerChunk - 1) / kRowsPerChunk) * cols * 8;
+    const size_t cnt_bytes = (size_t)((cols + kDenseThreads - 1) / kDenseThreads) * sizeof(unsigned);
     cudaError_t e = cudaMalloc(&plan->d_dense_part, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&plan->d_dense_cnt, cnt_bytes);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_dense_cnt, 0, cnt_bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
+      cudaFree(plan->d_dense_part);
+      cudaFree(plan->d_dense_cnt);
       plan->d_dense_part = nullptr;
-      set_error("pa_dense_matvec: cudaMalloc of %zu bytes failed", bytes);
+      plan->d_dense_cnt = nullptr;
+      set_error("pa_dense_matvec: cudaMalloc of %zu bytes failed", bytes + cnt_bytes);
       return PA_ERR_OOM;
     }
-    plan->bytes += (int64_t)bytes;
+    plan->bytes += (int64_t)(bytes + cnt_bytes);
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == PA_F64)

@@ -321,6 +321,7 @@ struct pa_plan {
   float2* d_parts_h = nullptr;   // [rows][n_partials] partials of the residual history
   int parts_h_rows = 0;
   void* d_dense_part = nullptr;  // dense-matrix mode: per-row-chunk partials of M^T v
+  unsigned* d_dense_cnt = nullptr;  // dense-matrix mode: finished chunks per column block
   void* d_freq = nullptr;        // frequency-domain model: per-tile spectra / partial images
   size_t freq_bytes = 0;
   unsigned* d_counter = nullptr;  // last-CTA counter of the fused reductions

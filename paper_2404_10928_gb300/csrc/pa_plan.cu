@@ -126,7 +126,7 @@ static void free_plan(pa_plan* p) {
   p->graphs.clear();
   void* ptrs[] = {p->d_sensors, p->d_table, p->d_fwd_copies, p->d_krange, p->d_part, p->d_sorted, p->d_upper,
                   p->d_packed, p->d_err, p->d_partials, p->d_parts_q, p->d_parts_s, p->d_parts_h,
-                  p->d_dense_part, p->d_freq,
+                  p->d_dense_part, p->d_dense_cnt, p->d_freq,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
                   p->d_scal,    p->d_counter,
                   p->d_yhost,   p->d_xhost};
