@@ -105,6 +105,18 @@ def test_argument_validation_without_gpu(lib):
     assert b"half the pixel" in lib.pa_last_error()
     bad_opts = _lib.pa_plan_opts(0.0, 1.0, 7, 0, 0)
     assert _create(lib, far, _grid(), opts=bad_opts)[0] == _lib.PA_ERR_INVALID_ARG
+    # adjoint clusters of 1, 2, 4 or 8 CTAs only; 1..256 sensors per forward work item
+    for cluster, spc in ((3, 0), (9, 0), (-1, 0), (0, 257), (0, -2)):
+        opts = _lib.pa_plan_opts(0.0, 1.0, _lib.PA_F32, cluster, spc)
+        assert _create(lib, far, _grid(), opts=opts)[0] == _lib.PA_ERR_INVALID_ARG
+        assert b"adj_cluster" in lib.pa_last_error()
+    # the dense, frequency-domain and back-projection entry points reject NULL plans
+    assert lib.pa_dense_assemble(None, _lib.PA_F64, None, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_dense_matvec(None, _lib.PA_F32, None, 0, None, None, None) == \
+        _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_freq_forward(None, 16, 1e5, 1e5, None, None, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_freq_adjoint(None, 16, 1e5, 1e5, None, None, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_backproject(None, None, _lib.PA_BP_UBP, None, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_plan_destroy(None) == _lib.PA_OK
     assert lib.pa_forward(None, None, None, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_adjoint(None, None, None, None) == _lib.PA_ERR_INVALID_ARG
