@@ -1010,6 +1010,30 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
 
+  // the sensors' table entries are staged and the windows cleared first, so
+  // that their latency overlaps the loads (and, for a CGLS direction, the
+  // reduction) below
+  for (int i = tid; i < ns; i += nt) {
+    const TileRef r = P.table[(int64_t)tile * P.S + s0 + i];
+    if (r.klo != kSkip) {
+      TileRef2 e = expand_ref(r);
+      if (P.copies) {
+        const unsigned long long c = P.copies[(int64_t)tile * P.S + s0 + i];
+        e.copy_lo = (unsigned)c;
+        e.copy_hi = (unsigned)(c >> 32);
+      }
+      refs[i] = e;
+    } else {
+      refs[i].klo = kSkip;
+    }
+  }
+  const int CS = fwd_copy_stride(L);           // words per window copy (a multiple of 4)
+  const int WS = kFwdCopies * CS;              // words per (tile, sensor) window
+  {
+    int4* w4 = reinterpret_cast<int4*>(win);  // 16-byte aligned: refs are 64-byte entries
+    for (int i = tid; i < (2 * kFwdSB * WS) / 4; i += nt) w4[i] = make_int4(0, 0, 0, 0);
+  }
+
   float2 ddx[2], ddy[2], ddz[2], cm[2], xs[2];
   float amax = 0.0f;
   int nonfinite = 0;
@@ -1074,23 +1098,6 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     set_lane(ddz[m >> 1], m & 1, oz);
     set_lane(cm[m >> 1], m & 1, oc);
   }
-  for (int i = tid; i < ns; i += nt) {
-    const TileRef r = P.table[(int64_t)tile * P.S + s0 + i];
-    if (r.klo != kSkip) {
-      TileRef2 e = expand_ref(r);
-      if (P.copies) {
-        const unsigned long long c = P.copies[(int64_t)tile * P.S + s0 + i];
-        e.copy_lo = (unsigned)c;
-        e.copy_hi = (unsigned)(c >> 32);
-      }
-      refs[i] = e;
-    } else {
-      refs[i].klo = kSkip;
-    }
-  }
-  const int CS = fwd_copy_stride(L);           // words per window copy
-  const int WS = kFwdCopies * CS;              // words per (tile, sensor) window
-  for (int i = tid; i < 2 * kFwdSB * WS; i += nt) win[i] = 0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if (lane == 0) s_max[warp] = amax;
