@@ -667,13 +667,33 @@ def run_profile_case(kind: str) -> int:
     A^T on random traces, three times each.  "dense": the 6144 x 16384 matrix
     (FP64 and FP32), M x and M^T r twice each.  "freq": the frequency-domain
     model on the 256x256 ring at 256 frequencies, forward and adjoint twice
-    each.  Prints nothing."""
+    each.  "batch": the first 16 frames of the ragged time series (FP16 y) as
+    one persistent batched launch of 4 projected Landweber iterations, twice.
+    Prints nothing."""
     import torch
 
     from paper_2404_10928_gb300 import phantoms as ph
-    from paper_2404_10928_gb300.api import Plan
+    from paper_2404_10928_gb300.api import Batch, Plan
 
     torch.cuda.set_device(0)
+    if kind == "batch":
+        plans, ys, xs, omegas = [], [], [], []
+        for prob in ph.ragged_time_series()[:16]:
+            plan = Plan.from_problem(prob, adj_cluster=1)
+            x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
+            ys.append(plan.forward(x_true).to(torch.float16))
+            omegas.append(1.0 / plan.power_iteration(20))
+            xs.append(torch.zeros(prob.n_pixels, dtype=torch.float32, device="cuda"))
+            plans.append(plan)
+        batch = Batch(plans)
+        for _ in range(2):
+            batch.landweber(ys, xs, omegas, 4)
+        torch.cuda.synchronize()
+        batch.close()
+        for plan in plans:
+            plan.sync_status()
+            plan.close()
+        return 0
     if kind == "dense":
         prob = ph.dense_paper_size()
         with Plan.from_problem(prob) as plan:
@@ -728,7 +748,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
-    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq"],
+    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch"],
                     help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
