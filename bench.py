@@ -669,13 +669,26 @@ def run_profile_case(kind: str) -> int:
     model on the 256x256 ring at 256 frequencies, forward and adjoint twice
     each.  "batch": the first 16 frames of the ragged time series (FP16 y) as
     one persistent batched launch of 4 projected Landweber iterations, twice.
-    Prints nothing."""
+    "dc": on the 64^3 planar plan, the speed-of-sound derivative and the
+    smoothed TV with its gradient, three times each.  Prints nothing."""
     import torch
 
     from paper_2404_10928_gb300 import phantoms as ph
     from paper_2404_10928_gb300.api import Batch, Plan
 
     torch.cuda.set_device(0)
+    if kind == "dc":
+        prob = ph.planar_vessel_tree(n=64)
+        with Plan.from_problem(prob, adj_cluster=2) as plan:
+            g = torch.Generator(device="cuda").manual_seed(0)
+            x = torch.rand(plan.n_pixels, device="cuda", generator=g)
+            r = torch.randn(plan.n_sensors * plan.n_samples, device="cuda", generator=g)
+            for _ in range(3):
+                plan.dc(x, r)
+                plan.tv(x, 1e-2)
+            torch.cuda.synchronize()
+            plan.sync_status()
+        return 0
     if kind == "batch":
         plans, ys, xs, omegas = [], [], [], []
         for prob in ph.ragged_time_series()[:16]:
@@ -748,7 +761,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
-    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch"],
+    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch", "dc"],
                     help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
