@@ -381,3 +381,37 @@ def test_freq_adjoint_identity():
     lhs = float(np.real(np.sum(np.conj(orc.freq_forward(geo, x, q, 0.5e6, 1.7e6)) * pq)))
     rhs = float(np.dot(x, orc.freq_adjoint(geo, pq, q, 0.5e6, 1.7e6)))
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+@pytest.mark.parametrize("d", [3.0e-3, 3.0137e-3, 7.45e-3])
+def test_freq_model_is_the_spectrum_of_the_time_derivative(d):
+    # Eq. 7 against Eq. 6 for one pixel at distance d (amp = 1, x = 1, t0 = 0):
+    # Eq. 6's impulse delta(t - d/c) / d has spectrum exp(-i k d) / d, and Eq. 7
+    # is i c k = 2 pi i f times it (the spectrum of its time derivative).  The
+    # discretised trace p[k] = h(u - k) / d samples a triangle of half-width
+    # 1/fs, whose transform is (1/fs) sinc^2(f/fs), so by Poisson summation
+    #   sum_k p[k] exp(-2 pi i f k / fs)
+    #     = sum_m sinc^2(f/fs - m) exp(-2 pi i (f - m fs) d / c) / d.
+    # The m = 0 term is sinc^2(f/fs) exp(-i k d) / d; the aliases m != 0 add at
+    # most B(f) = sum_{m != 0} sinc^2(f/fs - m) / sinc^2(f/fs) relative to it
+    # (they reach it when u is an integer, where the sum is exactly 1/d).  So
+    # |P(f) - 2 pi i f DTFT(p)(f) / sinc^2(f/fs)| <= B(f) |P(f)|.
+    c, fs, K = 1500.0, 40e6, 512
+    geo = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                       np.array([[0.0, d]]), c, fs, K)
+    p = orc.forward(geo, np.ones(1))[0]
+    assert np.count_nonzero(p) in (1, 2) and abs(p.sum() - 1.0 / d) <= 1e-9 / d
+    q, f0, df = 8, 0.125e6, 0.125e6
+    P = orc.freq_forward(geo, np.ones(1), q, f0, df)[0]
+    k = np.arange(K)
+    m = np.concatenate([np.arange(-200000, 0), np.arange(1, 200001)])
+    worst_conj = 0.0
+    for n in range(q):
+        f = f0 + n * df
+        bound = np.sum(np.sinc(f / fs - m) ** 2) / np.sinc(f / fs) ** 2 * (1 + 1e-3) + 1e-12
+        expected = 2j * np.pi * f * np.sum(p * np.exp(-2j * np.pi * f * k / fs)) / np.sinc(f / fs) ** 2
+        assert abs(P[n] - expected) <= bound * abs(P[n]), (f, P[n], expected, bound)
+        # a planted mistake, the conjugate phase exp(+i k d), must fail somewhere
+        wrong = 2j * np.pi * f * np.conj(P[n] / (2j * np.pi * f))
+        worst_conj = max(worst_conj, abs(wrong - expected) / abs(P[n]))
+    assert worst_conj > 0.5
