@@ -12,6 +12,16 @@ own frame (weak scaling, no collective on the data path).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
 reference arm), on a bounded sample of the same workload per step.
+
+Besides the contract keys (``roofline`` for the dominant gather, ``cpu_baseline``,
+``e2e`` through the host-buffer entry point, ``clocks``, ``gpu_launches``), the
+line carries the other workloads, each timed with CUDA events outside the timed
+region (``--no-extras`` skips them): ``bp_vs_ir`` (back-projection against
+CGLS and FISTA), ``batched`` (64 ragged frames, persistent launch against the
+per-frame loop), ``differentiable`` (loss and gradients in x and c),
+``volume3d`` (the 128^3 planar workload), ``dense_paper_size`` (the 6144 x 16384
+matrix) and ``frequency_domain``.  ``--profile-case 2d|3d|dense|freq|batch|dc``
+runs only a small fixed workload for ncu captures.
 """
 from __future__ import annotations
 
