@@ -97,3 +97,29 @@ def test_paper_size_against_oracle_operators(torch_cuda):
             assert rel_l2(p, p_ref) <= tol, (dt, rel_l2(p, p_ref))
             assert rel_l2(g, g_ref) <= tol, (dt, rel_l2(g, g_ref))
         plan.sync_status()
+
+
+def test_matvec_unaligned_views(torch_cuda):
+    # a matrix and vector starting one element past a 16-byte boundary: M x then
+    # takes scalar loads (the 16-byte path needs aligned rows and v); both
+    # products still match the FP64 product of the same entries
+    torch = torch_cuda
+    prob = SMALL["8x8-ring4-k48-t0"]  # 64 columns: aligned rows would take 16-byte loads
+    rng = np.random.default_rng(26)
+    with _plan(prob) as plan:
+        for dt, tol in ((torch.float64, 1e-13), (torch.float32, 2e-6)):
+            m = plan.dense_assemble(dt)
+            rows, cols = m.shape
+            big = torch.empty(m.numel() + 1, dtype=dt, device="cuda")
+            big[1:] = m.reshape(-1)
+            vbig = torch.empty(cols + 1, dtype=dt, device="cuda")
+            vbig[1:] = torch.tensor(rng.standard_normal(cols), dtype=dt, device="cuda")
+            m_off, v_off = big[1:], vbig[1:]
+            assert m_off.data_ptr() % 16 != 0 and v_off.data_ptr() % 16 != 0
+            mn = m.cpu().numpy().astype(np.float64)
+            out = plan.dense_matvec(m_off, v_off).cpu().numpy()
+            assert rel_l2(out, mn @ v_off.cpu().numpy().astype(np.float64)) <= tol
+            w = torch.tensor(rng.standard_normal(rows), dtype=dt, device="cuda")
+            out_t = plan.dense_matvec(m_off, w, transpose=True).cpu().numpy()
+            assert rel_l2(out_t, mn.T @ w.cpu().numpy().astype(np.float64)) <= tol
+        plan.sync_status()
