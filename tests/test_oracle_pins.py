@@ -383,8 +383,9 @@ def test_freq_adjoint_identity():
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
 
 
-@pytest.mark.parametrize("d", [3.0e-3, 3.0137e-3, 7.45e-3])
-def test_freq_model_is_the_spectrum_of_the_time_derivative(d):
+@pytest.mark.parametrize("dim,d,t0", [(2, 3.0e-3, 0.0), (2, 3.0137e-3, 0.0), (2, 7.45e-3, 0.0),
+                                       (3, 4.2311e-3, 0.0), (2, 3.0137e-3, 3.37 / 40e6)])
+def test_freq_model_is_the_spectrum_of_the_time_derivative(dim, d, t0):
     # Eq. 7 against Eq. 6 for one pixel at distance d (amp = 1, x = 1, t0 = 0):
     # Eq. 6's impulse delta(t - d/c) / d has spectrum exp(-i k d) / d, and Eq. 7
     # is i c k = 2 pi i f times it (the spectrum of its time derivative).  The
@@ -395,10 +396,12 @@ def test_freq_model_is_the_spectrum_of_the_time_derivative(d):
     # The m = 0 term is sinc^2(f/fs) exp(-i k d) / d; the aliases m != 0 add at
     # most B(f) = sum_{m != 0} sinc^2(f/fs - m) / sinc^2(f/fs) relative to it
     # (they reach it when u is an integer, where the sum is exactly 1/d).  So
-    # |P(f) - 2 pi i f DTFT(p)(f) / sinc^2(f/fs)| <= B(f) |P(f)|.
+    # |P(f) - 2 pi i f DTFT(p)(f) / sinc^2(f/fs)| <= B(f) |P(f)|.  With a time
+    # origin t0 the samples sit at t0 + k/fs, and the DTFT uses those times.
     c, fs, K = 1500.0, 40e6, 512
-    geo = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
-                       np.array([[0.0, d]]), c, fs, K)
+    sensor = [0.0, d] if dim == 2 else [0.0, 0.0, d]
+    geo = orc.Geometry(dim, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                       np.array([sensor]), c, fs, K, t0=t0)
     p = orc.forward(geo, np.ones(1))[0]
     assert np.count_nonzero(p) in (1, 2) and abs(p.sum() - 1.0 / d) <= 1e-9 / d
     q, f0, df = 8, 0.125e6, 0.125e6
@@ -409,7 +412,8 @@ def test_freq_model_is_the_spectrum_of_the_time_derivative(d):
     for n in range(q):
         f = f0 + n * df
         bound = np.sum(np.sinc(f / fs - m) ** 2) / np.sinc(f / fs) ** 2 * (1 + 1e-3) + 1e-12
-        expected = 2j * np.pi * f * np.sum(p * np.exp(-2j * np.pi * f * k / fs)) / np.sinc(f / fs) ** 2
+        dtft = np.sum(p * np.exp(-2j * np.pi * f * (t0 + k / fs)))
+        expected = 2j * np.pi * f * dtft / np.sinc(f / fs) ** 2
         assert abs(P[n] - expected) <= bound * abs(P[n]), (f, P[n], expected, bound)
         # a planted mistake, the conjugate phase exp(+i k d), must fail somewhere
         wrong = 2j * np.pi * f * np.conj(P[n] / (2j * np.pi * f))
