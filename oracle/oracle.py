@@ -20,7 +20,8 @@ What is computed, and where it comes from:
   (Hestenes-Stiefel recursion for least squares), then a final clamp x >= 0.
 * ``power_iteration``: largest eigenvalue of A^T A (step size for Landweber).
 * ``tv`` / ``tv_grad``: smoothed isotropic total variation (the TV term of
-  Eq. 8 with Psi' = identity).
+  Eq. 8 with Psi' = identity), 2D and 3D.
+* ``min_distance``: the smallest pixel-sensor distance (the geometry check).
 * ``freq_forward`` / ``freq_adjoint``: the frequency-domain measurement matrix
   of Eq. 7 applied to an image, and its adjoint (own loops).
 * ``fista``: the full objective of Eq. 8 (data term, L1 and smoothed TV) by
@@ -29,9 +30,9 @@ What is computed, and where it comes from:
   against the iterative one in Sec. 4 (Experiment 1, Table 2), with the
   universal back-projection trace filter (a reading: the paper names no filter).
 
-Readings where the paper is silent are listed in the design doc; each function
-names the one it uses.  Parity status: every function here is pinned by a
-``-m "not gpu"`` test in ``tests/test_oracle_*.py``.
+Where the paper is silent, each function states the reading it uses.  Parity
+status: every function here is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 
@@ -88,8 +89,15 @@ def _load():
             lib.oracle_min_distance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.oracle_min_distance.restype = ctypes.c_double
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Number of host threads the C loops use (results do not depend on it)."""
+    _load().oracle_set_threads(int(n))
 
 
 def _ptr(a: np.ndarray):
@@ -231,6 +239,7 @@ def dc_flip_bound(geo: Geometry, x, g, delta: float, c=None) -> float:
 
 
 def min_distance(geo: Geometry) -> float:
+    """Smallest pixel-centre to sensor distance (metres), over all pairs."""
     nx, ny, nz = geo.shape
     return float(_load().oracle_min_distance(geo.dim, nx, ny, nz, _ptr(geo.spacing),
                                              _ptr(geo.origin), _ptr(geo.sensors), geo.n_sensors))
@@ -272,7 +281,9 @@ def landweber(geo: Geometry, y, n_iter: int, omega: float, x0=None, nonneg: bool
     return x, np.array(hist)
 
 
-def cgls(geo: Geometry, y, n_iter: int, x0=None, nonneg: bool = True):
+def cgls(geo: Geometry, y, n_iter: int, x0=None, nonneg: bool = True, round_fp32: bool = False,
+         round_steps_fp32: bool = False, op_noise: float = 0.0, noise_seed: int = 0,
+         iterates=None):
     """CGLS (conjugate gradients on A^T A x = A^T y, Hestenes-Stiefel form).
 
     r = y - A x0; s = A^T r; p = s; gamma = ||s||^2; then per iteration
@@ -281,26 +292,51 @@ def cgls(geo: Geometry, y, n_iter: int, x0=None, nonneg: bool = True):
     A zero ||q||^2 or gamma stops the recursion (alpha = 0 / beta = 0).
     Reading: non-negativity is applied once after the last iteration.
     Returns (x, history) with history[n] = ||r_n||^2, n = 0..n_iter.
+
+    Sensitivity models (all off by default; the recursion itself is unchanged):
+    ``round_fp32`` rounds every vector the recursion stores (x, r, s, p and the
+    operator outputs) to FP32, the storage any FP32 implementation uses, with
+    everything else exact; ``round_steps_fp32`` rounds the step lengths alpha
+    and beta to FP32; ``op_noise`` > 0 adds to every operator output
+    i.i.d. Gaussian noise of rms ``op_noise`` times the output's rms (seeded by
+    ``noise_seed``), a model of rounding inside the operators; ``iterates``, a
+    list, receives a copy of x after every iteration (before the clamp).
     """
     y = _f64(y).reshape(geo.n_sensors, geo.n_samples)
-    x = np.zeros(geo.n_pixels) if x0 is None else _f64(x0).ravel().copy()
-    r = y - forward(geo, x)
-    s = adjoint(geo, r)
+    rng = np.random.default_rng(noise_seed)
+
+    def keep(v):
+        return v.astype(np.float32).astype(np.float64) if round_fp32 else v
+
+    def noisy(v):
+        if op_noise > 0.0:
+            v = v + op_noise * np.sqrt(np.mean(v * v)) * rng.standard_normal(v.shape)
+        return keep(v)
+
+    x = keep(np.zeros(geo.n_pixels) if x0 is None else _f64(x0).ravel().copy())
+    r = keep(y - noisy(forward(geo, x)))
+    s = noisy(adjoint(geo, r))
     p = s.copy()
     gamma = float(np.sum(s * s))
     hist = [float(np.sum(r * r))]
     for _ in range(n_iter):
-        q = forward(geo, p)
+        q = noisy(forward(geo, p))
         delta = float(np.sum(q * q))
         alpha = gamma / delta if delta > 0.0 else 0.0
-        x = x + alpha * p
-        r = r - alpha * q
+        if round_steps_fp32:
+            alpha = float(np.float32(alpha))
+        x = keep(x + alpha * p)
+        r = keep(r - alpha * q)
         hist.append(float(np.sum(r * r)))
-        s = adjoint(geo, r)
+        s = noisy(adjoint(geo, r))
         gamma_new = float(np.sum(s * s))
         beta = gamma_new / gamma if gamma > 0.0 else 0.0
+        if round_steps_fp32:
+            beta = float(np.float32(beta))
         gamma = gamma_new
-        p = s + beta * p
+        p = keep(s + beta * p)
+        if iterates is not None:
+            iterates.append(x.copy())
     if nonneg:
         x = np.maximum(x, 0.0)
     return x, np.array(hist)
@@ -314,7 +350,8 @@ def fista(geo: Geometry, y, n_iter: int, tau: float, alpha: float = 0.0, beta: f
     step tau: x_k = prox(z_k - tau grad f(z_k)) for the smooth part f (data term
     and TV_eps), prox the soft threshold of tau alpha |.| (with nonneg: max(0,
     v - tau alpha)), t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 and
-    z_{k+1} = x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1}).  TV needs a 2D grid.
+    z_{k+1} = x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1}).  TV is taken on the
+    image's own grid (2D or 3D).
     Returns (x, history) with history = ||y - A z_k||^2 for k < n_iter and
     ||y - A x_n||^2 last."""
     y = _f64(y).reshape(geo.n_sensors, geo.n_samples)
@@ -329,8 +366,8 @@ def fista(geo: Geometry, y, n_iter: int, tau: float, alpha: float = 0.0, beta: f
         hist.append(float(np.sum(r * r)))
         grad = -2.0 * adjoint(geo, r)
         if beta != 0.0:
-            assert nz == 1, "TV is defined here for 2D grids"
-            grad = grad + beta * tv_grad(z.reshape(ny, nx), eps).ravel()
+            img = z.reshape(ny, nx) if nz == 1 else z.reshape(nz, ny, nx)
+            grad = grad + beta * tv_grad(img, eps).ravel()
         v = z - tau * grad
         if nonneg:
             x_new = np.maximum(v - tau * alpha, 0.0)
@@ -363,31 +400,51 @@ def power_iteration(geo: Geometry, v0, n_iter: int = 50) -> float:
 
 
 # ----------------------------------------------------------------------------
-# smoothed total variation (2D), the TV term of Eq. 8 with Psi' = I
+# smoothed total variation (2D and 3D), the TV term of Eq. 8 with Psi' = I
 # ----------------------------------------------------------------------------
 
-def tv(img2d, eps: float = 1e-4) -> float:
-    """sum_ij sqrt((x[i,j+1]-x[i,j])^2 + (x[i+1,j]-x[i,j])^2 + eps^2), forward
-    differences, zero difference past the last row/column (Neumann)."""
-    x = _f64(img2d)
-    gx = np.zeros_like(x)
-    gy = np.zeros_like(x)
-    gx[:, :-1] = x[:, 1:] - x[:, :-1]
-    gy[:-1, :] = x[1:, :] - x[:-1, :]
-    return float(np.sum(np.sqrt(gx * gx + gy * gy + eps * eps)))
+def _forward_differences(x):
+    """Forward difference of x along every axis, zero past the last index
+    (Neumann).  x: [ny][nx] or [nz][ny][nx]; returns one array per axis."""
+    diffs = []
+    for axis in range(x.ndim):
+        d = np.zeros_like(x)
+        lead = [slice(None)] * x.ndim
+        lag = [slice(None)] * x.ndim
+        lead[axis] = slice(1, None)
+        lag[axis] = slice(None, -1)
+        d[tuple(lag)] = x[tuple(lead)] - x[tuple(lag)]
+        diffs.append(d)
+    return diffs
 
 
-def tv_grad(img2d, eps: float = 1e-4) -> np.ndarray:
-    """Analytic gradient of ``tv``."""
-    x = _f64(img2d)
-    gx = np.zeros_like(x)
-    gy = np.zeros_like(x)
-    gx[:, :-1] = x[:, 1:] - x[:, :-1]
-    gy[:-1, :] = x[1:, :] - x[:-1, :]
-    m = np.sqrt(gx * gx + gy * gy + eps * eps)
-    ax = gx / m
-    ay = gy / m
-    g = -(ax + ay)
-    g[:, 1:] += ax[:, :-1]
-    g[1:, :] += ay[:-1, :]
+def tv(img, eps: float = 1e-4) -> float:
+    """sum over pixels of sqrt(sum_a (x[i + e_a] - x[i])^2 + eps^2): forward
+    differences along each axis a, zero difference past the last index
+    (Neumann).  img: [ny][nx] (2D) or [nz][ny][nx] (3D)."""
+    x = _f64(img)
+    m2 = np.full_like(x, eps * eps)
+    for d in _forward_differences(x):
+        m2 += d * d
+    return float(np.sum(np.sqrt(m2)))
+
+
+def tv_grad(img, eps: float = 1e-4) -> np.ndarray:
+    """Analytic gradient of ``tv``: with a_a = (difference along a) / m at each
+    pixel, dTV/dx_i = -sum_a a_a(i) + sum_a a_a(i - e_a)."""
+    x = _f64(img)
+    diffs = _forward_differences(x)
+    m = np.full_like(x, eps * eps)
+    for d in diffs:
+        m += d * d
+    m = np.sqrt(m)
+    g = np.zeros_like(x)
+    for axis, d in enumerate(diffs):
+        a = d / m
+        g -= a
+        dst = [slice(None)] * x.ndim
+        src = [slice(None)] * x.ndim
+        dst[axis] = slice(1, None)
+        src[axis] = slice(None, -1)
+        g[tuple(dst)] += a[tuple(src)]
     return g

@@ -22,6 +22,7 @@
  * the thread count.
  */
 #include <math.h>
+#include <omp.h>
 #include <stddef.h>
 #include <string.h>
 
@@ -300,3 +301,8 @@ void oracle_freq_adjoint(int dim, int nx, int ny, int nz, const double *spacing,
     g[i] = amp * acc;
   }
 }
+
+/* Threads of the OpenMP loops above (timing of the CPU baseline on 1 core or
+ * all cores; the sums do not depend on it: every output element is summed by
+ * one thread in a fixed order). */
+void oracle_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }

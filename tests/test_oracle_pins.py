@@ -419,3 +419,141 @@ def test_freq_model_is_the_spectrum_of_the_time_derivative(dim, d, t0):
         wrong = 2j * np.pi * f * np.conj(P[n] / (2j * np.pi * f))
         worst_conj = max(worst_conj, abs(wrong - expected) / abs(P[n]))
     assert worst_conj > 0.5
+
+
+def test_tv_3d_constant_and_fd():
+    eps = 1e-4
+    img = np.full((3, 4, 5), -0.7)
+    assert abs(orc.tv(img, eps) - img.size * eps) <= 1e-15
+    assert np.all(orc.tv_grad(img, eps) == 0.0)
+    rng = np.random.default_rng(19)
+    img = rng.uniform(0, 1, (3, 4, 5))
+    g = orc.tv_grad(img, eps)
+    h = 1e-6
+    fd = np.zeros_like(img)
+    for idx in np.ndindex(img.shape):
+        e = np.zeros_like(img)
+        e[idx] = h
+        fd[idx] = (orc.tv(img + e, eps) - orc.tv(img - e, eps)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-7)
+
+
+def test_tv_3d_hand_value():
+    """2x2x2 volume with one unit voxel at (0,0,0), worked by hand: that voxel
+    has differences -1 along x, y and z (sqrt(3 + eps^2)); its three forward
+    neighbours and the other four voxels have none (eps each).  dTV/dx at the
+    unit voxel is 3/sqrt(3 + eps^2); at each of its three neighbours, which see
+    it as their backward neighbour, -1/sqrt(3 + eps^2); elsewhere 0."""
+    eps = 1e-3
+    img = np.zeros((2, 2, 2))
+    img[0, 0, 0] = 1.0
+    m = np.sqrt(3.0 + eps * eps)
+    assert abs(orc.tv(img, eps) - (m + 7 * eps)) <= 1e-15
+    expect = np.zeros((2, 2, 2))
+    expect[0, 0, 0] = 3.0 / m
+    expect[0, 0, 1] = expect[0, 1, 0] = expect[1, 0, 0] = -1.0 / m
+    np.testing.assert_allclose(orc.tv_grad(img, eps), expect, rtol=0, atol=1e-15)
+    # a misplaced axis (a difference taken along the wrong stride) moves these
+    # values: the z neighbour (1,0,0) must carry the backward term
+    assert orc.tv_grad(img, eps)[1, 0, 0] < 0.0
+
+
+def test_min_distance_bruteforce():
+    rng = np.random.default_rng(41)
+    for dim, shape in ((2, (7, 5, 1)), (3, (4, 6, 3))):
+        spacing = (1.1e-4, 0.9e-4, 1.3e-4)
+        origin = ph.centred_origin(shape, spacing)
+        sensors = rng.uniform(-1e-3, 1e-3, (9, dim))
+        geo = orc.Geometry(dim, shape, spacing, origin, sensors, 1500.0, 40e6, 64)
+        axes = [origin[a] + spacing[a] * np.arange(shape[a]) for a in range(dim)]
+        pts = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, dim)
+        brute = np.min(np.linalg.norm(pts[:, None, :] - sensors[None, :, :], axis=-1))
+        assert abs(orc.min_distance(geo) - brute) <= 1e-15
+
+
+def _one_tap_geometry():
+    # one unit pixel at the origin, one sensor 3 mm away: u = 80 exactly, so
+    # the operator is the column with the single entry 1/d at sample 80 (the
+    # first golden case, pinned above)
+    return orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                        np.array([[0.0, 3e-3]]), 1500.0, 4e7, 128)
+
+
+def test_fista_signed_soft_threshold_hand_value():
+    """Three FISTA steps on a one-pixel system, by hand.  With A = the column
+    (1/d at sample 80), m = A^T A = 1/d^2 and g = A^T y = y_80/d; the step from
+    z is v = z + 2 tau (g - m z) and the signed proximal step is
+    x = sign(v) max(|v| - tau alpha, 0).  A negative measurement drives x below
+    zero, so the threshold must move v towards zero from below (v + tau alpha):
+    a threshold taken without the sign, or a projection onto x >= 0, fails."""
+    geo = _one_tap_geometry()
+    d = 3e-3
+    y = np.zeros((1, 128))
+    y[0, 80] = -0.02
+    m, g = 1.0 / d**2, -0.02 / d
+    tau = 0.3 / m
+    alpha = 0.1 * abs(g)
+
+    def shrink(v):
+        return np.sign(v) * max(abs(v) - tau * alpha, 0.0)
+
+    x_prev, z, t = 0.0, 0.0, 1.0
+    for _ in range(3):
+        x = shrink(z + 2.0 * tau * (g - m * z))
+        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        z = x + ((t - 1.0) / t_new) * (x - x_prev)
+        x_prev, t = x, t_new
+    # numbers: step 1 from z = 0 gives v = 2 tau g = 0.6 g/m, and the threshold
+    # tau alpha = 0.03 |g|/m moves it towards zero: x1 = 0.57 g/m = -3.42e-5
+    x1, _ = orc.fista(geo, y, 1, tau, alpha, nonneg=False)
+    assert abs(x1[0] - (-3.42e-5)) <= 1e-15
+    x3, _ = orc.fista(geo, y, 3, tau, alpha, nonneg=False)
+    assert x3[0] < 0.0
+    assert abs(x3[0] - x_prev) <= 1e-12 * abs(x_prev)
+    # with the projection the same steps stop at zero
+    xp, _ = orc.fista(geo, y, 3, tau, alpha, nonneg=True)
+    assert xp[0] == 0.0
+
+
+def test_fista_signed_meets_the_optimality_conditions():
+    # minimiser of ||A x - y||^2 + alpha ||x||_1 (+ beta TV) without x >= 0:
+    # with G the gradient of the smooth part, G_i + alpha sign(x_i) = 0 where
+    # x_i != 0 and |G_i| <= alpha where x_i = 0 (the subgradient condition)
+    prob, geo, m, sigma2 = _tiny_fista_problem(37)
+    rng = np.random.default_rng(38)
+    truth = np.where(rng.uniform(size=prob.n_pixels) < 0.5, rng.uniform(-1.0, 1.0, prob.n_pixels),
+                     0.0)
+    y = m @ truth + 0.02 * rng.standard_normal(m.shape[0])
+    alpha, eps = 0.05 * np.abs(m.T @ y).max(), 1e-2
+    beta = 0.125 * sigma2 * eps
+    tau = 1.0 / (2.0 * sigma2 + 8.0 * beta / eps)
+    x, _ = orc.fista(geo, y, 20000, tau, alpha, beta, eps, nonneg=False)
+    nx, ny, _ = prob.shape
+    g = -2.0 * m.T @ (y - m @ x) + beta * orc.tv_grad(x.reshape(ny, nx), eps).ravel()
+    scale = alpha + np.abs(g).max()
+    nz = np.abs(x) > 1e-12 * np.abs(x).max()
+    assert (x[nz] < 0).any() and (x[nz] > 0).any() and (~nz).any()  # every case exercised
+    assert np.all(np.abs(g[nz] + alpha * np.sign(x[nz])) <= 1e-6 * scale)
+    assert np.all(np.abs(g[~nz]) <= alpha + 1e-6 * scale)
+
+
+def test_fista_3d_tv_meets_the_optimality_conditions():
+    # FISTA with the TV term on a 3D grid: the smooth part's gradient uses the
+    # 3D TV pinned above; at the minimiser over x >= 0 the KKT conditions hold
+    prob = ph.custom(3, (3, 3, 2), (1e-4, 1e-4, 1e-4), ph.planar_array(2, 2, 0.5e-3, 1.2e-3), 60,
+                     seed=39)
+    geo = orc.Geometry.of(prob)
+    m = orc.matrix(geo)
+    sigma2 = float(np.linalg.svd(m, compute_uv=False)[0] ** 2)
+    y = m @ prob.x_true
+    alpha, eps = 0.02 * np.abs(m.T @ y).max(), 1e-2
+    beta = 0.1 * sigma2 * eps
+    tau = 1.0 / (2.0 * sigma2 + 12.0 * beta / eps)  # 3D curvature bound 12 beta / eps
+    x, _ = orc.fista(geo, y, 20000, tau, alpha, beta, eps)
+    nx, ny, nz = prob.shape
+    g = -2.0 * m.T @ (y - m @ x) + beta * orc.tv_grad(x.reshape(nz, ny, nx), eps).ravel()
+    scale = alpha + np.abs(g).max()
+    active = x > 1e-12 * np.abs(x).max()
+    assert active.any()
+    assert np.all(np.abs(g[active] + alpha) <= 1e-6 * scale)
+    assert np.all(g[~active] + alpha >= -1e-6 * scale)
