@@ -72,3 +72,79 @@ def test_reference_arm_runs_on_rank0_only(tmp_path):
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+# ----------------------------------------------------------------------------
+# Sensor sharding of one large frame, checked with the oracle on two gloo ranks:
+# each rank owns half of the sensors, applies A to its own rows (no exchange)
+# and A^T to its own traces; the partial images are all-reduced, and so is the
+# one scalar ||A p||^2 that CGLS needs per iteration (||A^T r||^2 follows from
+# the reduced image on every rank).  The sharded recursion must reproduce the
+# unsharded oracle CGLS: the partition changes only the order of sums.
+# ----------------------------------------------------------------------------
+def _sharded_problem():
+    from paper_2404_10928_gb300 import phantoms as ph
+    return ph.custom(2, (24, 20), (1e-4, 1e-4), ph.ring_sensors(14, 3e-3), 200, seed=91)
+
+
+def _sharded_rank(rank, world, port, out_dir, n_iter):
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle as orc
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob = _sharded_problem()
+    full = orc.Geometry.of(prob)
+    y_full = orc.forward(full, prob.x_true)
+    mine = np.array_split(np.arange(prob.n_sensors), world)[rank]
+    geo = orc.Geometry(prob.dim, prob.shape, prob.spacing, prob.origin, prob.sensors[mine],
+                       prob.c, prob.fs, prob.n_samples, prob.t0, prob.amp_scale)
+    y = y_full[mine]
+
+    def allreduce(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+        dist.all_reduce(t)
+        return t.numpy()
+
+    x = np.zeros(prob.n_pixels)
+    r = y - orc.forward(geo, x)
+    s = allreduce(orc.adjoint(geo, r))           # the image all-reduce after A^T
+    p = s.copy()
+    gamma = float(np.sum(s * s))
+    deltas = []
+    for _ in range(n_iter):
+        q = orc.forward(geo, p)                   # own rows, no exchange
+        delta = float(allreduce(np.array([np.sum(q * q)]))[0])  # the scalar all-reduce
+        deltas.append(delta)
+        alpha = gamma / delta
+        x = x + alpha * p
+        r = r - alpha * q
+        s = allreduce(orc.adjoint(geo, r))
+        gamma_new = float(np.sum(s * s))
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+    dist.barrier()
+    dist.destroy_process_group()
+    np.savez(os.path.join(out_dir, f"shard{rank}.npz"), x=x, deltas=np.array(deltas))
+
+
+def test_sensor_sharded_cgls_matches_unsharded_oracle(tmp_path):
+    import torch.multiprocessing as mp
+    from oracle import oracle as orc
+    world, n_iter = 2, 6
+    mp.spawn(_sharded_rank, args=(world, _free_port(), str(tmp_path), n_iter), nprocs=world,
+             join=True)
+    prob = _sharded_problem()
+    geo = orc.Geometry.of(prob)
+    y = orc.forward(geo, prob.x_true)
+    ref = []
+    orc.cgls(geo, y, n_iter, nonneg=False, iterates=ref)
+    res = [np.load(tmp_path / f"shard{r}.npz") for r in range(world)]
+    # every rank holds the same image, equal to the unsharded CGLS iterate
+    assert np.array_equal(res[0]["x"], res[1]["x"])
+    err = np.linalg.norm(res[0]["x"] - ref[-1]) / np.linalg.norm(ref[-1])
+    assert err <= 1e-10, err
+    # and ||A p||^2 summed over the two shards is the full operator's (first
+    # iteration: p = A^T y)
+    q = orc.forward(geo, orc.adjoint(geo, y))
+    assert abs(res[0]["deltas"][0] - np.sum(q * q)) <= 1e-12 * np.sum(q * q)
