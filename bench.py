@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -105,11 +106,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.environ.get("PA_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"pa_bench_clocks_{os.getpid()}_{gpu_index}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -175,6 +177,56 @@ def oracle_sample(prob, y, target_s: float = 15.0):
     dt = time.perf_counter() - t
     apps = cgls_applications(n_it)
     return prob.pairs * apps / dt, dt, n_it
+
+
+def oracle_detail(c2_prob, c2_y) -> dict:
+    """The rest of the CPU-baseline plan, on the machine's host cores: the benchmark
+    frame's CGLS on one core, the linear-array disk workload in full (power
+    iteration and 10 Landweber steps), and one application of A and of A^T on
+    the 3D planar workload (128^3, dense random image) and on the ragged time
+    series (all 64 frames) -- per-application figures for the workloads whose
+    full reconstruction on the CPU would take far longer."""
+    from oracle import oracle as orc
+    from paper_2404_10928_gb300 import phantoms as ph
+    n_all = cores()
+    out = {"cores_all": n_all}
+    orc.set_threads(1)
+    rate1, secs1, it1 = oracle_sample(c2_prob, c2_y, target_s=5.0)
+    out["ring256_cgls_1core"] = {"pairs_per_s": rate1, "seconds": secs1, "cgls_iterations": it1}
+    orc.set_threads(n_all)
+    out["ring256_cgls_all_cores_vs_1core"] = None
+    d = ph.linear_array_disks()
+    geo = orc.Geometry.of(d)
+    y = orc.forward(geo, d.x_true)
+    t = time.perf_counter()
+    lam = orc.power_iteration(geo, ph.power_start(d.n_pixels), 50)
+    orc.landweber(geo, y, 10, omega=1.0 / lam)
+    dt = time.perf_counter() - t
+    out["disks64_landweber10_full"] = {"seconds": dt, "pairs_per_s": d.pairs * (100 + 21) / dt,
+                                       "includes": "50 power steps + 10 Landweber steps"}
+    v = ph.planar_vessel_tree()
+    geo = orc.Geometry.of(v)
+    xr = np.random.default_rng(0).uniform(0.0, 1.0, v.n_pixels)
+    t = time.perf_counter()
+    pv = orc.forward(geo, xr)
+    tf = time.perf_counter() - t
+    t = time.perf_counter()
+    orc.adjoint(geo, pv)
+    ta = time.perf_counter() - t
+    out["planar128_per_application"] = {"forward_s": tf, "adjoint_s": ta,
+                                        "pairs_per_s": 2 * v.pairs / (tf + ta),
+                                        "cgls30_extrapolated_s": 31 * (tf + ta)}
+    frames = ph.ragged_time_series()
+    t = time.perf_counter()
+    pairs = 0
+    for f in frames:
+        g = orc.Geometry.of(f)
+        orc.adjoint(g, orc.forward(g, f.x_true))
+        pairs += 2 * f.pairs
+    tr = time.perf_counter() - t
+    out["ragged64_per_application"] = {"seconds_all_frames_A_and_AT": tr, "pairs_per_s": pairs / tr,
+                                       "landweber20_extrapolated_s": 20.5 * tr}
+    return out
 
 
 def run_reference(args):
@@ -527,7 +579,7 @@ def run_gpu(args):
     # each rank reconstructs its own frame (same geometry, its own noise draw)
     noise = frame_noise(prob.noise_unit.shape, rank)
     from paper_2404_10928_gb300.autotune import Autotuner
-    tuner = Autotuner(os.path.join(ROOT, "gpurun_out", f"autotune_rank{rank}.json"))
+    tuner = Autotuner()  # cache: PA_TUNE_CACHE, else ~/.cache/pa_gb300/autotune.json
     tuned = tuner.best(prob)
     plan = Plan.from_problem(prob, adj_cluster=tuned["adj_cluster"],
                              fwd_sensors_per_cta=tuned["fwd_sensors_per_cta"])
@@ -536,40 +588,37 @@ def run_gpu(args):
     y_host = ph.add_noise(clean, noise, prob.noise_level).astype(np.float32)
     y = torch.tensor(y_host, device=dev)
     x = torch.zeros(prob.n_pixels, dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush_sum = torch.zeros((), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(timing: bool):
+    def evict_l2():
+        # reading a buffer twice the size of L2 leaves only its (clean) lines
+        # there: the next step finds none of its data cached and has no dirty
+        # lines to write back
+        torch.sum(flush, dim=0, out=flush_sum)
+
+    def step():
         x.zero_()
-        plan.reconstruct(y, "cgls", N_ITER, out=x, kernel_timing=timing)
+        plan.reconstruct(y, "cgls", N_ITER, out=x)
 
     for i in range(max(args.warmup, 0)):
-        step(i % 2 == 0)  # instantiate both graphs (with and without timing events)
-    step(False)
+        step()
+    step()
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    fwd_ms = adj_ms = 0.0
-    n_fwd = n_adj = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         t_wall = time.perf_counter()
         for i in range(args.steps):
-            flush.fill_(float(i))  # evict L2 between timed steps
-            timed_kernels = i == args.steps - 1  # per-launch events on the last step only
+            evict_l2()
             starts[i].record(stream)
-            step(timed_kernels)
+            step()
             ends[i].record(stream)
-            ends[i].synchronize()
-            if timed_kernels:
-                kt = plan.kernel_times()
-                fwd_ms += kt["fwd_ms"]
-                adj_ms += kt["adj_ms"]
-                n_fwd += kt["n_fwd"]
-                n_adj += kt["n_adj"]
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -589,12 +638,23 @@ def run_gpu(args):
         x_np[:] = 0
         plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter()
+    e2e_t = 0.0
     for _ in range(args.steps):
         x_np[:] = 0
-        plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)
-    e2e_t = max_over_ranks(dist, dev, time.perf_counter() - e2e_t)
+        evict_l2()  # the same L2 state as the device-timed steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.reconstruct_host(y_np, "cgls", N_ITER, x_out=x_np)  # waits for the result
+        e2e_t += time.perf_counter() - t0
+    e2e_t = max_over_ranks(dist, dev, e2e_t)
     e2e_value = whole_job_rate(pairs_rank, world, e2e_t)
+
+    # the gathers' own device time: back-to-back launches in the CGLS form, one
+    # pair of events around each run (no event between launches)
+    x_dense = torch.rand(prob.n_pixels, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(0))
+    gt = plan.time_gathers(x_dense, y, reps=100)
+    fwd_ms, adj_ms = gt["fwd_ms"], gt["adj_ms"]
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -617,6 +677,10 @@ def run_gpu(args):
                "kind": "oracle",
                "sample": f"FP64 oracle CGLS, {n_it} iterations ({cgls_applications(n_it)} operator "
                          f"applications) of the same frame, {secs:.1f} s"}
+        if not args.no_extras:
+            cpu["detail"] = oracle_detail(prob, y_host.astype(np.float64))
+            cpu["detail"]["ring256_cgls_all_cores_vs_1core"] = (
+                rate / cpu["detail"]["ring256_cgls_1core"]["pairs_per_s"])
 
     if rank == 0:
         import json as _json
@@ -627,31 +691,41 @@ def run_gpu(args):
         props = torch.cuda.get_device_properties(dev)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        flops = prob.pairs * FLOPS_PER_PAIR
+        fwd_tf = flops / (fwd_ms * 1e-3) / 1e12
+        adj_tf = flops / (adj_ms * 1e-3) / 1e12
         dom_is_adj = adj_ms >= fwd_ms
-        launch_ms = (adj_ms / max(n_adj, 1)) if dom_is_adj else (fwd_ms / max(n_fwd, 1))
-        achieved = prob.pairs * FLOPS_PER_PAIR / (launch_ms * 1e-3) / 1e12
+        achieved = adj_tf if dom_is_adj else fwd_tf
         kname = "k_adjoint<2>" if dom_is_adj else "k_fwd_tile<2>+k_fwd_combine"
+        peak_src = (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                    f"{sm_max:.0f} MHz (MEASURED_PEAKS.json has no FP32 figure)")
         clk = clocks.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames_per_rank_per_step": 1,
-                       "l2": "flushed between timed steps (256 MiB write)",
+                       "l2": "evicted before every timed step (a 256 MiB read), value and e2e alike",
                        "pairs_per_application": prob.pairs,
                        "applications_per_step": apps, "parallelism": f"frame-parallel x{world}"},
             "frames_per_s": world * args.steps / (total_ms * 1e-3),
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": read_traffic(kname),
-                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
-                         "flops_per_launch": prob.pairs * FLOPS_PER_PAIR},
-            "kernels": {"adjoint_ms_per_launch": adj_ms / max(n_adj, 1),
-                        "forward_ms_per_launch": fwd_ms / max(n_fwd, 1),
-                        "adjoint_pairs_per_s": prob.pairs / (adj_ms / max(n_adj, 1) * 1e-3),
-                        "forward_pairs_per_s": prob.pairs / (fwd_ms / max(n_fwd, 1) * 1e-3),
-                        "share_of_step": (adj_ms + fwd_ms) / step_ms[-1] if world == 1 else None,
-                        "timed_on": "last timed step (CUDA events around every gather launch)"},
+                         "traffic": read_traffic(kname), "peak_source": peak_src,
+                         "flops_per_launch": flops},
+            "roofline_adjoint": {"bound": "alu", "kernel": "k_adjoint<2>", "achieved": adj_tf,
+                                 "peak": peak_tflops, "unit": "TFLOP/s",
+                                 "frac": adj_tf / peak_tflops,
+                                 "traffic": read_traffic("k_adjoint<2>"),
+                                 "peak_source": peak_src, "flops_per_launch": flops},
+            "kernels": {"adjoint_ms_per_launch": adj_ms, "forward_ms_per_application": fwd_ms,
+                        "adjoint_pairs_per_s": prob.pairs / (adj_ms * 1e-3),
+                        "forward_pairs_per_s": prob.pairs / (fwd_ms * 1e-3),
+                        "gathers_share_of_step": (adj_ms + fwd_ms) * apps / 2
+                        / (total_ms / args.steps) if world == 1 else None,
+                        "timed_on": "pa_plan_time_gathers: 100 back-to-back launches of each "
+                                    "gather in its CGLS form (dense random image, the bench "
+                                    "traces), one pair of CUDA events per run, warm L2"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(y_host.nbytes + prob.n_pixels * 4),

@@ -140,11 +140,18 @@ typedef struct {
 
 void pa_recon_opts_default(pa_recon_opts *opts);
 
-/* Create a plan for one geometry.  Validates the geometry (PA_ERR_GEOMETRY if
+/* Create a plan for one geometry: the quantities that define the time-domain
+ * measurement matrix K(m,t)_(i,j) of Sec. 3.4 (Eq. 6) -- the pixel positions
+ * r_(i,j) (grid), the p probe positions r_m (sensors_xyz, n_sensors), the
+ * speed c and the q_s sampling instants t = s dt (fs, n_samples, opts->t0).
+ * Validates the geometry (PA_ERR_GEOMETRY if
  * any sensor lies closer than half the smallest pixel spacing to a pixel
  * centre), uploads it and builds the per-(pixel tile, sensor) reference table on
  * the current CUDA device.  Blocks until the table is built.  c > 0 (m/s),
- * fs > 0 (Hz), n_samples >= 2, n_sensors >= 1.  *out receives the plan. */
+ * fs > 0 (Hz), n_samples >= 2, n_sensors >= 1.  *out receives the plan.
+ * Limits (PA_ERR_UNSUPPORTED beyond them): at most 65535 sensors and 65535
+ * pixel tiles (32 x 32 pixels in 2D, 16 x 8 x 8 in 3D, e.g. 8160 x 8160 or
+ * 400^3), n_sensors * n_samples and the pixel count below 2^31. */
 pa_status pa_plan_create(pa_plan **out, const double *sensors_xyz, int n_sensors,
                          const pa_grid *grid, double c, double fs, int n_samples,
                          const pa_plan_opts *opts);
@@ -152,7 +159,9 @@ pa_status pa_plan_create(pa_plan **out, const double *sensors_xyz, int n_sensors
 /* Free the plan and its device memory.  NULL-safe.  Waits for the device. */
 pa_status pa_plan_destroy(pa_plan *plan);
 
-/* Change the speed of sound (rebuilds the reference table; blocks). */
+/* Change the speed c of Eq. 1 and Eq. 6 (read as the speed of sound; the
+ * paper's "speed of light" is taken to be a slip) -- e.g. during speed-of-sound
+ * calibration with pa_dc.  Rebuilds the reference table; blocks. */
 pa_status pa_plan_set_sound_speed(pa_plan *plan, double c);
 
 /* Wait for the device and report (then clear) device-side error flags. */
@@ -228,9 +237,93 @@ pa_status pa_freq_adjoint(pa_plan *plan, int n_freq, double f0, double df, const
                           float *x_dev, pa_stream stream);
 
 /* Largest eigenvalue of A^T A by n_iter power-iteration steps from v0_dev ([N]
- * float32, NULL = ones).  Blocks; *sigma2 receives the estimate. */
+ * float32, NULL = ones).  Blocks; *sigma2 receives the estimate.  The paper's
+ * gradient line (Table 3: 2 kn' (kn mk1r - y), the gradient of the data term
+ * of Eq. 8) needs a step length it does not give; a gradient step on the data
+ * term is stable below 2/sigma^2, so Landweber and FISTA take their default
+ * steps from this estimate. */
 pa_status pa_power_iteration(pa_plan *plan, int n_iter, const float *v0_dev, double *sigma2,
                              pa_stream stream);
+
+/* ---- Several frames on one plan's geometry ------------------------------
+ * A batch of n_frames images seen by the plan's sensors with its speed c (the
+ * frames of a time series at one c, or a training batch): images are
+ * [n_frames][N] float32 and traces [n_frames][S][K] (frame-major, device
+ * memory, caller-owned).  Each operator is one launch over all frames.  The
+ * first call with more frames than any before allocates the plan's
+ * multi-frame workspace (waits for the device; not during a stream capture).
+ * n_frames >= 1 and n_frames * S <= 65535.  Frames on one plan must not run
+ * concurrently with other calls on that plan. */
+
+/* p[f] = A x[f] (Eq. 6 discretised, as pa_forward), for every frame. */
+pa_status pa_forward_frames(pa_plan *plan, int n_frames, const float *x_dev, float *p_dev,
+                            pa_stream stream);
+
+/* x[f] = A^T p[f] (as pa_adjoint), for every frame. */
+pa_status pa_adjoint_frames(pa_plan *plan, int n_frames, const float *p_dev, float *x_dev,
+                            pa_stream stream);
+
+/* r[f] = y[f] - A x[f], the residual of the data term of Eq. 8, and, when
+ * sq_dev is not NULL, sq_dev[f] = ||r[f]||^2 (FP64-class sum, n_frames
+ * doubles on the device).  y_dev in the plan's y_dtype. */
+pa_status pa_residual_frames(pa_plan *plan, int n_frames, const float *x_dev, const void *y_dev,
+                             float *r_dev, double *sq_dev, pa_stream stream);
+
+/* out[f] = xin[f] + coef A^T p[f] + tv_weight tvg[f], then max(0, .) when
+ * nonneg: the fused update of the gradient methods on Eq. 8 (Table 3's gradient
+ * line followed by the step).  xin_dev and tvg_dev may be NULL (zero); out_dev
+ * may alias xin_dev (in place). */
+pa_status pa_adjoint_axpy_frames(pa_plan *plan, int n_frames, const float *p_dev,
+                                 const float *xin_dev, double coef, const float *tvg_dev,
+                                 double tv_weight, int nonneg, float *out_dev, pa_stream stream);
+
+/* *dc_dev = (accumulate ? *dc_dev : 0) + scale * sum_f d/dc <g[f], A(x[f]; c)>
+ * (the derivative of pa_dc summed over the frames; one device double). */
+pa_status pa_dc_frames(pa_plan *plan, int n_frames, const float *x_dev, const float *g_dev,
+                       double scale, int accumulate, double *dc_dev, pa_stream stream);
+
+/* tv_dev[f] = TV_eps(x[f]) and grad_dev[f] = its gradient (as pa_tv). */
+pa_status pa_tv_frames(pa_plan *plan, int n_frames, const float *x_dev, double eps, double *tv_dev,
+                       float *grad_dev, pa_stream stream);
+
+/* One projected Landweber step on every frame (the gradient step of Table 3
+ * on the data term of Eq. 8, plus the projection onto x >= 0 when nonneg):
+ *     x_out[f] = max(0, x[f] + omega A^T (y[f] - A x[f])).
+ * x_out_dev must not alias x_dev. */
+pa_status pa_landweber_step_frames(pa_plan *plan, int n_frames, const float *x_dev,
+                                   const void *y_dev, double omega, int nonneg, float *x_out_dev,
+                                   pa_stream stream);
+
+/* Vector-Jacobian product of pa_landweber_step_frames for an incoming
+ * gradient g_out with respect to x_out: with z = x + omega A^T (y - A x) and
+ * gz = g_out where x_out > 0 (everywhere when !nonneg),
+ *     gx = gz - omega A^T A gz                                  (d/dx),
+ *     gy = omega A gz                        (d/dy; skipped when NULL),
+ *     *dc_dev = omega (<(dA/dc) gz, y - A x> - <(dA/dc) x, A gz>)
+ *               summed over frames                 (skipped when NULL).
+ * x_out_dev is the step's output for the same x, y, omega and nonneg. */
+pa_status pa_landweber_step_vjp_frames(pa_plan *plan, int n_frames, const float *x_dev,
+                                       const void *y_dev, const float *x_out_dev,
+                                       const float *g_out_dev, double omega, int nonneg,
+                                       float *gx_dev, float *gy_dev, double *dc_dev,
+                                       pa_stream stream);
+
+/* The loss sum_f ||A x[f] - y[f]||^2 + tv_weight TV_eps(x[f]) (the data and TV
+ * terms of Eq. 8 with Psi' = identity) into *loss_dev (one device double),
+ * with the residuals r[f] = y[f] - A x[f] in r_dev and, when tv_weight != 0,
+ * the TV gradients in tvgrad_dev (both kept for the vector-Jacobian product). */
+pa_status pa_data_tv_loss_frames(pa_plan *plan, int n_frames, const float *x_dev,
+                                 const void *y_dev, double tv_weight, double eps,
+                                 double *loss_dev, float *r_dev, float *tvgrad_dev,
+                                 pa_stream stream);
+
+/* Gradients of that loss times g_loss, from its residuals and TV gradients:
+ *     gx[f] = g_loss (-2 A^T r[f] + tv_weight tvgrad[f])   (skipped when NULL),
+ *     *dc_dev = -2 g_loss sum_f <r[f], (dA/dc) x[f]>        (skipped when NULL). */
+pa_status pa_data_tv_loss_vjp_frames(pa_plan *plan, int n_frames, const float *x_dev,
+                                     const float *r_dev, const float *tvgrad_dev,
+                                     double tv_weight, double g_loss, float *gx_dev,
+                                     double *dc_dev, pa_stream stream);
 
 /* Derivative of <g, A(x; c)> with respect to the speed of sound c (the c of
  * Eq. 1 and Eq. 6), for speed-of-sound calibration:
@@ -271,6 +364,19 @@ pa_status pa_reconstruct(pa_plan *plan, pa_method method, int n_iter, const void
 pa_status pa_reconstruct_host(pa_plan *plan, pa_method method, int n_iter, const void *y_host,
                               float *x_host, const pa_recon_opts *opts, pa_stream stream);
 
+/* Device time of the two gathers in the form a CGLS iteration runs them, for
+ * benchmarks and roofline figures: after one warm-up of each, `reps`
+ * back-to-back applications of A to x_dev (the tile gather and the window
+ * combine, storing the per-CTA partials of ||A x||^2), then `reps` back-to-back
+ * launches of the A^T gather (storing the partials of ||A^T r||^2) on p_dev,
+ * packed once beforehand.  Each of the two runs is bracketed by one pair of
+ * CUDA events on `stream`, with no event between its launches.  x_dev: [N]
+ * float32; p_dev: [S][K] float32 (device); outputs go to the plan's workspace
+ * only.  Blocks; *fwd_ms and *adj_ms receive the average time of one
+ * application.  reps >= 1. */
+pa_status pa_plan_time_gathers(pa_plan *plan, int reps, const float *x_dev, const float *p_dev,
+                               double *fwd_ms, double *adj_ms, pa_stream stream);
+
 /* Sum of the device durations (ms) and counts of the A and A^T gather launches
  * of the last reconstruction run with kernel_timing = 1.  Call after the stream
  * finished.  Any pointer may be NULL. */
@@ -291,11 +397,13 @@ pa_status pa_plan_kernel_times(pa_plan *plan, double *fwd_ms, int *n_fwd, double
  * library holds it until the process exits.  Geometries needing more scratch
  * than that, or a staged trace window of more than 48 KiB of shared memory,
  * return PA_ERR_UNSUPPORTED with a message (use a plan instead).
- *   - The first call on a device looks up the array's device address (a
- *     runtime symbol query, not an allocation); make that first call before
- *     any stream capture on that device.
- *   - Each call rebuilds the geometry tables in the array and blocks until they
- *     are built; the adjoint itself is then enqueued on `stream`.
+ *   - opts is validated as pa_plan_create validates it; of its fields, t0,
+ *     amp_scale and adj_cluster are used (y_dtype and fwd_sensors_per_cta
+ *     concern entry points this one does not run).
+ *   - Every call looks up the array's address on the current device (a runtime
+ *     symbol query, not an allocation), rebuilds the geometry tables in the
+ *     array and blocks until they are built; the adjoint itself is then
+ *     enqueued on `stream`.
  *   - All calls share the one array, which keeps the last call's contents:
  *     calls that overlap on the GPU (other streams, other host threads) race
  *     and corrupt each other's results; serialise them.
@@ -305,7 +413,10 @@ pa_status pa_adjoint_static(const double *sensors_xyz, int n_sensors, const pa_g
                             const float *p_dev, float *x_dev, pa_stream stream);
 
 /* Batched projected Landweber over many frames of uneven size (grid, sensors,
- * samples may all differ; a hemodynamic time series, say), one plan per frame.
+ * samples may all differ), one plan per frame.  The paper reconstructs frames
+ * of a 166-frame murine vascular series one at a time (Sec. 4, Experiment 1)
+ * and names hemodynamic monitoring as the application its speed-up is for
+ * (Abstract, Sec. 5): a time series of frames is the unit of work here.
  * pa_batch_create groups existing plans (same device and dimension); the plans'
  * workspaces are used by the batch, so they must not run other work meanwhile.
  * pa_batch_landweber runs n_iter steps x_f <- max(0, x_f + omega_f A_f^T(y_f -
@@ -324,6 +435,24 @@ pa_status pa_batch_destroy(pa_batch *batch);
 pa_status pa_batch_landweber(pa_batch *batch, int n_iter, const void *const *y_dev,
                              float *const *x_dev, const double *omega, int nonneg,
                              double *residual_history_host, pa_stream stream);
+
+/* Limit of every grid-barrier wait inside the batch's persistent launch, in
+ * seconds (default 2; 0 <= seconds <= 3600).  A wait that runs past it gives
+ * up: the launch finishes without blocking the GPU, its results are invalid,
+ * and pa_batch_landweber reports PA_ERR_TIMEOUT when it waits for the stream
+ * (residual_history_host given).  The next call starts from a clean barrier
+ * state.  With 0 every wait that does not find its barrier complete at the
+ * first poll gives up, which lets a test exercise this path. */
+pa_status pa_batch_set_wait_limit(pa_batch *batch, double seconds);
+
+/* Test hook: the next `after` device allocations made by the library (plan
+ * tables and workspaces, reconstruction workspace, batch buffers) succeed and
+ * every later one fails with PA_ERR_OOM as if the device were out of memory,
+ * until the hook is reset with after = -1 (the default: no injection).  The
+ * entry point that hits the failure returns PA_ERR_OOM and frees what it had
+ * allocated; a plan whose workspace allocation failed stays valid (destroy it
+ * or retry).  after < -1 returns PA_ERR_INVALID_ARG.  Process-wide. */
+pa_status pa_debug_fail_allocations(long long after);
 
 const char *pa_status_string(pa_status status);
 const char *pa_last_error(void);

@@ -83,12 +83,31 @@ SIGNATURES = {
     "pa_reconstruct_host": (c_int, [_P, c_int, c_int, c_void_p, c_void_p,
                                     ctypes.POINTER(pa_recon_opts), _STREAM]),
     "pa_plan_kernel_times": (c_int, [_P, _DP, ctypes.POINTER(c_int), _DP, ctypes.POINTER(c_int)]),
+    "pa_plan_time_gathers": (c_int, [_P, c_int, c_void_p, c_void_p, _DP, _DP, _STREAM]),
     "pa_dc": (c_int, [_P, c_void_p, c_void_p, c_void_p, _STREAM]),
     "pa_batch_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int]),
     "pa_batch_destroy": (c_int, [c_void_p]),
     "pa_batch_landweber": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), _DP, c_int, _DP, _STREAM]),
+    "pa_batch_set_wait_limit": (c_int, [c_void_p, c_double]),
+    "pa_debug_fail_allocations": (c_int, [ctypes.c_longlong]),
     "pa_tv": (c_int, [_P, c_void_p, c_double, c_void_p, c_void_p, _STREAM]),
+    "pa_forward_frames": (c_int, [_P, c_int, c_void_p, c_void_p, _STREAM]),
+    "pa_adjoint_frames": (c_int, [_P, c_int, c_void_p, c_void_p, _STREAM]),
+    "pa_residual_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_void_p, c_void_p, _STREAM]),
+    "pa_adjoint_axpy_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_double, c_void_p,
+                                       c_double, c_int, c_void_p, _STREAM]),
+    "pa_dc_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_double, c_int, c_void_p, _STREAM]),
+    "pa_tv_frames": (c_int, [_P, c_int, c_void_p, c_double, c_void_p, c_void_p, _STREAM]),
+    "pa_landweber_step_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_double, c_int,
+                                         c_void_p, _STREAM]),
+    "pa_landweber_step_vjp_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                             c_double, c_int, c_void_p, c_void_p, c_void_p,
+                                             _STREAM]),
+    "pa_data_tv_loss_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_double, c_double,
+                                       c_void_p, c_void_p, c_void_p, _STREAM]),
+    "pa_data_tv_loss_vjp_frames": (c_int, [_P, c_int, c_void_p, c_void_p, c_void_p, c_double,
+                                           c_double, c_void_p, c_void_p, _STREAM]),
     "pa_adjoint_static": (c_int, [_DP, c_int, ctypes.POINTER(pa_grid), c_double, c_double, c_int,
                                   ctypes.POINTER(pa_plan_opts), c_void_p, c_void_p, _STREAM]),
     "pa_status_string": (ctypes.c_char_p, [c_int]),

@@ -228,6 +228,160 @@ class Plan:
                               _stream_handle(self.device)), "pa_tv")
         return val, grad
 
+    # -- several frames on this geometry (one launch per operator) ----------
+    def _frames_img(self, t: torch.Tensor, name: str) -> int:
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be a float32 tensor on {self.device}")
+        if not t.is_contiguous() or t.numel() % self.n_pixels or t.numel() == 0:
+            raise ValueError(f"{name} must be contiguous with a multiple of {self.n_pixels} elements")
+        return t.numel() // self.n_pixels
+
+    def _frames_trace(self, t: torch.Tensor, n: int, name: str, dtype=torch.float32):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype:
+            raise ValueError(f"{name} must be a {dtype} tensor on {self.device}")
+        if not t.is_contiguous() or t.numel() != n * self.n_sensors * self.n_samples:
+            raise ValueError(f"{name} must be contiguous with {n} x {self.n_sensors} x "
+                             f"{self.n_samples} elements")
+
+    def _ydtype(self):
+        return torch.float16 if self.y_dtype == "f16" else torch.float32
+
+    def forward_frames(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """p[f] = A x[f] for x of shape [F, N]; returns [F, S, K]."""
+        n = self._frames_img(x, "x")
+        if out is None:
+            out = torch.empty((n, self.n_sensors, self.n_samples), device=self.device)
+        self._frames_trace(out, n, "out")
+        check(self._lib.pa_forward_frames(self._h, n, x.data_ptr(), out.data_ptr(),
+                                          _stream_handle(self.device)), "pa_forward_frames")
+        return out
+
+    def adjoint_frames(self, p: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """x[f] = A^T p[f] for p of shape [F, S, K]; returns [F, N]."""
+        n = p.numel() // max(self.n_sensors * self.n_samples, 1)
+        self._frames_trace(p, n, "p")
+        if out is None:
+            out = torch.empty((n, self.n_pixels), device=self.device)
+        self._frames_img(out, "out")
+        check(self._lib.pa_adjoint_frames(self._h, n, p.data_ptr(), out.data_ptr(),
+                                          _stream_handle(self.device)), "pa_adjoint_frames")
+        return out
+
+    def residual_frames(self, x: torch.Tensor, y: torch.Tensor, r: Optional[torch.Tensor] = None,
+                        norms: bool = False):
+        """r[f] = y[f] - A x[f] (and the float64 norms ||r[f]||^2 when asked)."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(y, n, "y", self._ydtype())
+        if r is None:
+            r = torch.empty((n, self.n_sensors, self.n_samples), device=self.device)
+        self._frames_trace(r, n, "r")
+        sq = torch.empty(n, dtype=torch.float64, device=self.device) if norms else None
+        check(self._lib.pa_residual_frames(self._h, n, x.data_ptr(), y.data_ptr(), r.data_ptr(),
+                                           sq.data_ptr() if norms else None,
+                                           _stream_handle(self.device)), "pa_residual_frames")
+        return (r, sq) if norms else r
+
+    def adjoint_axpy_frames(self, p: torch.Tensor, coef: float, xin: Optional[torch.Tensor] = None,
+                            tvg: Optional[torch.Tensor] = None, tv_weight: float = 0.0,
+                            nonneg: bool = False, out: Optional[torch.Tensor] = None):
+        """out[f] = [max(0,)](xin[f] + coef A^T p[f] + tv_weight tvg[f])."""
+        n = p.numel() // max(self.n_sensors * self.n_samples, 1)
+        self._frames_trace(p, n, "p")
+        for t, name in ((xin, "xin"), (tvg, "tvg")):
+            if t is not None and self._frames_img(t, name) != n:
+                raise ValueError(f"{name} must hold {n} frames")
+        if out is None:
+            out = torch.empty((n, self.n_pixels), device=self.device)
+        self._frames_img(out, "out")
+        check(self._lib.pa_adjoint_axpy_frames(
+            self._h, n, p.data_ptr(), xin.data_ptr() if xin is not None else None, float(coef),
+            tvg.data_ptr() if tvg is not None else None, float(tv_weight), int(bool(nonneg)),
+            out.data_ptr(), _stream_handle(self.device)), "pa_adjoint_axpy_frames")
+        return out
+
+    def dc_frames(self, x: torch.Tensor, g: torch.Tensor, scale: float = 1.0,
+                  out: Optional[torch.Tensor] = None, accumulate: bool = False):
+        """scale * sum_f d/dc <g[f], A(x[f]; c)> as a float64 scalar tensor."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(g, n, "g")
+        if out is None:
+            out = torch.zeros((), dtype=torch.float64, device=self.device)
+        check(self._lib.pa_dc_frames(self._h, n, x.data_ptr(), g.data_ptr(), float(scale),
+                                     int(bool(accumulate)), out.data_ptr(),
+                                     _stream_handle(self.device)), "pa_dc_frames")
+        return out
+
+    def tv_frames(self, x: torch.Tensor, eps: float = 1e-4, grad: Optional[torch.Tensor] = None):
+        """Per-frame smoothed TV (float64 [F]) and gradients ([F, N])."""
+        n = self._frames_img(x, "x")
+        if grad is None:
+            grad = torch.empty((n, self.n_pixels), device=self.device)
+        self._frames_img(grad, "grad")
+        val = torch.empty(n, dtype=torch.float64, device=self.device)
+        check(self._lib.pa_tv_frames(self._h, n, x.data_ptr(), float(eps), val.data_ptr(),
+                                     grad.data_ptr(), _stream_handle(self.device)), "pa_tv_frames")
+        return val, grad
+
+    def landweber_step_frames(self, x: torch.Tensor, y: torch.Tensor, omega: float,
+                              nonneg: bool = True, out: Optional[torch.Tensor] = None):
+        """x_out[f] = [max(0,)](x[f] + omega A^T (y[f] - A x[f]))."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(y, n, "y", self._ydtype())
+        if out is None:
+            out = torch.empty((n, self.n_pixels), device=self.device)
+        self._frames_img(out, "out")
+        check(self._lib.pa_landweber_step_frames(self._h, n, x.data_ptr(), y.data_ptr(),
+                                                 float(omega), int(bool(nonneg)), out.data_ptr(),
+                                                 _stream_handle(self.device)),
+              "pa_landweber_step_frames")
+        return out
+
+    def landweber_step_vjp_frames(self, x, y, x_out, g_out, omega: float, nonneg: bool = True,
+                                  need_y: bool = False, need_c: bool = False):
+        """(gx, gy or None, gc or None) of one Landweber step for the gradient g_out."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(y, n, "y", self._ydtype())
+        for t, name in ((x_out, "x_out"), (g_out, "g_out")):
+            if self._frames_img(t, name) != n:
+                raise ValueError(f"{name} must hold {n} frames")
+        gx = torch.empty((n, self.n_pixels), device=self.device)
+        gy = torch.empty((n, self.n_sensors, self.n_samples), device=self.device) if need_y else None
+        gc = torch.zeros((), dtype=torch.float64, device=self.device) if need_c else None
+        check(self._lib.pa_landweber_step_vjp_frames(
+            self._h, n, x.data_ptr(), y.data_ptr(), x_out.data_ptr(), g_out.data_ptr(),
+            float(omega), int(bool(nonneg)), gx.data_ptr(),
+            gy.data_ptr() if gy is not None else None, gc.data_ptr() if gc is not None else None,
+            _stream_handle(self.device)), "pa_landweber_step_vjp_frames")
+        return gx, gy, gc
+
+    def data_tv_loss_frames(self, x: torch.Tensor, y: torch.Tensor, tv_weight: float,
+                            eps: float = 1e-4):
+        """(loss float64 scalar, residuals [F, S, K], TV gradients [F, N] or None)."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(y, n, "y", self._ydtype())
+        loss = torch.empty((), dtype=torch.float64, device=self.device)
+        r = torch.empty((n, self.n_sensors, self.n_samples), device=self.device)
+        tg = torch.empty((n, self.n_pixels), device=self.device) if tv_weight != 0.0 else None
+        check(self._lib.pa_data_tv_loss_frames(
+            self._h, n, x.data_ptr(), y.data_ptr(), float(tv_weight), float(eps), loss.data_ptr(),
+            r.data_ptr(), tg.data_ptr() if tg is not None else None, _stream_handle(self.device)),
+            "pa_data_tv_loss_frames")
+        return loss, r, tg
+
+    def data_tv_loss_vjp_frames(self, x, r, tvgrad, tv_weight: float, g_loss: float,
+                                need_x: bool = True, need_c: bool = False):
+        """(gx or None, gc or None) of the data + TV loss times g_loss."""
+        n = self._frames_img(x, "x")
+        self._frames_trace(r, n, "r")
+        gx = torch.empty((n, self.n_pixels), device=self.device) if need_x else None
+        gc = torch.zeros((), dtype=torch.float64, device=self.device) if need_c else None
+        check(self._lib.pa_data_tv_loss_vjp_frames(
+            self._h, n, x.data_ptr(), r.data_ptr(),
+            tvgrad.data_ptr() if tvgrad is not None else None, float(tv_weight), float(g_loss),
+            gx.data_ptr() if gx is not None else None, gc.data_ptr() if gc is not None else None,
+            _stream_handle(self.device)), "pa_data_tv_loss_vjp_frames")
+        return gx, gc
+
     def power_iteration(self, n_iter: int = 50, v0: Optional[torch.Tensor] = None) -> float:
         if v0 is not None:
             self._check_tensor(v0, self.n_pixels, "v0")
@@ -304,6 +458,17 @@ class Plan:
                                             _stream_handle(self.device)), "pa_reconstruct_host")
         return x_out
 
+    def time_gathers(self, x: torch.Tensor, p: torch.Tensor, reps: int = 20) -> dict:
+        """Average device time (ms) of one application of A and of one A^T
+        gather launch, each timed over `reps` back-to-back launches."""
+        self._check_tensor(x, self.n_pixels, "x")
+        self._check_tensor(p, self.n_sensors * self.n_samples, "p")
+        fm, am = ctypes.c_double(), ctypes.c_double()
+        check(self._lib.pa_plan_time_gathers(self._h, int(reps), x.data_ptr(), p.data_ptr(),
+                                             ctypes.byref(fm), ctypes.byref(am),
+                                             _stream_handle(self.device)), "pa_plan_time_gathers")
+        return {"fwd_ms": fm.value, "adj_ms": am.value, "reps": int(reps)}
+
     def kernel_times(self) -> dict:
         fm, am = ctypes.c_double(), ctypes.c_double()
         fn, an = ctypes.c_int(), ctypes.c_int()
@@ -341,6 +506,10 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of each grid-barrier wait of the persistent launch (seconds)."""
+        check(self._lib.pa_batch_set_wait_limit(self._h, float(seconds)), "pa_batch_set_wait_limit")
 
     def landweber(self, ys, xs, omegas, n_iter: int, nonneg: bool = True, history: bool = False):
         """Run n_iter projected Landweber steps on every frame in place (xs are the

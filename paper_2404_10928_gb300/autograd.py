@@ -1,20 +1,29 @@
 """Differentiable forms of the time-of-flight operator for PyTorch.
 
-``ForwardOp`` (p = A(x; c)) and ``AdjointOp`` (g = A^T(r; c)) are
-``torch.autograd.Function``s whose backward passes are the library's own
-kernels: the backward of A is A^T, the backward of A^T is A, and the derivative
-with respect to the speed of sound c (the c of Eq. 1 and Eq. 6) is ``pa_dc``:
+Every function here is marshalling: the arithmetic of each forward and
+backward pass runs in the library's kernels, one launch per operator for all
+frames of a batch (images ``[..., N]``, traces ``[..., S, K]``; the leading
+dimensions are frames sharing the plan's geometry and c).
 
-    d/dc <g, A(x; c)>   = pa_dc(x, g)
-    <v, (dA^T/dc) r>    = <(dA/dc) v, r> = pa_dc(v, r).
+* ``ForwardOp`` (p = A(x; c)) and ``AdjointOp`` (g = A^T(r; c)): the backward
+  of A is A^T and vice versa; the derivative with respect to the speed of sound
+  c (the c of Eq. 1 and Eq. 6) is the library's speed-of-sound derivative
+  summed over the frames:
+      d/dc <g, A(x; c)>   = pa_dc_frames(x, g)
+      <v, (dA^T/dc) r>    = <(dA/dc) v, r> = pa_dc_frames(v, r).
+* ``TVOp``: the smoothed TV term of Eq. 8 per frame (``pa_tv_frames``).
+* ``DataTVLoss`` / ``data_tv_loss``: sum over frames of ||A(x; c) - p||^2 +
+  tv_weight TV(x), the data and TV terms of Eq. 8, with residual, norms, TV and
+  the loss total computed by ``pa_data_tv_loss_frames`` and the gradients in x
+  and c by ``pa_data_tv_loss_vjp_frames``.
+* ``LandweberStep`` / ``UnrolledLandweber``: projected Landweber steps
+  x <- max(0, x + omega A^T(y - A(x; c))) (``pa_landweber_step_frames``), whose
+  backward (``pa_landweber_step_vjp_frames``) gives the gradients in x, y and
+  c; the unrolled loop checkpoints every step (only x_k is kept and each step
+  is recomputed in backward).
 
-``TVOp`` is the smoothed TV term of Eq. 8 (``pa_tv``).  ``UnrolledLandweber``
-chains projected Landweber steps x <- max(0, x - omega A^T(A(x; c) - y)) and
-checkpoints every step (only x_k is kept; A x_k is recomputed in backward).
-
-Images are ``[..., N]`` float32 CUDA tensors and traces ``[..., S, K]``; leading
-dimensions are a batch of frames sharing the plan's geometry and c.  c is a
-0-d tensor; changing it rebuilds the plan's reference table (a blocking call).
+c is a 0-d tensor; changing it rebuilds the plan's reference table (a
+blocking call).
 """
 from __future__ import annotations
 
@@ -28,21 +37,28 @@ def _set_c(plan, c) -> None:
         plan.set_sound_speed(cv)
 
 
-def _frames(t: torch.Tensor, n: int) -> torch.Tensor:
-    return t.reshape(-1, n).contiguous()
+def _img(t: torch.Tensor, plan) -> torch.Tensor:
+    return t.reshape(-1, plan.n_pixels).contiguous()
+
+
+def _trace(t: torch.Tensor, plan) -> torch.Tensor:
+    return t.reshape(-1, plan.n_sensors, plan.n_samples).contiguous()
+
+
+def _upstream(g: torch.Tensor) -> float:
+    """The incoming gradient of a scalar output, as the factor the library
+    applies to the gradients it forms."""
+    return float(g)
 
 
 class ForwardOp(torch.autograd.Function):
-    """p = A(x; c) with gradients for x (A^T) and c (pa_dc)."""
+    """p = A(x; c) with gradients for x (A^T) and c (speed-of-sound derivative)."""
 
     @staticmethod
     def forward(ctx, x, c, plan):
         _set_c(plan, c)
-        xb = _frames(x, plan.n_pixels)
-        out = torch.empty((xb.shape[0], plan.n_sensors, plan.n_samples), device=x.device,
-                          dtype=torch.float32)
-        for b in range(xb.shape[0]):
-            plan.forward(xb[b], out=out[b])
+        xb = _img(x, plan)
+        out = plan.forward_frames(xb)
         ctx.plan = plan
         ctx.xshape = x.shape
         ctx.save_for_backward(xb, c)
@@ -53,31 +69,23 @@ class ForwardOp(torch.autograd.Function):
         xb, c = ctx.saved_tensors
         plan = ctx.plan
         _set_c(plan, c)
-        gb = _frames(gp, plan.n_sensors * plan.n_samples)
+        gb = _trace(gp.to(torch.float32), plan)
         gx = gc = None
         if ctx.needs_input_grad[0]:
-            gx = torch.empty_like(xb)
-            for b in range(xb.shape[0]):
-                plan.adjoint(gb[b], out=gx[b])
-            gx = gx.reshape(ctx.xshape)
+            gx = plan.adjoint_frames(gb).reshape(ctx.xshape)
         if ctx.needs_input_grad[1]:
-            tot = torch.zeros((), dtype=torch.float64, device=xb.device)
-            for b in range(xb.shape[0]):
-                tot = tot + plan.dc(xb[b], gb[b])
-            gc = tot.to(c.dtype)
+            gc = plan.dc_frames(xb, gb).to(c.dtype)
         return gx, gc, None
 
 
 class AdjointOp(torch.autograd.Function):
-    """g = A^T(r; c) with gradients for r (A) and c (pa_dc)."""
+    """g = A^T(r; c) with gradients for r (A) and c (speed-of-sound derivative)."""
 
     @staticmethod
     def forward(ctx, r, c, plan):
         _set_c(plan, c)
-        rb = _frames(r, plan.n_sensors * plan.n_samples)
-        out = torch.empty((rb.shape[0], plan.n_pixels), device=r.device, dtype=torch.float32)
-        for b in range(rb.shape[0]):
-            plan.adjoint(rb[b], out=out[b])
+        rb = _trace(r, plan)
+        out = plan.adjoint_frames(rb)
         ctx.plan = plan
         ctx.rshape = r.shape
         ctx.save_for_backward(rb, c)
@@ -88,63 +96,118 @@ class AdjointOp(torch.autograd.Function):
         rb, c = ctx.saved_tensors
         plan = ctx.plan
         _set_c(plan, c)
-        gb = _frames(gg, plan.n_pixels)
+        gb = _img(gg.to(torch.float32), plan)
         gr = gc = None
         if ctx.needs_input_grad[0]:
-            gr = torch.empty_like(rb)
-            for b in range(rb.shape[0]):
-                plan.forward(gb[b], out=gr[b])
-            gr = gr.reshape(ctx.rshape)
+            gr = plan.forward_frames(gb).reshape(ctx.rshape)
         if ctx.needs_input_grad[1]:
-            tot = torch.zeros((), dtype=torch.float64, device=rb.device)
-            for b in range(rb.shape[0]):
-                tot = tot + plan.dc(gb[b], rb[b])
-            gc = tot.to(c.dtype)
+            gc = plan.dc_frames(gb, rb).to(c.dtype)
         return gr, gc, None
 
 
 class TVOp(torch.autograd.Function):
-    """Sum over frames of the smoothed TV (float64 scalar); backward uses pa_tv's gradient."""
+    """Per-frame smoothed TV (float64 [frames]); backward uses the gradients
+    pa_tv_frames returns with the values."""
 
     @staticmethod
     def forward(ctx, x, plan, eps):
-        xb = _frames(x, plan.n_pixels)
-        grads = torch.empty_like(xb)
-        tot = torch.zeros((), dtype=torch.float64, device=x.device)
-        for b in range(xb.shape[0]):
-            val, _ = plan.tv(xb[b], eps, grad=grads[b])
-            tot = tot + val
+        xb = _img(x, plan)
+        vals, grads = plan.tv_frames(xb, eps)
         ctx.save_for_backward(grads)
         ctx.xshape = x.shape
-        return tot
+        return vals
 
     @staticmethod
     def backward(ctx, gv):
         (grads,) = ctx.saved_tensors
-        return (gv.to(torch.float32) * grads).reshape(ctx.xshape), None, None
+        return (gv.to(torch.float32)[:, None] * grads).reshape(ctx.xshape), None, None
+
+
+class DataTVLoss(torch.autograd.Function):
+    """sum over frames of ||A(x; c) - p||^2 + tv_weight TV_eps(x) (float64
+    scalar), with gradients in x and c; p (the measured traces) gets none."""
+
+    @staticmethod
+    def forward(ctx, x, c, p, plan, tv_weight, eps):
+        _set_c(plan, c)
+        xb = _img(x, plan)
+        loss, r, tg = plan.data_tv_loss_frames(xb, _trace(p.to(torch.float32), plan),
+                                               float(tv_weight), float(eps))
+        ctx.plan = plan
+        ctx.xshape = x.shape
+        ctx.tv_weight = float(tv_weight)
+        ctx.save_for_backward(xb, r, tg if tg is not None else xb, c)
+        ctx.has_tv = tg is not None
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        xb, r, tg, c = ctx.saved_tensors
+        plan = ctx.plan
+        _set_c(plan, c)
+        gx, gc = plan.data_tv_loss_vjp_frames(xb, r, tg if ctx.has_tv else None, ctx.tv_weight,
+                                              _upstream(g), need_x=ctx.needs_input_grad[0],
+                                              need_c=ctx.needs_input_grad[1])
+        if gx is not None:
+            gx = gx.reshape(ctx.xshape)
+        if gc is not None:
+            gc = gc.to(c.dtype)
+        return gx, gc, None, None, None, None
 
 
 def data_tv_loss(plan, x, c, p, tv_weight: float = 1e-3, eps: float = 1e-4):
     """||A(x; c) - p||^2 + tv_weight * TV(x), summed over frames (float64 scalar)."""
-    r = ForwardOp.apply(x, c, plan) - p
-    return (r.double() ** 2).sum() + tv_weight * TVOp.apply(x, plan, eps)
+    return DataTVLoss.apply(x, c, p, plan, tv_weight, eps)
+
+
+class LandweberStep(torch.autograd.Function):
+    """x_out = max(0, x + omega A^T (y - A(x; c))) (the projection only with
+    nonneg), with gradients in x, y and c."""
+
+    @staticmethod
+    def forward(ctx, x, y, c, plan, omega, nonneg):
+        _set_c(plan, c)
+        xb = _img(x, plan)
+        yb = _trace(y, plan)
+        out = plan.landweber_step_frames(xb, yb, float(omega), bool(nonneg))
+        ctx.plan = plan
+        ctx.shapes = (x.shape, y.shape)
+        ctx.omega, ctx.nonneg = float(omega), bool(nonneg)
+        ctx.save_for_backward(xb, yb, out, c)
+        return out.reshape(x.shape)
+
+    @staticmethod
+    def backward(ctx, g):
+        xb, yb, out, c = ctx.saved_tensors
+        plan = ctx.plan
+        _set_c(plan, c)
+        gx, gy, gc = plan.landweber_step_vjp_frames(
+            xb, yb, out, _img(g.to(torch.float32), plan), ctx.omega, ctx.nonneg,
+            need_y=ctx.needs_input_grad[1], need_c=ctx.needs_input_grad[2])
+        gx = gx.reshape(ctx.shapes[0])
+        if gy is not None:
+            gy = gy.reshape(ctx.shapes[1])
+        if gc is not None:
+            gc = gc.to(c.dtype)
+        return gx, gy, gc, None, None, None
 
 
 class UnrolledLandweber(torch.nn.Module):
-    """n steps of x <- max(0, x - omega A^T(A(x; c) - y)), differentiable in x0, y
+    """n steps of x <- max(0, x + omega A^T(y - A(x; c))), differentiable in x0, y
     and c; with ``checkpointing`` only the iterates are kept and each step is
     recomputed in backward."""
 
-    def __init__(self, plan, n_iter: int, omega: float, checkpointing: bool = True):
+    def __init__(self, plan, n_iter: int, omega: float, checkpointing: bool = True,
+                 nonneg: bool = True):
         super().__init__()
         self.plan = plan
         self.n_iter = int(n_iter)
         self.omega = float(omega)
         self.checkpointing = checkpointing
+        self.nonneg = bool(nonneg)
 
     def step(self, x, y, c):
-        r = ForwardOp.apply(x, c, self.plan) - y
-        return torch.relu(x - self.omega * AdjointOp.apply(r, c, self.plan))
+        return LandweberStep.apply(x, y, c, self.plan, self.omega, self.nonneg)
 
     def forward(self, x0, y, c):
         x = x0

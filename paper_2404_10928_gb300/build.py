@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpa.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["pa_plan.cu", "pa_ops.cu", "pa_recon.cu", "pa_static.cu", "pa_batch.cu", "pa_dense.cu",
-           "pa_freq.cu"]
+           "pa_freq.cu", "pa_frames.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

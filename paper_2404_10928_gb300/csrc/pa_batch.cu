@@ -21,7 +21,12 @@ struct pa_batch {
   std::vector<pa_plan*> plans;
   std::vector<float*> d_r;        // per-frame residual [S][K]
   BatchFrame* d_frames = nullptr;
-  int* d_pre = nullptr;           // [3][n + 1] item prefix sums
+  int* d_pre = nullptr;           // [4][n + 1] item prefix sums
+  // CGLS workspace per frame (allocated on the first CGLS call, for up to
+  // cgls_iter_cap iterations): one block per frame, carved below
+  std::vector<unsigned char*> d_cgls;
+  int cgls_iter_cap = -1;
+  int grid_cgls = 0;
   unsigned* d_state = nullptr;    // barrier + queues
   int* d_err = nullptr;
   double* d_omega = nullptr;      // [n]
@@ -29,6 +34,7 @@ struct pa_batch {
   int hist_cap = 0;
   int grid = 0;
   size_t smem = 0;
+  uint64_t wait_ns = kWaitLimitNs;  // limit of each grid-barrier wait
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<unsigned char> key;  // descriptor bytes + n_iter of the captured graph
@@ -48,10 +54,19 @@ struct Guard {
   }
 };
 
+// cudaMalloc, or the injected failure of pa_debug_fail_allocations
+template <typename T>
+cudaError_t batch_alloc(T** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
 void free_batch(pa_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (float* r : b->d_r) cudaFree(r);
+  for (unsigned char* w : b->d_cgls) cudaFree(w);
   void* ptrs[] = {b->d_frames, b->d_pre, b->d_state, b->d_err, b->d_omega, b->d_hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -82,7 +97,7 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
   Guard guard(b->device);
   // item counts per frame: forward (tile x sensor chunk), combine (sensor x
   // block of 4 kBatchThreads samples), adjoint (tile)
-  std::vector<int> pre(3 * (n_frames + 1), 0);
+  std::vector<int> pre(4 * (n_frames + 1), 0);
   int Lmax = 0, spc_max = 0;
   for (int f = 0; f < n_frames; ++f) {
     const pa_plan* p = plans[f];
@@ -91,6 +106,8 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
     pre[f + 1] = pre[f] + p->ntiles * chunks;
     pre[(n_frames + 1) + f + 1] = pre[(n_frames + 1) + f] + p->S * nk;
     pre[2 * (n_frames + 1) + f + 1] = pre[2 * (n_frames + 1) + f] + p->ntiles;
+    pre[3 * (n_frames + 1) + f + 1] =
+        pre[3 * (n_frames + 1) + f] + p->S * combine_kblocks(p->K, kBatchXrThreads, 4);
     Lmax = std::max(Lmax, p->L);
     spc_max = std::max(spc_max, p->fwd_spc);
   }
@@ -106,15 +123,27 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
     return st;
   }
   b->grid = per_sm * sms;
+  {
+    int per_sm_cgls = 0;
+    e = batch_cgls_config(b->dim, b->smem, &per_sm_cgls);
+    if (e != cudaSuccess || per_sm_cgls < 1) {
+      pa_status st = e != cudaSuccess ? cuda_fail(e, "batch CGLS occupancy", __FILE__, __LINE__)
+                                      : PA_ERR_UNSUPPORTED;
+      if (e == cudaSuccess) set_error("pa_batch_create: the batched CGLS kernel does not fit");
+      free_batch(b);
+      return st;
+    }
+    b->grid_cgls = per_sm_cgls * sms;
+  }
   e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_frames, n_frames * sizeof(BatchFrame));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_pre, pre.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_state, 8 * sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_omega, n_frames * sizeof(double));
+  if (e == cudaSuccess) e = batch_alloc(&b->d_frames, n_frames * sizeof(BatchFrame));
+  if (e == cudaSuccess) e = batch_alloc(&b->d_pre, pre.size() * sizeof(int));
+  if (e == cudaSuccess) e = batch_alloc(&b->d_state, 8 * sizeof(unsigned));
+  if (e == cudaSuccess) e = batch_alloc(&b->d_err, sizeof(int));
+  if (e == cudaSuccess) e = batch_alloc(&b->d_omega, n_frames * sizeof(double));
   for (int f = 0; f < n_frames && e == cudaSuccess; ++f) {
     float* r = nullptr;
-    e = cudaMalloc(&r, (size_t)plans[f]->S * plans[f]->K * sizeof(float));
+    e = batch_alloc(&r, (size_t)plans[f]->S * plans[f]->K * sizeof(float));
     b->d_r.push_back(r);
   }
   if (e == cudaSuccess)
@@ -137,6 +166,15 @@ pa_status pa_batch_destroy(pa_batch* batch) {
   return PA_OK;
 }
 
+pa_status pa_batch_set_wait_limit(pa_batch* b, double seconds) {
+  if (!b || !(seconds >= 0.0) || !(seconds <= 3600.0)) {
+    set_error("pa_batch_set_wait_limit: NULL batch or a limit outside [0, 3600] s");
+    return PA_ERR_INVALID_ARG;
+  }
+  b->wait_ns = (uint64_t)(seconds * 1e9);
+  return PA_OK;
+}
+
 pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
                              float* const* x_dev, const double* omega, int nonneg,
                              double* residual_history_host, pa_stream stream) {
@@ -156,8 +194,9 @@ pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
     PA_CUDA(cudaDeviceSynchronize());
     if (b->d_hist) cudaFree(b->d_hist);
     b->d_hist = nullptr;
+    b->hist_cap = 0;
+    PA_CUDA(batch_alloc(&b->d_hist, (size_t)n * (n_iter + 1) * sizeof(double)));
     b->hist_cap = n * (n_iter + 1);
-    PA_CUDA(cudaMalloc(&b->d_hist, b->hist_cap * sizeof(double)));
     b->key.clear();
   }
   std::vector<BatchFrame> frames(n);
@@ -173,10 +212,13 @@ pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
     F.hist = b->d_hist + (size_t)f * (n_iter + 1);
   }
   // the graph is valid while the descriptors, the steps and n_iter stay the same
-  std::vector<unsigned char> key(n * sizeof(BatchFrame) + n * sizeof(double) + sizeof(int));
-  std::memcpy(key.data(), frames.data(), n * sizeof(BatchFrame));
-  std::memcpy(key.data() + n * sizeof(BatchFrame), omega, n * sizeof(double));
-  std::memcpy(key.data() + n * sizeof(BatchFrame) + n * sizeof(double), &n_iter, sizeof(int));
+  std::vector<unsigned char> key(n * sizeof(BatchFrame) + n * sizeof(double) + sizeof(int) +
+                                 sizeof(uint64_t));
+  unsigned char* kp = key.data();
+  std::memcpy(kp, frames.data(), n * sizeof(BatchFrame));
+  std::memcpy(kp += n * sizeof(BatchFrame), omega, n * sizeof(double));
+  std::memcpy(kp += n * sizeof(double), &n_iter, sizeof(int));
+  std::memcpy(kp + sizeof(int), &b->wait_ns, sizeof(uint64_t));
   if (!b->exec || key != b->key) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
@@ -189,7 +231,7 @@ pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
     cudaError_t e = cudaMemsetAsync(b->d_state, 0, 8 * sizeof(unsigned), b->cap);
     if (e == cudaSuccess)
       e = launch_batch_landweber(b->dim, b->d_frames, n, b->d_pre, n_iter, b->d_state, b->d_err,
-                                 b->grid, b->smem, b->cap);
+                                 b->wait_ns, b->grid, b->smem, b->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {

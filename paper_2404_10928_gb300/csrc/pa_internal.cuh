@@ -58,6 +58,16 @@ enum : int {
 // sentinel for (tile, sensor) pairs whose taps all fall outside [0, K)
 constexpr int kSkip = INT_MIN;
 
+// largest gridDim.y of a launch: pixel tiles and sensors index it
+constexpr int kMaxGridY = 65535;
+
+// default limit of a bounded device-side wait (mbarrier, grid barrier)
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Test hook for allocation failures (pa_debug_fail_allocations): true when
+// the device allocation about to be made must fail as if out of memory.
+bool alloc_should_fail();
+
 // ---------------------------------------------------------------------------
 // per (pixel tile, sensor) time-of-flight reference, 32 bytes.
 //
@@ -78,7 +88,8 @@ struct __align__(16) TileRef {
   float ex2k;   // 2*kappa*(centre - sensor).x
   float ey2k;   // 2*kappa*(centre - sensor).y
   float ez2k;   // 2*kappa*(centre - sensor).z (0 in 2D)
-  float dlo;    // lower bound on |pixel - sensor| over the tile (>= half a pixel)
+  float dlo;    // forward tap scale: a lower bound on |pixel - sensor| over the tile
+                // (>= half a pixel) times the factor g of k_fwd_copies
 };
 // Low bit of klo: the sensor is much closer to some pixel than to the tile
 // centre, where d^2 = d_ref^2 + q/kappa cancels; such pairs form d^2 from the
@@ -112,7 +123,12 @@ struct GridF {
 enum ScalarOp : int { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_INVSQRT = 3, OP_STORE = 4 };
 
 // kernel modes
-enum AdjMode : int { ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3, ADJ_FISTA = 4 };
+// ADJ_AXPY: out = xin + coef g + tvw tvg (absent xin / tvg count as zero),
+// then max(0, .) if nonneg -- the Landweber update of frames sharing a plan and
+// the vector-Jacobian products of the differentiable forms
+enum AdjMode : int {
+  ADJ_STORE = 0, ADJ_LANDWEBER = 1, ADJ_NORM = 2, ADJ_DC = 3, ADJ_FISTA = 4, ADJ_AXPY = 5
+};
 enum FwdMode : int { FWD_STORE = 0, FWD_RESID = 1, FWD_NORM = 2 };
 
 // Cross-CTA FP64 reduction finished inside the producing kernel: every CTA
@@ -126,6 +142,7 @@ struct Reduce {
   const double* other;   // gamma for OP_ALPHA / OP_BETA
   double* out2;          // alpha / beta / 1/sqrt(sum)
   double post_scale;     // out_sum receives sum * post_scale (0 means 1)
+  int accumulate;        // 1: out_sum += instead of =
 };
 
 struct AdjParams {
@@ -146,8 +163,14 @@ struct AdjParams {
   // A^T r, r = y - A z, v = z + tau (2 g - tv_beta tvg), x_new = prox(v), and
   // z = x_new + mu (x_new - x_k), both in place
   float* z;
-  const float* tvg;       // gradient of TV_eps at z
+  const float* tvg;       // gradient of TV_eps at z (ADJ_FISTA), or the TV term (ADJ_AXPY)
   float l1, tv_beta, mu;
+  float coef, tvw;        // ADJ_AXPY weights of A^T p and of tvg
+  // frames of one launch (blockIdx.z), all on the plan's geometry: strides
+  // between consecutive frames (0 for a single frame)
+  int64_t fs_img;         // out, xin, z, tvg: N
+  int64_t fs_packed;      // packed: S * Kp
+  int fs_red;             // OP_STORE partial slots per frame
 };
 
 struct FwdParams {
@@ -180,6 +203,12 @@ struct FwdParams {
   double* beta;
   double* gamma_new;
   int* err;
+  // frames of one launch (blockIdx.z): strides between consecutive frames (0
+  // for a single frame; the CGLS direction update is single-frame only)
+  int64_t fs_img;         // x: N
+  int64_t fs_trace;       // out, y: S * K
+  int64_t fs_part;        // part: S * ntiles * L
+  int fs_red;             // OP_STORE partial slots per frame
 };
 
 // Scalars of the CGLS vector step: alpha = gamma / delta, gamma = ||s||^2 and
@@ -202,6 +231,20 @@ struct BatchFrame {
   int fwd_chunks;     // sensor chunks per tile in the forward gather
   int n_kblk;         // sample blocks per sensor in the combine
   double* hist;       // [n_iter + 1] ||r_n||^2
+  // CGLS (k_batch_cgls); unused by the Landweber launch
+  float* x;           // [N] image, in: x_0, out: the result
+  float* rbuf[2];     // residual ping-pong [S][K]
+  float* pbuf[2];     // direction ping-pong [N]
+  float* s;           // A^T r [N]
+  float* q;           // A p [S][K]
+  float2* q_parts;    // [S * n_kblk] partials of ||q||^2
+  float2* s_parts;    // [ntiles] partials of ||s||^2
+  float2* h_parts;    // [n_iter + 1][h_stride] partials of ||r_n||^2
+  int h_stride;
+  int n_xr;           // work items of the CGLS vector step
+  double* rec;        // [4][n_iter + 1]: gamma, delta, alpha, beta
+  int N;
+  int nonneg;         // clamp x >= 0 once after the iterations
 };
 
 // tile shapes
@@ -236,14 +279,16 @@ constexpr int kCombThreads = 256;            // samples per combine CTA
 cudaError_t launch_build_table(int dim, TileRef* table, int2* krange, const double* sensors_dev,
                                int S, const pa_grid& grid, const GridF& g, double kappa,
                                double t0fs, int K, int L, double hmin, int* err, cudaStream_t st);
-cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, const double* sensors_dev, int S,
-                              const pa_grid& grid, const GridF& g, double kappa, cudaStream_t st);
+cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, TileRef* table,
+                              const double* sensors_dev, int S, const pa_grid& grid, const GridF& g,
+                              double kappa, int L, cudaStream_t st);
 cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, int pad,
                         cudaStream_t st);
 cudaError_t launch_bp_filter(const float* p, float2* packed, int S, int K, int Kp, int pad,
                              float t0fs, cudaStream_t st);
-cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st);
-cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st);
+cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st,
+                           int frames = 1);
+cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st, int frames = 1);
 int adjoint_smem_bytes(int L);
 cudaError_t configure_kernels(int smem_adj, int smem_fwd);
 int forward_smem_bytes(int L, int spc);
@@ -268,6 +313,11 @@ cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st);
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st);
+cudaError_t launch_relu_mask(const float* g, const float* xout, float* gz, int64_t n, int nonneg,
+                             cudaStream_t st);
+cudaError_t launch_scale_by(float* v, const float* w, float f, int64_t n, cudaStream_t st);
+cudaError_t launch_affine_sum(const double* a, int n, const double* b, int m, double wb,
+                              double* out, cudaStream_t st);
 // *tau = 1 / (2 / *inv_lam + c_tv): the FISTA step from the power iteration
 cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
@@ -277,8 +327,14 @@ cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps
 int tv_blocks(int64_t n);
 cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm);
 cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_frames, const int* pre,
-                                   int n_iter, unsigned* state, int* err, int grid, size_t smem,
-                                   cudaStream_t st);
+                                   int n_iter, unsigned* state, int* err, uint64_t wait_ns,
+                                   int grid, size_t smem, cudaStream_t st);
+cudaError_t batch_cgls_config(int dim, size_t smem, int* blocks_per_sm);
+cudaError_t launch_batch_cgls(int dim, const BatchFrame* frames, int n_frames, const int* pre,
+                              int n_iter, unsigned* state, int* err, uint64_t wait_ns, int grid,
+                              size_t smem, cudaStream_t st);
+// threads of a CGLS vector-step work item inside the persistent launch
+constexpr int kBatchXrThreads = 256;
 
 }  // namespace pa
 
@@ -336,6 +392,17 @@ struct pa_plan {
   int scal_cap = 0;
   void* d_yhost = nullptr;    // device copies for pa_reconstruct_host
   float* d_xhost = nullptr;
+  // workspace of the multi-frame entry points (pa_*_frames), for up to
+  // frames_cap frames: windows, packed traces, partials, per-frame sums and
+  // the temporaries of the vector-Jacobian products
+  int frames_cap = 0;
+  float* d_part_f = nullptr;     // [F][S][ntiles][L]
+  float2* d_packed_f = nullptr;  // [F][S][Kp]
+  float2* d_parts_f = nullptr;   // [F][n_partials]
+  double* d_fsum = nullptr;      // [2F] per-frame sums
+  float* d_q_f = nullptr;        // [F][S][K]
+  float* d_r_f = nullptr;        // [F][S][K]
+  float* d_gz_f = nullptr;       // [F][N]
   int64_t bytes = 0;
 
   // graphs

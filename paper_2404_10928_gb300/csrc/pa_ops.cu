@@ -66,7 +66,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // A wait that gives up after ~2 s (or 2^30 polls) instead of spinning forever.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
+// (The grid barrier of the batched launch takes its limit as a launch argument,
+// kWaitLimitNs by default.)
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1; it < (1u << 30); ++it) {
@@ -152,6 +153,34 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (do
 __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
   return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
+// a / b in double-float (b.hi > 0): q1 = a.hi / b.hi, then one correction
+// step q2 = (a - q1 b) / b.hi, with q1 b.hi split exactly by an FMA and the
+// remainder's leading difference exact (q1 b.hi lies within a few ulps of
+// a.hi).  The quotient q1 + q2 carries ~44 significant bits: the CGLS step
+// lengths alpha and beta reach the update with the accuracy of an FP64
+// division, without FP64 instructions.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float ph = __fmul_rn(q1, b.hi);
+  const float pl = __fmaf_rn(q1, b.hi, -ph);
+  float r = __fsub_rn(a.hi, ph);
+  r = __fsub_rn(r, pl);
+  r = __fadd_rn(r, a.lo);
+  r = __fmaf_rn(-q1, b.lo, r);
+  const float q2 = __fdiv_rn(r, b.hi);
+  const float s = __fadd_rn(q1, q2);
+  return DF{s, __fsub_rn(q2, __fsub_rn(s, q1))};
+}
+// a double as a double-float pair (host-recorded scalars read back by a kernel)
+__device__ __forceinline__ DF df_from_double(double v) {
+  const float hi = (float)v;
+  return DF{hi, (float)(v - (double)hi)};
+}
+// y + a v with a double-float a: the low part enters first, so the result is
+// the FP32 rounding of y + a v up to the one rounding of the inner FMA.
+__device__ __forceinline__ float df_axpy(DF a, float v, float y) {
+  return __fmaf_rn(a.hi, v, __fmaf_rn(a.lo, v, y));
+}
 
 // Deterministic block sum: xor-tree within warps, warps in index order.
 // nw = warps in the block; s_red holds >= nw pairs; the result is valid in
@@ -200,7 +229,10 @@ __device__ __forceinline__ void reduce_across_ctas(const Reduce& R, DF part, int
   const DF tdf = block_sum(v, s_red, nw);
   if (threadIdx.x == 0) {
     const double t = df_to_double(tdf);
-    if (R.out_sum) *R.out_sum = R.post_scale != 0.0 ? t * R.post_scale : t;
+    if (R.out_sum) {
+      const double v = R.post_scale != 0.0 ? t * R.post_scale : t;
+      *R.out_sum = R.accumulate ? *R.out_sum + v : v;
+    }
     switch (R.op) {
       case OP_ALPHA:  // alpha = gamma / ||q||^2
         *R.out2 = t > 0.0 ? *R.other / t : 0.0;
@@ -617,8 +649,8 @@ __device__ __forceinline__ void adj_pair2(const TileRef2& r, uint32_t base, floa
 // (kTilePixels / (32 NW) pixels per thread, as packed pairs), warp NW produces;
 // any further warps of the block only take part in the barriers.
 template <int DIM, bool DC, int NW>
-__device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, int s_begin,
-                                                 int s_end, unsigned char* smem) {
+__device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float2* packed, int tile,
+                                                 int s_begin, int s_end, unsigned char* smem) {
   constexpr int PPT = kTilePixels / (32 * NW);
   constexpr int NPAIR = PPT / 2;
   static_assert(PPT % 2 == 0, "pixels are processed in pairs");
@@ -672,7 +704,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, int tile, i
           r = P.table[(int64_t)tile * P.S + s];
           if (r.klo != kSkip) {
             bytes = (uint32_t)L * (uint32_t)sizeof(float2);
-            src = P.packed + (int64_t)s * P.Kp + P.pad + window_start(r.klo);
+            src = packed + (int64_t)s * P.Kp + P.pad + window_start(r.klo);
           }
         }
         if (r.klo != kSkip) {
@@ -773,10 +805,14 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   const int rank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
   const int tile = blockIdx.y;
+  const int frame = blockIdx.z;
   const int tid = threadIdx.x;
   const int s_begin = rank * P.sensors_per_rank;
   const int s_end = min(P.S, s_begin + P.sensors_per_rank);
-  float* s_acc = adj_accumulate<DIM, DC, kAdjWarps>(P, tile, s_begin, s_end, smem);
+  float* s_acc = adj_accumulate<DIM, DC, kAdjWarps>(P, P.packed + frame * P.fs_packed, tile,
+                                                    s_begin, s_end, smem);
+  float* out = P.out ? P.out + frame * P.fs_img : nullptr;
+  const float* xin = P.xin ? P.xin + frame * P.fs_img : nullptr;
 
   cluster.sync();
   // --------------- cluster reduction in rank order + epilogue ---------------
@@ -800,11 +836,16 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
       const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
       const float gval = P.amp * v;
       if (DC) {
-        part = df_add(part, df_prod(P.xin[i], v));
+        part = df_add(part, df_prod(xin[i], v));
       } else if (P.mode == ADJ_LANDWEBER) {
-        float xv = fmaf((float)(*P.omega), gval, P.out[i]);
+        float xv = fmaf((float)(*P.omega), gval, out[i]);
         if (P.nonneg) xv = fmaxf(xv, 0.0f);
-        P.out[i] = xv;
+        out[i] = xv;
+      } else if (P.mode == ADJ_AXPY) {
+        float xv = fmaf(P.coef, gval, xin ? xin[i] : 0.0f);
+        if (P.tvg) xv = fmaf(P.tvw, P.tvg[frame * P.fs_img + i], xv);
+        if (P.nonneg) xv = fmaxf(xv, 0.0f);
+        out[i] = xv;
       } else if (P.mode == ADJ_FISTA) {
         // gradient step on ||A z - y||^2 + beta TV(z) at z, proximal step of
         // tau l1 ||.||_1 (and x >= 0), then the extrapolation
@@ -817,7 +858,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
         P.out[i] = xn;
         P.z[i] = fmaf(P.mu, xn - xo, xn);
       } else {
-        P.out[i] = gval;
+        out[i] = gval;
         part = df_add(part, df_sq(gval));
       }
     }
@@ -832,22 +873,25 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
       if (rank == 0 && tid == 0) {
         DF u = df_zero();
         for (int q = 0; q < C; ++q) u = df_add(u, *cluster.map_shared_rank(&s_cta, q));
-        P.red.partials[tile] = make_float2(u.hi, u.lo);
+        P.red.partials[frame * P.fs_red + tile] = make_float2(u.hi, u.lo);
       }
     } else {
-      reduce_across_ctas<kAdjWarps + 1>(P.red, t, tile * C + rank, gridDim.x * gridDim.y, s_red);
+      // one total over every frame of the launch
+      reduce_across_ctas<kAdjWarps + 1>(P.red, t, (frame * gridDim.y + tile) * C + rank,
+                                        gridDim.x * gridDim.y * gridDim.z, s_red);
     }
   }
   cluster.sync();
   (void)TZ;
 }
 
-cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st) {
+cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st,
+                           int frames) {
   const bool dc = p.mode == ADJ_DC;
   auto kernel = dim == 2 ? (dc ? k_adjoint<2, true> : k_adjoint<2, false>)
                          : (dc ? k_adjoint<3, true> : k_adjoint<3, false>);
-  return launch_k(kernel, dim3(cluster, ntiles, 1), dim3(kAdjThreads), adjoint_smem_bytes(p.L), st,
-                  cluster, p);
+  return launch_k(kernel, dim3(cluster, ntiles, frames), dim3(kAdjThreads), adjoint_smem_bytes(p.L),
+                  st, cluster, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -856,9 +900,10 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // A CTA owns one 1024-pixel tile and kFwdSPC sensors: four pixels per thread,
 // kept in registers with their offsets.  For each sensor, every pixel adds its
 // two taps x (1-f)/d and x f/d to the (tile, sensor) window of L samples in
-// shared memory.  The taps are added as fixed-point integers (scaled so that a
-// window sum cannot exceed 2^30): integer addition is associative, so the
-// shared-memory atomics give the same bits in any order.  Windows are written
+// shared memory.  The taps are added as fixed-point integers (scaled per (tile,
+// sensor) so that a window sum stays below 2^31, see k_fwd_copies): integer
+// addition is associative, so the shared-memory atomics give the same bits in
+// any order.  Windows are written
 // out (rescaled to float) once per stage of kFwdSB sensors.
 //
 // A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
@@ -882,24 +927,37 @@ int forward_smem_bytes(int L, int spc) {
          2 * kFwdSB * kFwdCopies * fwd_copy_stride(L) * (int)sizeof(int);
 }
 
-// Copy assignment of the forward windows.  One warp per (tile, sensor) pair;
-// lane r holds the sample bins of pixel row r (compute-order pixels 32 r ..
-// 32 r + 31: thread lane l of warp r % 8 deposits pixel 32 r + l), so every
-// warp atomic of the gather is one row.  Lanes l = 0..31 in turn take the copy
-// c whose bank (bin + c kFwdCopyRes) mod 32 minimises, summed over the 32
-// rows, the squared number of lanes already assigned to that bank (ties to
-// the lower copy).  Bins come from FP32 distances: an occasional bin off by
-// one costs at most a bank conflict.  Output: copies[tile * S + s], 2 bits per
-// lane.
+// Copy assignment and tap scale of the forward windows.  One warp per (tile,
+// sensor) pair; lane r holds the sample bins of pixel row r (compute-order
+// pixels 32 r .. 32 r + 31: thread lane l of warp r % 8 deposits pixel 32 r +
+// l), so every warp atomic of the gather is one row.
+//   Copies: lanes l = 0..31 in turn take the copy c whose bank (bin + c
+// kFwdCopyRes) mod 32 minimises, summed over the 32 rows, the squared number
+// of lanes already assigned to that bank (ties to the lower copy).  Bins come
+// from FP32 distances: an occasional bin off by one costs at most a bank
+// conflict.  Output: copies[tile * S + s], 2 bits per lane.
+//   Tap scale: a window sample receives one tap from every pixel whose arrival
+// u lies within one sample of it.  The warp counts, per sample, the pixels with
+// u within 1 + kTapSlack samples (the slack covers the FP32 distances here
+// against the gather's own arrival), and the largest count n bounds every
+// window sum at n times the largest tap.  The gather scales its taps to at
+// most 2^20 * g with g = 4, 2 or 1 (n <= 511, <= 1023, else): a window sum stays
+// below 2^31, and a tap below 2^22, the range the magic-number rounding takes
+// exactly.  g multiplies the table's d_lo, the forward's tap scale.
+constexpr float kTapSlack = 1.0e-2f;
+
 template <int DIM>
-__global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies,
+__global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies, TileRef* table,
                                                     const double* sensors, int S, int nx, int ny,
                                                     int nz, double dx, double dy, double dz,
                                                     double ox, double oy, double oz, int ntx,
-                                                    int nty, int ntz, float kappa) {
+                                                    int nty, int ntz, float kappa, int L) {
   __shared__ unsigned char s_load[8][32][33];  // per warp and row: lanes per bank
+  extern __shared__ int s_hist[];               // per warp: [L + 4] taps per sample
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nh = L + 4;
+  int* hist = s_hist + wib * nh;
   const int64_t total = (int64_t)ntx * nty * ntz * S;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned char* ld = s_load[wib][lane];
@@ -912,7 +970,9 @@ __global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies,
     const float cx = (float)(ox + tx * TX * dx - sensors[(int64_t)s * DIM]);
     const float cy = (float)(oy + ty * TY * dy - sensors[(int64_t)s * DIM + 1]);
     const float cz = DIM == 3 ? (float)(oz + tz * TZ * dz - sensors[(int64_t)s * DIM + 2]) : 0.0f;
+    float uf[32];
     int bins[32];
+    int bmin = INT_MAX;
 #pragma unroll
     for (int l = 0; l < 32; ++l) {
       int lx, ly, lz;
@@ -920,10 +980,34 @@ __global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies,
       const float ex = cx + (float)min(lx, nvx - 1) * (float)dx;
       const float ey = cy + (float)min(ly, nvy - 1) * (float)dy;
       const float ez = cz + (float)min(lz, nvz - 1) * (float)dz;
-      bins[l] = (int)floorf(kappa * sqrtf(ex * ex + ey * ey + ez * ez));
+      uf[l] = kappa * sqrtf(ex * ex + ey * ey + ez * ez);
+      bins[l] = (int)floorf(uf[l]);
+      bmin = min(bmin, (int)floorf(uf[l] - kTapSlack));
     }
 #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+    for (int j = lane; j < nh; j += 32) hist[j] = 0;
+#pragma unroll
     for (int b = 0; b < 32; ++b) ld[b] = 0;
+    __syncwarp();
+    int over = 0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int lo = (int)floorf(uf[l] - kTapSlack) - bmin;
+      const int hi = (int)floorf(uf[l] + kTapSlack) - bmin + 1;
+      for (int b = lo; b <= hi; ++b) {
+        if (b >= 0 && b < nh)
+          atomicAdd(&hist[b], 1);
+        else
+          over = 1;
+      }
+    }
+    __syncwarp();
+    int nmax = 0;
+    for (int j = lane; j < nh; j += 32) nmax = max(nmax, hist[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    if (__any_sync(0xffffffffu, over)) nmax = kTilePixels;  // unknown: the plain bound
     unsigned lo = 0, hi = 0;
 #pragma unroll
     for (int l = 0; l < 32; ++l) {
@@ -944,27 +1028,34 @@ __global__ void __launch_bounds__(256) k_fwd_copies(unsigned long long* copies,
       else
         hi |= (unsigned)best << (2 * (l - 16));
     }
-    if (lane == 0) copies[idx] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    if (lane == 0) {
+      copies[idx] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+      const float g = nmax <= 511 ? 4.0f : (nmax <= 1023 ? 2.0f : 1.0f);
+      table[idx].dlo *= g;  // table[tile * S + s], the layout of idx
+    }
     __syncwarp();
   }
 }
 
-cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, const double* sensors_dev, int S,
-                              const pa_grid& grid, const GridF& g, double kappa, cudaStream_t st) {
+cudaError_t launch_fwd_copies(int dim, unsigned long long* copies, TileRef* table,
+                              const double* sensors_dev, int S, const pa_grid& grid, const GridF& g,
+                              double kappa, int L, cudaStream_t st) {
   const int64_t warps = (int64_t)g.ntx * g.nty * g.ntz * S;
   const int blocks = (int)std::min<int64_t>((warps + 7) / 8, 65535);
   auto kernel = dim == 2 ? k_fwd_copies<2> : k_fwd_copies<3>;
-  return launch_k(kernel, dim3(blocks), dim3(256), 0, st, 0, copies, sensors_dev, S, grid.nx,
-                  grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.origin[0], grid.origin[1],
-                  grid.origin[2], g.ntx, g.nty, g.ntz, (float)kappa);
+  const size_t smem = (size_t)8 * (L + 4) * sizeof(int);
+  return launch_k(kernel, dim3(blocks), dim3(256), smem, st, 0, copies, table, sensors_dev, S,
+                  grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.origin[0],
+                  grid.origin[1], grid.origin[2], g.ntx, g.nty, g.ntz, (float)kappa, L);
 }
 
-constexpr float kFixedScale = 1048576.0f;  // 2^20: |tap| <= 2^20, window sums <= 1024 taps
+// 2^20: before the per-(tile, sensor) factor g (k_fwd_copies) |tap| <= 2^20
+constexpr float kFixedScale = 1048576.0f;
 
 // Deposits the two taps xs (1-f)/d and xs f/d of a pixel pair for one sensor
-// (xs_dlo: the pixel values in fixed-point units times d_lo, so every tap is at
-// most 2^20) into the sensor's centred window of int32 (`base`: its
-// magic_base).  Rounding: ws = xs d_lo / d and the first tap ws (1 - f) are
+// (xs_dlo: the pixel values in fixed-point units times the tap scale g d_lo, so
+// every tap is at most g 2^20 <= 2^22) into the sensor's centred window of int32
+// (`base`: its magic_base).  Rounding: ws = xs d_lo / d and the first tap ws (1 - f) are
 // each rounded to the nearest integer on the magic grid (W and a); the second
 // tap is W - a, so the taps of every pair sum exactly to its rounded weight.
 template <int DIM, bool NEAR>
@@ -992,7 +1083,7 @@ __device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, floa
 // threads of the block only help with the copies and barriers.
 template <int DIM, bool DIR>
 __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int chunk,
-                                               unsigned char* smem) {
+                                               unsigned char* smem, int frame = 0) {
   constexpr int PPT = kTilePixels / kFwdThreads;
   static_assert(PPT == 4, "two packed pixel pairs per thread");
   TileRef2* refs = reinterpret_cast<TileRef2*>(smem);
@@ -1042,9 +1133,9 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   // from the adjoint's per-tile partials
   float sv[PPT], pv[PPT];
   int64_t pix[PPT];
-  float beta = 0.0f;
+  DF beta = df_zero();
   if (DIR) {
-    __shared__ float s_beta;
+    __shared__ float s_beta, s_beta_lo;
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       int lx, ly, lz;
@@ -1058,12 +1149,14 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     if (warp == 0) {
       const DF t = warp_sum_partials(P.s_parts, P.n_s_parts);
       if (lane == 0) {
-        // the update runs in FP32, so beta is formed in FP32 from the leading
-        // parts (an FP64 division is a long chain on GB300's FP64 pipe); one
-        // CTA records the FP64 values
+        // beta = ||s||^2 / gamma_old in double-float (an FP64 division would
+        // be a long chain on GB300's FP64 pipe); one CTA records the FP64
+        // values
         const double g_old = *P.gamma_old;
-        const float gof = (float)g_old;
-        s_beta = gof > 0.0f ? __fdiv_rn(t.hi, gof) : 0.0f;
+        const DF go = df_from_double(g_old);
+        const DF b = go.hi > 0.0f ? df_div(t, go) : df_zero();
+        s_beta = b.hi;
+        s_beta_lo = b.lo;
         if (tile == 0 && chunk == 0) {
           const double g_new = df_to_double(t);
           *P.beta = g_old > 0.0 ? g_new / g_old : 0.0;
@@ -1072,7 +1165,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
       }
     }
     __syncthreads();
-    beta = s_beta;
+    beta = DF{s_beta, s_beta_lo};
   }
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
@@ -1081,11 +1174,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     float xv = 0.0f;
     if (DIR) {
       if (pix[m] >= 0) {
-        xv = fmaf(beta, pv[m], sv[m]);
+        xv = df_axpy(beta, pv[m], sv[m]);
         if (chunk == 0) P.p_new[pix[m]] = xv;
       }
     } else if (owner && lx < nvx && ly < nvy && lz < nvz) {
-      xv = P.x[((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)];
+      xv = P.x[frame * P.fs_img + ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx +
+               (tx * TX + lx)];
     }
     amax = fmaxf(amax, fabsf(xv));
     nonfinite |= !(fabsf(xv) <= 3.0e38f);
@@ -1147,11 +1241,11 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
       const int klo = refs[g0 + warp].klo;
       if (klo != kSkip) {
         const float u = !finite ? __int_as_float(0x7fc00000)
-                        : (xscale > 0.0f ? __fdividef(xmax, kFixedScale * refs[g0 + warp].dlo)
+                        : (xscale > 0.0f ? __fdiv_rn(xmax, kFixedScale * refs[g0 + warp].dlo)
                                          : 0.0f);
         int4* src = reinterpret_cast<int4*>(wb + warp * WS);
         float4* dst = reinterpret_cast<float4*>(
-            P.part + ((int64_t)(s0 + g0 + warp) * P.ntiles + tile) * L);
+            P.part + frame * P.fs_part + ((int64_t)(s0 + g0 + warp) * P.ntiles + tile) * L);
         for (int k4 = lane; k4 < L / 4; k4 += 32) {
           int4 v = make_int4(0, 0, 0, 0);
 #pragma unroll
@@ -1175,7 +1269,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
 template <int DIM, bool DIR>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  fwd_tile_block<DIM, DIR>(P, blockIdx.y, blockIdx.x, smem);
+  fwd_tile_block<DIM, DIR>(P, blockIdx.y, blockIdx.x, smem, blockIdx.z);
 }
 
 // One (sensor, block of SPT blockDim samples) work item of the combine: p[s,k]
@@ -1189,7 +1283,8 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
 // each sample (large 3D grids).  nkblk = sample blocks per sensor (for the
 // in-kernel reduction's slot numbering).
 template <int MODE, int SPT>
-__device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kblk, int nkblk) {
+__device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kblk, int nkblk,
+                                              int frame = 0) {
   static_assert(SPT == 1 || SPT == 4, "1 or 4 samples per thread");
   __shared__ DF s_red[32];
   const int k = SPT * (kblk * blockDim.x + threadIdx.x);
@@ -1198,7 +1293,7 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
     const int* up = P.upper + (int64_t)s * (P.K + P.L);
     const int i0 = up[k], i1 = up[k + P.L];  // windows starting in (k - L, k]
     const int2* srt = P.sorted + (int64_t)s * P.ntiles;
-    const float* ps = P.part + (int64_t)s * P.ntiles * P.L;
+    const float* ps = P.part + frame * P.fs_part + (int64_t)s * P.ntiles * P.L;
     float v[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) v[j] = 0.0f;
@@ -1223,7 +1318,7 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
       add(d);
     }
     for (; i < i1; ++i) add(srt[i]);
-    const int64_t o = (int64_t)s * P.K + k;
+    const int64_t o = frame * P.fs_trace + (int64_t)s * P.K + k;
     const int n = min(SPT, P.K - k);
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
@@ -1248,26 +1343,26 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
   }
   if (MODE != FWD_STORE) {
     const DF t = block_sum(part, s_red, blockDim.x >> 5);
-    reduce_across_ctas(P.red, t, s * nkblk + kblk, P.S * nkblk, s_red);
+    reduce_across_ctas(P.red, t, frame * P.fs_red + s * nkblk + kblk, P.S * nkblk, s_red);
   }
 }
 
 template <int MODE, int SPT>
 __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P) {
-  combine_block<MODE, SPT>(P, blockIdx.y, blockIdx.x, gridDim.x);
+  combine_block<MODE, SPT>(P, blockIdx.y, blockIdx.x, gridDim.x, blockIdx.z);
 }
 
 int forward_combine_blocks(int S, int K, int spt) { return S * combine_kblocks(K, kCombThreads, spt); }
 
-cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st) {
+cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st, int frames) {
   const int smem = forward_smem_bytes(p.L, p.spc);
-  dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, 1);
+  dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, frames);
   const bool dir = p.s_in != nullptr;
   auto tile_kernel = dim == 2 ? (dir ? k_fwd_tile<2, true> : k_fwd_tile<2, false>)
                               : (dir ? k_fwd_tile<3, true> : k_fwd_tile<3, false>);
   const cudaError_t e = launch_k(tile_kernel, grid1, dim3(kFwdThreads), smem, st, 0, p);
   if (e != cudaSuccess) return e;
-  const dim3 grid2(combine_kblocks(p.K, kCombThreads, p.comb_spt), p.S, 1);
+  const dim3 grid2(combine_kblocks(p.K, kCombThreads, p.comb_spt), p.S, frames);
   auto combine = p.comb_spt == 4
                      ? (p.mode == FWD_RESID ? k_fwd_combine<FWD_RESID, 4>
                         : p.mode == FWD_NORM ? k_fwd_combine<FWD_NORM, 4>
@@ -1316,20 +1411,22 @@ constexpr int kVecThreads = 128;
 
 // CGLS: alpha from the partials, then x += alpha p over this CTA's image
 // slice and r_out = r_in - alpha q for its samples (four consecutive samples
-// per thread, CTA b = s * kblocks + sample block), with the packed residual and
-// the double-float partial of ||r_out||^2 (one per CTA).
-__global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
-    float* x, const float* pv, const float* r_in,
-    float* r_out, const float* q, float2* packed,
-    const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red) {
-  __shared__ DF s_red[kVecThreads / 32];
-  __shared__ float s_alpha;
-  // CTA b owns samples 4 (j kVecThreads + thread) .. + 3 of sensor s (b = s kb + j)
-  // and the image slice [b chunk, (b + 1) chunk)
-  const int kb = combine_kblocks(K, kVecThreads, 4);
-  const int b = blockIdx.x, nb = gridDim.x;
+// per thread, work item b = s * kblocks + sample block of NT threads), with the
+// packed residual and the double-float partial of ||r_out||^2 (one per item).
+// Threads NT.. of a larger block only take part in the barriers.
+template <int NT>
+__device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const float* r_in,
+                                              float* r_out, const float* q, float2* packed,
+                                              const CglsAlpha& ca, int N, int S, int K, int Kp,
+                                              int pad, const Reduce& red, int b, int nb) {
+  __shared__ DF s_red[32];
+  __shared__ float s_alpha, s_alpha_lo;
+  __shared__ DF s_dg[2][32];
+  const int tid = threadIdx.x;
+  const bool worker = tid < NT;
+  const int kb = combine_kblocks(K, NT, 4);
   const int s = b / kb;
-  const int k = 4 * ((b - s * kb) * kVecThreads + (int)threadIdx.x);
+  const int k = 4 * ((b - s * kb) * NT + tid);
   const int64_t o = (int64_t)s * K + k;
   const int n = min(4, K - k);
   const int64_t chunk = ((int64_t)N + nb - 1) / nb;
@@ -1338,45 +1435,48 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
   // partials are loaded first (their chain is the longest), then this thread's
   // operands, and every warp takes a share of the partials, warps in order
   DF d = df_zero(), g = df_zero();
-  for (int i = threadIdx.x; i < ca.n_q_parts; i += kVecThreads) {
-    const float2 v = __ldcg(ca.q_parts + i);
-    d = df_add(d, DF{v.x, v.y});
-  }
-  for (int i = threadIdx.x; i < ca.n_s_parts; i += kVecThreads) {
-    const float2 v = __ldcg(ca.s_parts + i);
-    g = df_add(g, DF{v.x, v.y});
+  if (worker) {
+    for (int i = tid; i < ca.n_q_parts; i += NT) {
+      const float2 v = __ldcg(ca.q_parts + i);
+      d = df_add(d, DF{v.x, v.y});
+    }
+    for (int i = tid; i < ca.n_s_parts; i += NT) {
+      const float2 v = __ldcg(ca.s_parts + i);
+      g = df_add(g, DF{v.x, v.y});
+    }
   }
   float qv[5], rv[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {  // sample 4 = the next group's first (0 past the row)
-    const bool use = k < K && j <= n && k + j < K;
+    const bool use = worker && k < K && j <= n && k + j < K;
     qv[j] = use ? q[o + j] : 0.0f;
     rv[j] = use ? r_in[o + j] : 0.0f;
   }
-  const int64_t xi = x0 + threadIdx.x;
-  const float xv0 = xi < x1 ? x[xi] : 0.0f, pv0 = xi < x1 ? pv[xi] : 0.0f;
+  const int64_t xi = x0 + tid;
+  const bool xin = worker && xi < x1;
+  const float xv0 = xin ? x[xi] : 0.0f, pv0 = xin ? pv[xi] : 0.0f;
 #pragma unroll
   for (int sh = 16; sh > 0; sh >>= 1) {
     d = df_add(d, df_shfl_xor(d, sh));
     g = df_add(g, df_shfl_xor(g, sh));
   }
-  __shared__ DF s_dg[2][kVecThreads / 32];
-  if ((threadIdx.x & 31) == 0) {
-    s_dg[0][threadIdx.x >> 5] = d;
-    s_dg[1][threadIdx.x >> 5] = g;
+  if ((tid & 31) == 0 && worker) {
+    s_dg[0][tid >> 5] = d;
+    s_dg[1][tid >> 5] = g;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     d = df_zero();
     g = df_zero();
-    for (int w = 0; w < kVecThreads / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       d = df_add(d, s_dg[0][w]);
       g = df_add(g, s_dg[1][w]);
     }
-    // alpha in FP32 from the leading parts (the update runs in FP32); CTA 0
-    // records the FP64 values
-    s_alpha = d.hi > 0.0f ? __fdiv_rn(g.hi, d.hi) : 0.0f;
-    if (blockIdx.x == 0) {
+    // alpha = gamma / delta in double-float; item 0 records the FP64 values
+    const DF a = d.hi > 0.0f ? df_div(g, d) : df_zero();
+    s_alpha = a.hi;
+    s_alpha_lo = a.lo;
+    if (b == 0) {
       const double delta = df_to_double(d), gamma = df_to_double(g);
       *ca.alpha = delta > 0.0 ? gamma / delta : 0.0;
       *ca.gamma = gamma;
@@ -1384,15 +1484,17 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     }
   }
   __syncthreads();
-  const float alpha = s_alpha;
-  // x += alpha p over this CTA's image slice
-  if (xi < x1) x[xi] = fmaf(alpha, pv0, xv0);
-  for (int64_t i = xi + kVecThreads; i < x1; i += kVecThreads) x[i] = fmaf(alpha, pv[i], x[i]);
+  const DF alpha{s_alpha, s_alpha_lo};
+  const DF malpha{-s_alpha, -s_alpha_lo};
+  // x += alpha p over this item's image slice
+  if (xin) x[xi] = df_axpy(alpha, pv0, xv0);
+  if (worker)
+    for (int64_t i = xi + NT; i < x1; i += NT) x[i] = df_axpy(alpha, pv[i], x[i]);
   DF part = df_zero();
-  if (k < K) {
+  if (worker && k < K) {
     float rk[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) rk[j] = fmaf(-alpha, qv[j], rv[j]);
+    for (int j = 0; j < 5; ++j) rk[j] = df_axpy(malpha, qv[j], rv[j]);
     float2* row = packed + (int64_t)s * Kp + pad + k;
     if (n == 4 && (K & 3) == 0) {
       *reinterpret_cast<float4*>(r_out + o) = make_float4(rk[0], rk[1], rk[2], rk[3]);
@@ -1412,8 +1514,16 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     for (int j = 0; j < 4; ++j)
       if (j < n) part = df_add(part, df_sq(rk[j]));
   }
-  const DF t = block_sum<kVecThreads / 32>(part, s_red);
-  reduce_across_ctas<kVecThreads / 32>(red, t, b, nb, s_red);
+  const DF t = block_sum(part, s_red, blockDim.x >> 5);
+  reduce_across_ctas(red, t, b, nb, s_red);
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
+    float* x, const float* pv, const float* r_in,
+    float* r_out, const float* q, float2* packed,
+    const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red) {
+  cgls_xr_block<kVecThreads>(x, pv, r_in, r_out, q, packed, ca, N, S, K, Kp, pad, red, blockIdx.x,
+                             gridDim.x);
 }
 
 // number of r blocks of k_cgls_xr for S x K traces
@@ -1477,6 +1587,29 @@ __global__ void __launch_bounds__(kVecThreads) k_norm(const float* v, int64_t n,
   reduce_across_ctas<kVecThreads / 32>(red, t, blockIdx.x, gridDim.x, s_red);
 }
 
+// gz = g where xout > 0 (or everywhere when !nonneg), else 0: the derivative
+// of the projection max(0, .) applied to an incoming gradient
+__global__ void k_relu_mask(const float* g, const float* xout, float* gz, int64_t n, int nonneg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    gz[i] = (!nonneg || xout[i] > 0.0f) ? g[i] : 0.0f;
+}
+
+__global__ void k_scale_by(float* v, const float* w, float f, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * f;
+}
+
+// out = sum_i a[i] + wb sum_j b[j] (FP64; n, m small: one thread)
+__global__ void k_affine_sum(const double* a, int n, const double* b, int m, double wb,
+                             double* out) {
+  double sa = 0.0, sb = 0.0;
+  for (int i = 0; i < n; ++i) sa += a[i];
+  for (int j = 0; j < m; ++j) sb += b[j];
+  *out = sa + wb * sb;
+}
+
 static int vec_blocks(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecThreads - 1) / kVecThreads, 152 * 8));
 }
@@ -1487,6 +1620,18 @@ cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
 }
 cudaError_t launch_clamp(float* x, int N, cudaStream_t st) {
   return launch_k(k_clamp, dim3(vec_blocks(N)), dim3(kVecThreads), 0, st, 0, x, N);
+}
+cudaError_t launch_relu_mask(const float* g, const float* xout, float* gz, int64_t n, int nonneg,
+                             cudaStream_t st) {
+  return launch_k(k_relu_mask, dim3(vec_blocks(n)), dim3(kVecThreads), 0, st, 0, g, xout, gz, n,
+                  nonneg);
+}
+cudaError_t launch_scale_by(float* v, const float* w, float f, int64_t n, cudaStream_t st) {
+  return launch_k(k_scale_by, dim3(vec_blocks(n)), dim3(kVecThreads), 0, st, 0, v, w, f, n);
+}
+cudaError_t launch_affine_sum(const double* a, int n, const double* b, int m, double wb,
+                              double* out, cudaStream_t st) {
+  return launch_k(k_affine_sum, dim3(1), dim3(1), 0, st, 0, a, n, b, m, wb, out);
 }
 cudaError_t launch_set_scalar(double* dst, double value, cudaStream_t st) {
   return launch_k(k_set_scalar, dim3(1), dim3(1), 0, st, 0, dst, value);
@@ -1591,7 +1736,7 @@ cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps
 // [4] adjoint queue.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void grid_barrier(unsigned* st, unsigned nblocks, int* err,
-                                             unsigned* queue_to_reset) {
+                                             unsigned* queue_to_reset, uint64_t wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = st + 1;
@@ -1603,13 +1748,14 @@ __device__ __forceinline__ void grid_barrier(unsigned* st, unsigned nblocks, int
       __threadfence();
       atomicAdd(st + 1, 1u);
     } else {
-      // bounded: after kWaitLimitNs, or as soon as an earlier wait of the launch
-      // has given up (ERR_WAIT_TIMEOUT latched), stop waiting
+      // bounded: after wait_ns, or as soon as an earlier wait of the launch
+      // has given up (ERR_WAIT_TIMEOUT latched), stop waiting; the clock is
+      // read at the first poll and then every 256 polls
       const uint64_t t0 = global_ns();
       for (uint32_t it = 1; *gen == g; ++it) {
-        if ((it & 255u) == 0u) {
+        if ((it & 255u) == 1u) {
           if (*(volatile int*)err & ERR_WAIT_TIMEOUT) break;
-          if (global_ns() - t0 > kWaitLimitNs) {
+          if (global_ns() - t0 > wait_ns) {
             atomicOr(err, ERR_WAIT_TIMEOUT);
             break;
           }
@@ -1643,7 +1789,7 @@ template <int DIM>
 __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile,
                                                     unsigned char* smem) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
-  float* s_acc = adj_accumulate<DIM, false, kBatchAdjWarps>(P, tile, 0, P.S, smem);
+  float* s_acc = adj_accumulate<DIM, false, kBatchAdjWarps>(P, P.packed, tile, 0, P.S, smem);
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
   const float om = (float)(*P.omega);
   for (int p = threadIdx.x; p < kTilePixels; p += blockDim.x) {
@@ -1663,7 +1809,7 @@ __device__ __forceinline__ void adj_landweber_block(const AdjParams& P, int tile
 template <int DIM>
 __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
     const BatchFrame* __restrict__ frames, int nf, const int* __restrict__ pre, int n_iter,
-    unsigned* state, int* err) {
+    unsigned* state, int* err, uint64_t wait_ns) {
   extern __shared__ __align__(128) unsigned char smem[];
   const unsigned nb = gridDim.x;
   const int* pf = pre;                 // forward items
@@ -1676,7 +1822,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
       const int chunks = frames[f].fwd_chunks;
       fwd_tile_block<DIM, false>(frames[f].f, li / chunks, li % chunks, smem);
     }
-    grid_barrier(state, nb, err, state + 2);
+    grid_barrier(state, nb, err, state + 2, wait_ns);
     for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
       const int f = frame_of(pc, nf, gi);
       const int li = gi - pc[f];
@@ -1685,7 +1831,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
       const int nk = frames[f].n_kblk;
       combine_block<FWD_RESID, 4>(P, li / nk, li % nk, nk);
     }
-    grid_barrier(state, nb, err, state + 3);
+    grid_barrier(state, nb, err, state + 3, wait_ns);
     if (it == n_iter) break;
     for (int f = 0; f < nf; ++f) {  // pack r of every frame (grid-stride)
       const FwdParams& F = frames[f].f;
@@ -1702,13 +1848,199 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
             make_float2(0.5f * (a + b), b - a);
       }
     }
-    grid_barrier(state, nb, err, nullptr);
+    grid_barrier(state, nb, err, nullptr, wait_ns);
     for (int gi = grab_item(state + 4); gi < pa[nf]; gi = grab_item(state + 4)) {
       const int f = frame_of(pa, nf, gi);
       adj_landweber_block<DIM>(frames[f].a, gi - pa[f], smem);
     }
-    grid_barrier(state, nb, err, state + 4);
+    grid_barrier(state, nb, err, state + 4, wait_ns);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batched CGLS over frames of uneven size, in one persistent cooperative
+// launch: the phases of pa_reconstruct's CGLS (setup: r = y - A x, s = A^T r,
+// p = s; per iteration: A p with the direction update fused, the vector step
+// with alpha, A^T r), each drawing the work items of all frames from one
+// queue and separated by bounded grid barriers.  Every item runs the device
+// function of the single-frame kernel, so a frame's result is bitwise that of
+// pa_reconstruct with adj_cluster = 1.  Queues: state[2] forward, [3]
+// combine, [4] adjoint, [5] vector step, [6] history sums.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void adj_norm_block(const AdjParams& P, int tile, float* s_out,
+                                               float2* s_parts, unsigned char* smem) {
+  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
+  __shared__ DF s_red[32];
+  float* s_acc = adj_accumulate<DIM, false, kBatchAdjWarps>(P, P.packed, tile, 0, P.S, smem);
+  const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
+  DF part = df_zero();
+  for (int p = threadIdx.x; p < kTilePixels; p += blockDim.x) {
+    int lx, ly, lz;
+    pixel_rowmajor<DIM>(p, lx, ly, lz);
+    const int gx = tx * TX + lx, gy = ty * TY + ly, gz = tz * TZ + lz;
+    if (gx < P.g.nx && gy < P.g.ny && gz < P.g.nz) {
+      const int64_t i = ((int64_t)gz * P.g.ny + gy) * P.g.nx + gx;
+      const float gval = P.amp * s_acc[p];
+      s_out[i] = gval;
+      part = df_add(part, df_sq(gval));
+    }
+  }
+  const DF t = block_sum(part, s_red, blockDim.x >> 5);
+  if (threadIdx.x == 0) s_parts[tile] = make_float2(t.hi, t.lo);
+  __syncthreads();
+}
+
+__device__ __forceinline__ Reduce stored_parts(float2* parts) {
+  Reduce r{};
+  r.op = OP_STORE;
+  r.partials = parts;
+  return r;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch_cgls(
+    const BatchFrame* frames, int nf, const int* pre, int n_iter, unsigned* state, int* err,
+    uint64_t wait_ns) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const unsigned nb = gridDim.x;
+  const int* pf = pre;                 // forward items
+  const int* pc = pre + (nf + 1);      // combine items
+  const int* pa = pre + 2 * (nf + 1);  // adjoint items
+  const int* px = pre + 3 * (nf + 1);  // vector-step items
+  const int nrec = n_iter + 1;
+  // ---- setup: r_0 = y - A x_0 (||r_0||^2 -> history row 0), s = A^T r_0 -> p
+  for (int gi = grab_item(state + 2); gi < pf[nf]; gi = grab_item(state + 2)) {
+    const int f = frame_of(pf, nf, gi), li = gi - pf[f];
+    FwdParams P = frames[f].f;
+    P.x = frames[f].x;
+    fwd_tile_block<DIM, false>(P, li / frames[f].fwd_chunks, li % frames[f].fwd_chunks, smem);
+  }
+  grid_barrier(state, nb, err, state + 2, wait_ns);
+  for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
+    const int f = frame_of(pc, nf, gi), li = gi - pc[f];
+    FwdParams P = frames[f].f;
+    P.out = frames[f].rbuf[0];
+    P.red = stored_parts(frames[f].h_parts);
+    const int nk = frames[f].n_kblk;
+    combine_block<FWD_RESID, 4>(P, li / nk, li % nk, nk);
+  }
+  grid_barrier(state, nb, err, state + 3, wait_ns);
+  for (int f = 0; f < nf; ++f) {  // pack r_0 of every frame (grid-stride)
+    const FwdParams& F = frames[f].f;
+    const AdjParams& A = frames[f].a;
+    const float* rs0 = frames[f].rbuf[0];
+    const int64_t row = F.K + 1, total = (int64_t)F.S * row;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      const int s = (int)(idx / row);
+      const int k = (int)(idx % row) - 1;
+      const float* rs = rs0 + (int64_t)s * F.K;
+      const float a = (k >= 0) ? rs[k] : 0.0f;
+      const float b = (k + 1 < F.K) ? rs[k + 1] : 0.0f;
+      const_cast<float2*>(A.packed)[(int64_t)s * A.Kp + A.pad + k] = make_float2(0.5f * (a + b), b - a);
+    }
+  }
+  grid_barrier(state, nb, err, nullptr, wait_ns);
+  for (int gi = grab_item(state + 4); gi < pa[nf]; gi = grab_item(state + 4)) {
+    const int f = frame_of(pa, nf, gi);
+    adj_norm_block<DIM>(frames[f].a, gi - pa[f], frames[f].pbuf[0], frames[f].s_parts, smem);
+  }
+  grid_barrier(state, nb, err, state + 4, wait_ns);
+  for (int it = 0; it < n_iter; ++it) {
+    const int cur = it & 1, prv = cur ^ 1;
+    // q = A p, p = s + beta p_old fused from the second iteration on
+    for (int gi = grab_item(state + 2); gi < pf[nf]; gi = grab_item(state + 2)) {
+      const int f = frame_of(pf, nf, gi), li = gi - pf[f];
+      const BatchFrame& B = frames[f];
+      FwdParams P = B.f;
+      const int tile = li / B.fwd_chunks, chunk = li % B.fwd_chunks;
+      if (it == 0) {
+        P.x = B.pbuf[0];
+        fwd_tile_block<DIM, false>(P, tile, chunk, smem);
+      } else {
+        P.x = nullptr;
+        P.s_in = B.s;
+        P.p_old = B.pbuf[prv];
+        P.p_new = B.pbuf[cur];
+        P.s_parts = B.s_parts;
+        P.n_s_parts = B.f.ntiles;
+        P.gamma_old = B.rec + (it - 1);
+        P.beta = B.rec + 3 * nrec + (it - 1);
+        P.gamma_new = B.rec + it;
+        fwd_tile_block<DIM, true>(P, tile, chunk, smem);
+      }
+    }
+    grid_barrier(state, nb, err, state + 2, wait_ns);
+    for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
+      const int f = frame_of(pc, nf, gi), li = gi - pc[f];
+      FwdParams P = frames[f].f;
+      P.out = frames[f].q;
+      P.red = stored_parts(frames[f].q_parts);
+      const int nk = frames[f].n_kblk;
+      combine_block<FWD_NORM, 4>(P, li / nk, li % nk, nk);
+    }
+    grid_barrier(state, nb, err, state + 3, wait_ns);
+    // alpha = gamma / ||q||^2; x += alpha p; r -= alpha q (packed)
+    for (int gi = grab_item(state + 5); gi < px[nf]; gi = grab_item(state + 5)) {
+      const int f = frame_of(px, nf, gi), li = gi - px[f];
+      const BatchFrame& B = frames[f];
+      CglsAlpha ca;
+      ca.q_parts = B.q_parts;
+      ca.n_q_parts = B.f.S * B.n_kblk;
+      ca.s_parts = B.s_parts;
+      ca.n_s_parts = B.f.ntiles;
+      ca.alpha = B.rec + 2 * nrec + it;
+      ca.gamma = B.rec + it;
+      ca.delta = B.rec + nrec + it;
+      cgls_xr_block<kBatchXrThreads>(B.x, B.pbuf[cur], B.rbuf[cur], B.rbuf[prv], B.q,
+                                     const_cast<float2*>(B.a.packed), ca, B.N, B.f.S, B.f.K,
+                                     B.a.Kp, B.a.pad,
+                                     stored_parts(B.h_parts + (int64_t)(it + 1) * B.h_stride), li,
+                                     B.n_xr);
+    }
+    grid_barrier(state, nb, err, state + 5, wait_ns);
+    // s = A^T r (||s||^2 per tile)
+    for (int gi = grab_item(state + 4); gi < pa[nf]; gi = grab_item(state + 4)) {
+      const int f = frame_of(pa, nf, gi);
+      adj_norm_block<DIM>(frames[f].a, gi - pa[f], frames[f].s, frames[f].s_parts, smem);
+    }
+    grid_barrier(state, nb, err, state + 4, wait_ns);
+  }
+  // residual history (one item per frame and row), then the final clamp
+  __shared__ DF s_red[32];
+  const int rows = n_iter + 1;
+  for (int gi = grab_item(state + 6); gi < nf * rows; gi = grab_item(state + 6)) {
+    const BatchFrame& B = frames[gi / rows];
+    const int row = gi % rows;
+    const DF t = sum_partials(B.h_parts + (int64_t)row * B.h_stride,
+                              row == 0 ? B.f.S * B.n_kblk : B.n_xr, s_red);
+    if (threadIdx.x == 0) B.hist[row] = df_to_double(t);
+  }
+  for (int f = 0; f < nf; ++f) {
+    if (!frames[f].nonneg) continue;
+    float* x = frames[f].x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < frames[f].N;
+         i += (int64_t)gridDim.x * blockDim.x)
+      x[i] = fmaxf(x[i], 0.0f);
+  }
+}
+
+cudaError_t batch_cgls_config(int dim, size_t smem, int* blocks_per_sm) {
+  auto kernel = dim == 2 ? k_batch_cgls<2> : k_batch_cgls<3>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kBatchThreads, smem);
+}
+
+cudaError_t launch_batch_cgls(int dim, const BatchFrame* frames, int n_frames, const int* pre,
+                              int n_iter, unsigned* state, int* err, uint64_t wait_ns, int grid,
+                              size_t smem, cudaStream_t st) {
+  void* args[] = {(void*)&frames, (void*)&n_frames, (void*)&pre, (void*)&n_iter, (void*)&state,
+                  (void*)&err, (void*)&wait_ns};
+  const void* kernel = dim == 2 ? (const void*)k_batch_cgls<2> : (const void*)k_batch_cgls<3>;
+  return cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBatchThreads), args, smem, st);
 }
 
 cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm) {
@@ -1728,10 +2060,10 @@ cudaError_t batch_kernel_config(int dim, size_t smem, int* blocks_per_sm) {
 }
 
 cudaError_t launch_batch_landweber(int dim, const BatchFrame* frames, int n_frames, const int* pre,
-                                   int n_iter, unsigned* state, int* err, int grid, size_t smem,
-                                   cudaStream_t st) {
+                                   int n_iter, unsigned* state, int* err, uint64_t wait_ns,
+                                   int grid, size_t smem, cudaStream_t st) {
   void* args[] = {(void*)&frames, (void*)&n_frames, (void*)&pre, (void*)&n_iter, (void*)&state,
-                  (void*)&err};
+                  (void*)&err, (void*)&wait_ns};
   if (dim == 2)
     return cudaLaunchCooperativeKernel((const void*)k_batch_landweber<2>, dim3(grid),
                                        dim3(kBatchThreads), args, smem, st);

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 #include "pa_internal.cuh"
@@ -26,10 +27,27 @@ pa_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
 }
 
 
+// Allocation-failure injection (pa_debug_fail_allocations): the number of
+// device allocations still allowed to succeed, or -1 for no injection.
+static std::atomic<long long> g_allocs_left{-1};
+
+bool alloc_should_fail() {
+  long long left = g_allocs_left.load();
+  while (left >= 0) {
+    if (left == 0) return true;
+    if (g_allocs_left.compare_exchange_weak(left, left - 1)) return false;
+  }
+  return false;
+}
+
 template <typename T>
 static pa_status dev_alloc(pa_plan* p, T** ptr, size_t count) {
   *ptr = nullptr;
   if (count == 0) count = 1;
+  if (alloc_should_fail()) {
+    set_error("cudaMalloc of %zu bytes failed: out of memory (injected)", count * sizeof(T));
+    return PA_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -54,8 +72,8 @@ static pa_status build_table(pa_plan* p) {
   PA_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->cap_stream));
   PA_CUDA(launch_build_table(p->dim, p->d_table, p->d_krange, p->d_sensors, p->S, p->grid, p->g,
                              kappa, p->t0 * p->fs, p->K, p->L, hmin, p->d_err, p->cap_stream));
-  PA_CUDA(launch_fwd_copies(p->dim, p->d_fwd_copies, p->d_sensors, p->S, p->grid, p->g, kappa,
-                            p->cap_stream));
+  PA_CUDA(launch_fwd_copies(p->dim, p->d_fwd_copies, p->d_table, p->d_sensors, p->S, p->grid,
+                            p->g, kappa, p->L, p->cap_stream));
   int err = 0;
   PA_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->cap_stream));
   PA_CUDA(cudaStreamSynchronize(p->cap_stream));
@@ -129,7 +147,9 @@ static void free_plan(pa_plan* p) {
                   p->d_dense_part, p->d_dense_cnt, p->d_freq,
                   p->d_ra,      p->d_rb,    p->d_q,      p->d_pv,     p->d_pb,  p->d_sv,
                   p->d_scal,    p->d_counter,
-                  p->d_yhost,   p->d_xhost};
+                  p->d_yhost,   p->d_xhost,
+                  p->d_part_f,  p->d_packed_f, p->d_parts_f, p->d_fsum, p->d_q_f, p->d_r_f,
+                  p->d_gz_f};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -175,6 +195,15 @@ using namespace pa;
 extern "C" {
 
 int pa_version(void) { return PA_VERSION; }
+
+pa_status pa_debug_fail_allocations(long long after) {
+  if (after < -1) {
+    set_error("pa_debug_fail_allocations: after must be >= -1");
+    return PA_ERR_INVALID_ARG;
+  }
+  g_allocs_left.store(after);
+  return PA_OK;
+}
 
 const char* pa_last_error(void) { return g_last_error; }
 
@@ -301,6 +330,17 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   p->g.hdx = (float)(0.5 * p->grid.dx);
   p->g.hdy = (float)(0.5 * p->grid.dy);
   p->g.hdz = (float)(0.5 * p->grid.dz);
+  {
+    // tiles and sensors index the second grid dimension of the gather,
+    // combine and packing launches, which CUDA caps at 65535
+    const int64_t nt = (int64_t)p->g.ntx * p->g.nty * p->g.ntz;
+    if (nt > kMaxGridY || p->S > kMaxGridY) {
+      set_error("grid of %lld pixel tiles (%d x %d x %d pixels each) and %d sensors: both must be "
+                "at most %d", (long long)nt, TX, TY, TZ, p->S, kMaxGridY);
+      delete p;
+      return PA_ERR_UNSUPPORTED;
+    }
+  }
   p->ntiles = p->g.ntx * p->g.nty * p->g.ntz;
   {
     const double kappa = fs / c;
@@ -538,6 +578,7 @@ Reduce make_reduce(const pa_plan* p, int op, double* out_sum, const double* othe
   r.other = other;
   r.out2 = out2;
   r.post_scale = 0.0;
+  r.accumulate = 0;
   return r;
 }
 

@@ -57,6 +57,10 @@ void drop_graphs(pa_plan* p) {
 template <typename T>
 pa_status alloc_once(pa_plan* p, T** ptr, size_t count) {
   if (*ptr) return PA_OK;
+  if (alloc_should_fail()) {
+    set_error("cudaMalloc of %zu bytes failed: out of memory (injected)", count * sizeof(T));
+    return PA_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -450,6 +454,44 @@ pa_status pa_reconstruct_host(pa_plan* plan, pa_method method, int n_iter, const
   PA_CUDA(cudaMemcpyAsync(x_host, plan->d_xhost, N * sizeof(float), cudaMemcpyDeviceToHost, st));
   PA_CUDA(cudaStreamSynchronize(st));
   return PA_OK;
+}
+
+pa_status pa_plan_time_gathers(pa_plan* plan, int reps, const float* x_dev, const float* p_dev,
+                               double* fwd_ms, double* adj_ms, pa_stream stream) {
+  if (!plan || reps < 1 || !x_dev || !p_dev || !fwd_ms || !adj_ms) {
+    set_error("pa_plan_time_gathers: NULL argument or reps < 1");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  PA_TRY(ensure_workspace(plan, 0));
+  cudaStream_t st = (cudaStream_t)stream;
+  Timing none;
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) PA_CUDA(cudaEventCreate(&ev[i]));
+  pa_status s = PA_OK;
+  auto run = [&]() -> pa_status {
+    PA_CUDA(launch_pack(p_dev, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad, st));
+    // one warm-up of each, then the two timed runs
+    PA_TRY(fwd(plan, x_dev, plan->d_q, FWD_NORM, nullptr, stored(plan->d_parts_q), none, st));
+    PA_TRY(adj(plan, plan->d_sv, ADJ_NORM, nullptr, 0, stored(plan->d_parts_s), none, st));
+    PA_CUDA(cudaEventRecord(ev[0], st));
+    for (int i = 0; i < reps; ++i)
+      PA_TRY(fwd(plan, x_dev, plan->d_q, FWD_NORM, nullptr, stored(plan->d_parts_q), none, st));
+    PA_CUDA(cudaEventRecord(ev[1], st));
+    for (int i = 0; i < reps; ++i)
+      PA_TRY(adj(plan, plan->d_sv, ADJ_NORM, nullptr, 0, stored(plan->d_parts_s), none, st));
+    PA_CUDA(cudaEventRecord(ev[2], st));
+    PA_CUDA(cudaEventSynchronize(ev[2]));
+    float a = 0.f, b = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    PA_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    *fwd_ms = a / reps;
+    *adj_ms = b / reps;
+    return PA_OK;
+  };
+  s = run();
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  return s;
 }
 
 pa_status pa_plan_kernel_times(pa_plan* plan, double* fwd_ms, int* n_fwd, double* adj_ms,

@@ -9,8 +9,8 @@
 // whose memory budget is fixed at start-up.  They pass their inputs and outputs
 // and get the adjoint without any cudaMalloc/cudaFree.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "pa_internal.cuh"
 
@@ -21,28 +21,18 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device; the first call on
-// a device asks the runtime for it (cudaGetSymbolAddress), later calls reuse it.
-pa_status scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("pa_adjoint_static: device ordinal %d out of range", dev);
-    return PA_ERR_UNSUPPORTED;
+// Device address of the scratch array on the current device.  Every call asks
+// the runtime (cudaGetSymbolAddress is a lookup in the loaded module, not an
+// allocation), so the address stays right after a cudaDeviceReset has
+// re-created the device's context and reloaded the module.
+pa_status scratch_address(unsigned char** out) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+  if (e != cudaSuccess || ptr == nullptr) {
+    if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
+    return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess || ptr == nullptr) {
-      if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
-      return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
-    }
-    g_scratch_addr[dev] = ptr;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(ptr);
   return PA_OK;
 }
 
@@ -68,8 +58,16 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   }
   const double t0 = opts ? opts->t0 : 0.0;
   const double amp = (opts && opts->amp_scale != 0.0) ? opts->amp_scale : 1.0;
-  if (!std::isfinite(t0) || !std::isfinite(amp)) {
-    set_error("pa_adjoint_static: invalid options");
+  // the options are validated as pa_plan_create validates them; adj_cluster is
+  // honoured, y_dtype and fwd_sensors_per_cta concern entry points this one
+  // does not run
+  if (!std::isfinite(t0) || !std::isfinite(amp) ||
+      (opts && ((opts->y_dtype != PA_F32 && opts->y_dtype != PA_F16) || opts->adj_cluster < 0 ||
+                opts->adj_cluster > 8 || (opts->adj_cluster & (opts->adj_cluster - 1)) != 0 ||
+                opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256))) {
+    set_error("pa_adjoint_static: invalid options (adj_cluster must be 0, 1, 2, 4 or 8, "
+              "fwd_sensors_per_cta in [0, 256], y_dtype PA_F32 or PA_F16, t0 and amp_scale "
+              "finite)");
     return PA_ERR_INVALID_ARG;
   }
   const int dim = grid->dim;
@@ -121,6 +119,11 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   g.hdy = (float)(0.5 * gr.dy);
   g.hdz = (float)(0.5 * gr.dz);
   const int64_t ntiles = (int64_t)g.ntx * g.nty * g.ntz;
+  if (ntiles > kMaxGridY || n_sensors > kMaxGridY) {
+    set_error("pa_adjoint_static: %lld pixel tiles and %d sensors: both must be at most %d",
+              (long long)ntiles, n_sensors, kMaxGridY);
+    return PA_ERR_UNSUPPORTED;
+  }
   const double kappa = fs / c;
   const double ex = (TX - 1) * gr.dx, ey = (TY - 1) * gr.dy, ez = dim == 3 ? (TZ - 1) * gr.dz : 0.0;
   const int L = ((int)std::ceil(kappa * std::sqrt(ex * ex + ey * ey + ez * ez)) + 8 + 15) / 16 * 16;
@@ -137,6 +140,7 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
   int C = 1;
   while (C < 8 && ntiles * C < 2LL * sms && 2 * C <= n_sensors) C *= 2;
+  if (opts && opts->adj_cluster > 0) C = std::min(opts->adj_cluster, n_sensors);
 
   // scratch layout: flag | sensors | reference table | tap ranges | packed traces
   const size_t off_err = 0;
@@ -151,7 +155,7 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
     return PA_ERR_UNSUPPORTED;
   }
   unsigned char* base = nullptr;
-  PA_TRY(scratch_address(dev, &base));
+  PA_TRY(scratch_address(&base));
   int* d_err = reinterpret_cast<int*>(base + off_err);
   double* d_sens = reinterpret_cast<double*>(base + off_sens);
   TileRef* d_tab = reinterpret_cast<TileRef*>(base + off_tab);

@@ -121,6 +121,9 @@ def test_argument_validation_without_gpu(lib):
     assert lib.pa_forward(None, None, None, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_adjoint(None, None, None, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_reconstruct(None, 0, 1, None, None, None, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_batch_set_wait_limit(None, 1.0) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_debug_fail_allocations(-2) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_debug_fail_allocations(-1) == _lib.PA_OK
     assert lib.pa_status_string(_lib.PA_ERR_TIMEOUT) == b"device wait timed out"
     assert lib.pa_version() == 1
 

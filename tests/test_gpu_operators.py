@@ -87,18 +87,27 @@ def test_linearity_and_zero(torch_cuda):
 @pytest.mark.parametrize("factory", ["ring_vessels", "planar_vessel_tree"])
 def test_full_size_operators(torch_cuda, factory):
     """The benchmark workloads at full size (2D 256^2 x 256 sensors x 2048 samples;
-    3D 128^3 x 1024 sensors x 1024 samples) in the launch configuration the
-    benchmark uses."""
+    3D 128^3 x 1024 sensors x 1024 samples), with the plan defaults and with
+    every work decomposition the autotuner can pick for the benchmark (adjoint
+    clusters change the order of the final per-pixel sum, forward chunks the
+    windows' grouping)."""
     torch = torch_cuda
+    from paper_2404_10928_gb300.api import Plan
+    from paper_2404_10928_gb300.autotune import candidates
     prob = getattr(ph, factory)()
     geo = orc.Geometry.of(prob)
     x, y = _inputs(prob, seed=3)
-    with _plan(prob) as plan:
-        p_gpu = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
-        g_gpu = plan.adjoint(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
-        plan.sync_status()
-    assert rel_l2(p_gpu, orc.forward(geo, x)) <= OP_TOL
-    assert rel_l2(g_gpu, orc.adjoint(geo, y)) <= OP_TOL
+    p_ref, g_ref = orc.forward(geo, x), orc.adjoint(geo, y)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    shapes = [(0, 0)] + list(candidates(prob.n_sensors))
+    for c, spc in shapes:
+        with Plan.from_problem(prob, adj_cluster=c, fwd_sensors_per_cta=spc) as plan:
+            p_gpu = plan.forward(xt).cpu().numpy()
+            g_gpu = plan.adjoint(yt).cpu().numpy()
+            plan.sync_status()
+        assert rel_l2(p_gpu, p_ref) <= OP_TOL, (c, spc, rel_l2(p_gpu, p_ref))
+        assert rel_l2(g_gpu, g_ref) <= OP_TOL, (c, spc, rel_l2(g_gpu, g_ref))
 
 
 def test_sound_speed_change(torch_cuda):

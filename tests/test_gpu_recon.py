@@ -5,7 +5,8 @@ import pytest
 from oracle import oracle as orc
 from paper_2404_10928_gb300 import phantoms as ph
 
-from helpers import OP_TOL, RECON_TOL, f32, rel_l2
+from helpers import (CGLS_ENSEMBLE, CGLS_ENVELOPE_FACTOR, OP_TOL, RECON_TOL, cgls_spread,
+                     cgls_with_iterates, f32, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -91,29 +92,33 @@ def test_cgls_ring_vessels_early(torch_cuda, vessels):
     np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL)
 
 
-# Past ~8 iterations CGLS on this workload amplifies 1e-8-level perturbations to
-# the 1e-3 level: the FP64 oracle itself, with only its iteration vectors
-# rounded to FP32, departs from exact FP64 CGLS by 1.7e-3 (20 iterations) and
-# 2.2e-3 (50 iterations); with operator errors of 3e-6 (the FP32 operators'
-# level) the departure reaches 2.8e-2 in 3D.  The full-length runs are therefore
-# checked against that envelope, not against 1e-4.
-CGLS_X_ENVELOPE = 2e-2
-CGLS_HIST_ENVELOPE = 2e-3
-
-
 def test_cgls_ring_vessels_full(torch_cuda, vessels):
-    """50 CGLS iterations on the full 256^2 ring workload with 1% noise."""
+    """CGLS on the full 256^2 ring workload with 1% noise, at 10, 20 and 50
+    iterations.  Past the semi-convergence knee FP32-level perturbations move
+    CGLS by 1e-3 and more (tests/test_cgls_sensitivity.py), so x and the
+    residual history are held to CGLS_ENVELOPE_FACTOR times the spread of the
+    perturbed oracle ensemble (helpers.cgls_spread), computed here on the same
+    frame."""
     torch = torch_cuda
     prob, geo, y = vessels
-    x_ref, h_ref = orc.cgls(geo, y, 50)
+    ref, href = cgls_with_iterates(orc, geo, y, 50)
+    dx, dh, _ = cgls_spread(orc, geo, y, 50, ref, href)
     with _plan(prob) as plan:
-        x, h = plan.reconstruct(_dev(torch, y), "cgls", 50, history=True)
-        x = x.cpu().numpy()
-    assert rel_l2(x, x_ref) <= CGLS_X_ENVELOPE, rel_l2(x, x_ref)
-    assert np.max(np.abs(h - h_ref)) <= CGLS_HIST_ENVELOPE * h_ref[0]
-    assert np.all(np.diff(h) <= 1e-7 * h[0])
+        yd = _dev(torch, y)
+        for n in (10, 20, 50):
+            x, h = plan.reconstruct(yd, "cgls", n, nonneg=False, history=True)
+            x = x.cpu().numpy()
+            e = rel_l2(x, ref[n - 1])
+            assert e <= CGLS_ENVELOPE_FACTOR * dx[n - 1], (n, e, dx[n - 1])
+            eh = np.max(np.abs(h - href[:n + 1])) / href[0]
+            assert eh <= CGLS_ENVELOPE_FACTOR * dh[:n + 1].max(), (n, eh, dh[:n + 1].max())
+            assert np.all(np.diff(h) <= 1e-7 * h[0])
+        # the benchmark's setting: the same 50 iterations, clamped once at the end
+        xc = plan.reconstruct(yd, "cgls", 50).cpu().numpy()
+    assert np.array_equal(xc, np.maximum(x, 0.0).astype(np.float32))
     # same reconstruction quality against the phantom
-    e_gpu, e_ref = rel_l2(x, prob.x_true), rel_l2(x_ref, prob.x_true)
+    x_ref = np.maximum(ref[-1], 0.0)
+    e_gpu, e_ref = rel_l2(xc, prob.x_true), rel_l2(x_ref, prob.x_true)
     assert abs(e_gpu - e_ref) <= 0.02 * e_ref, (e_gpu, e_ref)
 
 
@@ -163,23 +168,50 @@ def test_f16_measurements(torch_cuda, disks):
 
 def test_cgls_3d_small(torch_cuda):
     """3D planar-array vessel tree at 32^3 (the 128^3 workload's geometry, scaled):
-    5 CGLS iterations at 1e-4; 30 iterations within the rounding envelope."""
+    5 CGLS iterations at 1e-4; 30 iterations within the perturbed-oracle envelope."""
     torch = torch_cuda
     prob = ph.planar_vessel_tree(n=32)
     geo = orc.Geometry.of(prob)
     y = f32(orc.forward(geo, prob.x_true))
-    x5, h5 = orc.cgls(geo, y, 5)
-    x30, h30 = orc.cgls(geo, y, 30)
+    ref, href = cgls_with_iterates(orc, geo, y, 30)
+    dx, dh, _ = cgls_spread(orc, geo, y, 30, ref, href)
     with _plan(prob) as plan:
-        g5, gh5 = plan.reconstruct(_dev(torch, y), "cgls", 5, history=True)
-        g30, gh30 = plan.reconstruct(_dev(torch, y), "cgls", 30, history=True)
-    assert rel_l2(g5.cpu().numpy(), x5) <= RECON_TOL
-    np.testing.assert_allclose(gh5, h5, rtol=RECON_TOL)
+        g5, gh5 = plan.reconstruct(_dev(torch, y), "cgls", 5, nonneg=False, history=True)
+        g30, gh30 = plan.reconstruct(_dev(torch, y), "cgls", 30, nonneg=False, history=True)
+    assert rel_l2(g5.cpu().numpy(), ref[4]) <= RECON_TOL
+    np.testing.assert_allclose(gh5, href[:6], rtol=RECON_TOL)
     g30 = g30.cpu().numpy()
-    assert rel_l2(g30, x30) <= 5e-2
-    assert np.max(np.abs(gh30 - h30)) <= 5e-3 * h30[0]
+    assert rel_l2(g30, ref[29]) <= CGLS_ENVELOPE_FACTOR * dx[29], (rel_l2(g30, ref[29]), dx[29])
+    assert np.max(np.abs(gh30 - href)) / href[0] <= CGLS_ENVELOPE_FACTOR * dh.max()
     assert np.all(np.diff(gh30) <= 1e-7 * gh30[0])
-    assert rel_l2(g30, prob.x_true) <= 2.0 * rel_l2(x30, prob.x_true)
+    assert rel_l2(g30, prob.x_true) <= 2.0 * rel_l2(ref[29], prob.x_true)
+
+
+def test_cgls_planar_128_full_size(torch_cuda):
+    """The 3D workload at full size: 128^3 voxels at 0.2 mm, 32x32 planar array,
+    1024 samples, 30 CGLS iterations (2.15 G pixel-sensor pairs per operator
+    application).  5 iterations at 1e-4; after 30, x within the envelope of an
+    oracle run whose operator outputs carry noise at the operator tolerance, and
+    the objective ||r_30||^2 within CGLS_ENVELOPE_FACTOR times that run's (FP32
+    CGLS on this noise-free problem converges more slowly than FP64)."""
+    torch = torch_cuda
+    prob = ph.planar_vessel_tree()
+    geo = orc.Geometry.of(prob)
+    y = f32(orc.forward(geo, prob.x_true))
+    ref, href = cgls_with_iterates(orc, geo, y, 30)
+    member = CGLS_ENSEMBLE[1]  # operator outputs perturbed at OP_TOL
+    its, hist = cgls_with_iterates(orc, geo, y, 30, **member)
+    with _plan(prob) as plan:
+        yd = _dev(torch, y)
+        g5 = plan.reconstruct(yd, "cgls", 5, nonneg=False).cpu().numpy()
+        g30, gh30 = plan.reconstruct(yd, "cgls", 30, nonneg=False, history=True)
+    g30 = g30.cpu().numpy()
+    assert rel_l2(g5, ref[4]) <= RECON_TOL, rel_l2(g5, ref[4])
+    spread = rel_l2(its[29], ref[29])
+    assert rel_l2(g30, ref[29]) <= CGLS_ENVELOPE_FACTOR * spread, (rel_l2(g30, ref[29]), spread)
+    assert gh30[-1] <= CGLS_ENVELOPE_FACTOR * max(hist[-1], href[-1]), (gh30[-1], hist[-1],
+                                                                         href[-1])
+    assert np.all(np.diff(gh30) <= 1e-7 * gh30[0])
 
 
 @pytest.mark.parametrize("alpha_rel,beta_rel,nonneg", [(0.02, 0.0, True), (0.02, 0.05, True),
