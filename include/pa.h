@@ -436,6 +436,25 @@ pa_status pa_batch_landweber(pa_batch *batch, int n_iter, const void *const *y_d
                              float *const *x_dev, const double *omega, int nonneg,
                              double *residual_history_host, pa_stream stream);
 
+/* Batched reconstruction by `method`: PA_LANDWEBER is pa_batch_landweber
+ * (omega required); PA_CGLS runs n_iter CGLS iterations on every frame (the
+ * recursion of pa_reconstruct's PA_CGLS: unconstrained, then one clamp
+ * x >= 0 when nonneg; omega unused, may be NULL) in ONE persistent cooperative
+ * launch: its setup and each iteration's four phases (A p with the direction
+ * update, the window combine with ||A p||^2, the vector step with alpha, A^T r
+ * with ||A^T r||^2) draw the work items of all frames from shared queues,
+ * separated by bounded grid barriers, captured as a CUDA graph and replayed
+ * while the buffers, n_iter and method are unchanged.  Every work item runs
+ * the single-frame kernels' device code; only the grouping of the per-item
+ * norm partials differs from pa_reconstruct, so results agree to rounding.
+ * The first CGLS call allocates a workspace per frame (3 [S][K] and 3 [N]
+ * float32 buffers, partials and scalar records).  PA_FISTA returns
+ * PA_ERR_UNSUPPORTED.  Other arguments as pa_batch_landweber. */
+pa_status pa_batch_reconstruct(pa_batch *batch, pa_method method, int n_iter,
+                               const void *const *y_dev, float *const *x_dev,
+                               const double *omega, int nonneg, double *residual_history_host,
+                               pa_stream stream);
+
 /* Limit of every grid-barrier wait inside the batch's persistent launch, in
  * seconds (default 2; 0 <= seconds <= 3600).  A wait that runs past it gives
  * up: the launch finishes without blocking the GPU, its results are invalid,

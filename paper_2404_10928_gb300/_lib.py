@@ -90,6 +90,8 @@ SIGNATURES = {
     "pa_batch_landweber": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), _DP, c_int, _DP, _STREAM]),
     "pa_batch_set_wait_limit": (c_int, [c_void_p, c_double]),
+    "pa_batch_reconstruct": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_void_p),
+                                     ctypes.POINTER(c_void_p), _DP, c_int, _DP, _STREAM]),
     "pa_debug_fail_allocations": (c_int, [ctypes.c_longlong]),
     "pa_tv": (c_int, [_P, c_void_p, c_double, c_void_p, c_void_p, _STREAM]),
     "pa_forward_frames": (c_int, [_P, c_int, c_void_p, c_void_p, _STREAM]),

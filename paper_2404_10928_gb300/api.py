@@ -511,6 +511,28 @@ class Batch:
         """Limit of each grid-barrier wait of the persistent launch (seconds)."""
         check(self._lib.pa_batch_set_wait_limit(self._h, float(seconds)), "pa_batch_set_wait_limit")
 
+    def reconstruct(self, ys, xs, method: str = "cgls", n_iter: int = 50, omegas=None,
+                    nonneg: bool = True, history: bool = False):
+        """Run n_iter iterations of `method` ("landweber" or "cgls") on every frame
+        in one persistent launch (xs: start images, receive the results)."""
+        n = len(self.plans)
+        if not (len(ys) == len(xs) == n) or (omegas is not None and len(omegas) != n):
+            raise ValueError("need one y and x (and omega) per frame")
+        for p, y, x in zip(self.plans, ys, xs):
+            ydt = torch.float16 if p.y_dtype == "f16" else torch.float32
+            p._check_tensor(y, p.n_sensors * p.n_samples, "y", ydt)
+            p._check_tensor(x, p.n_pixels, "x")
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        om = (ctypes.c_double * n)(*[float(o) for o in omegas]) if omegas is not None else None
+        hist = np.zeros((n, n_iter + 1)) if history else None
+        hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if history else None
+        check(self._lib.pa_batch_reconstruct(self._h, METHODS[method], int(n_iter), yp, xp, om,
+                                             int(bool(nonneg)), hp,
+                                             _stream_handle(self.plans[0].device)),
+              "pa_batch_reconstruct")
+        return hist
+
     def landweber(self, ys, xs, omegas, n_iter: int, nonneg: bool = True, history: bool = False):
         """Run n_iter projected Landweber steps on every frame in place (xs are the
         start images and receive the results)."""

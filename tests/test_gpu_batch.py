@@ -93,3 +93,76 @@ def test_batch_time_series_sample(torch_cuda):
     finally:
         for p in plans:
             p.close()
+
+
+def test_batch_cgls_matches_single_frame_and_oracle(torch_cuda):
+    """Batched CGLS (one persistent launch for all frames and iterations) on
+    four ragged frames: 5 iterations within RECON_TOL of the oracle and of the
+    single-frame path; 20 iterations within the perturbed-oracle envelope of
+    each frame (past the knee FP32-level perturbations move CGLS by >1e-3);
+    the clamp, the residual history and a graph replay."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300.api import Batch, Plan
+    from helpers import CGLS_ENVELOPE_FACTOR, cgls_spread, cgls_with_iterates
+    frames = _ragged_frames()
+    ys = [f32(orc.forward(orc.Geometry.of(p), p.x_true)) for p in frames]
+    plans = [Plan.from_problem(p, adj_cluster=1) for p in frames]
+    try:
+        yd = [torch.tensor(y, dtype=torch.float32, device="cuda") for y in ys]
+        zeros = lambda: [torch.zeros(p.n_pixels, dtype=torch.float32, device="cuda")
+                         for p in frames]
+        with Batch(plans) as batch:
+            x5 = zeros()
+            h5 = batch.reconstruct(yd, x5, "cgls", 5, nonneg=False, history=True)
+            x20 = zeros()
+            h20 = batch.reconstruct(yd, x20, "cgls", 20, nonneg=False, history=True)
+            x20b = zeros()
+            batch.reconstruct(yd, x20b, "cgls", 20, nonneg=False)  # graph replay
+            x20c = zeros()
+            batch.reconstruct(yd, x20c, "cgls", 20, nonneg=True)
+        for f, (prob, plan) in enumerate(zip(frames, plans)):
+            geo = orc.Geometry.of(prob)
+            ref, href = cgls_with_iterates(orc, geo, ys[f], 20)
+            single = plan.reconstruct(yd[f], "cgls", 5, nonneg=False).cpu().numpy()
+            got5 = x5[f].cpu().numpy()
+            assert rel_l2(got5, ref[4]) <= RECON_TOL, (f, rel_l2(got5, ref[4]))
+            assert rel_l2(got5, single) <= RECON_TOL, (f, rel_l2(got5, single))
+            np.testing.assert_allclose(h5[f], href[:6], rtol=RECON_TOL, atol=RECON_TOL * href[0])
+            dx, dh, _ = cgls_spread(orc, geo, ys[f], 20, ref, href)
+            got20 = x20[f].cpu().numpy()
+            e = rel_l2(got20, ref[19])
+            assert e <= max(CGLS_ENVELOPE_FACTOR * dx[19], RECON_TOL), (f, e, dx[19])
+            assert np.max(np.abs(h20[f] - href)) / href[0] <= max(CGLS_ENVELOPE_FACTOR * dh.max(),
+                                                                 RECON_TOL)
+            assert np.all(np.diff(h20[f]) <= 1e-7 * h20[f][0])
+            assert torch.equal(x20[f], x20b[f])
+            assert np.array_equal(x20c[f].cpu().numpy(), np.maximum(got20, 0.0))
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_batch_cgls_3d_and_fista_rejected(torch_cuda):
+    torch = torch_cuda
+    from paper_2404_10928_gb300 import _lib
+    from paper_2404_10928_gb300.api import Batch, Plan
+    frames = [ph.custom(3, (20, 17, 12), (2e-4, 2e-4, 2e-4), ph.planar_array(6, 5, 0.8e-3, 3.5e-3),
+                        200, seed=81),
+              ph.custom(3, (33, 9, 17), (1.5e-4, 2e-4, 1e-4), ph.planar_array(4, 7, 0.6e-3, -3e-3),
+                        151, seed=82)]
+    ys = [f32(orc.forward(orc.Geometry.of(p), p.x_true)) for p in frames]
+    plans = [Plan.from_problem(p, adj_cluster=1) for p in frames]
+    try:
+        yd = [torch.tensor(y, dtype=torch.float32, device="cuda") for y in ys]
+        xs = [torch.zeros(p.n_pixels, dtype=torch.float32, device="cuda") for p in frames]
+        with Batch(plans) as batch:
+            batch.reconstruct(yd, xs, "cgls", 5)
+            with pytest.raises(_lib.PAError) as exc:
+                batch.reconstruct(yd, xs, "fista", 5)
+            assert exc.value.status == _lib.PA_ERR_UNSUPPORTED
+        for f, prob in enumerate(frames):
+            ref, _ = orc.cgls(orc.Geometry.of(prob), ys[f], 5)
+            assert rel_l2(xs[f].cpu().numpy(), ref) <= RECON_TOL
+    finally:
+        for p in plans:
+            p.close()
