@@ -20,7 +20,7 @@ region (``--no-extras`` skips them): ``bp_vs_ir`` (back-projection against
 CGLS and FISTA), ``batched`` (64 ragged frames, persistent launch against the
 per-frame loop), ``differentiable`` (loss and gradients in x and c),
 ``volume3d`` (the 128^3 planar workload), ``dense_paper_size`` (the 6144 x 16384
-matrix) and ``frequency_domain``.  ``--profile-case 2d|3d|dense|freq|batch|dc``
+matrix) and ``frequency_domain``.  ``--profile-case 2d|3d|dense|freq|batch|dc|cgls``
 runs only a small fixed workload for ncu captures.
 """
 from __future__ import annotations
@@ -327,20 +327,40 @@ def bench_batched(torch, tuner, n_iter: int = 20, reps: int = 3) -> dict:
             x.zero_()
         batch.landweber(ys, xs, omegas, n_iter)
 
+    def plain_cgls():
+        for plan, y, x in zip(plans, ys, xs):
+            x.zero_()
+            plan.reconstruct(y, "cgls", n_iter, out=x)
+
+    def batched_cgls():
+        for x in xs:
+            x.zero_()
+        batch.reconstruct(ys, xs, "cgls", n_iter)
+
     plain()
     batched()
     t_plain = _events_time(torch, plain, reps)
     t_batch = _events_time(torch, batched, reps)
+    plain_cgls()
+    batched_cgls()
+    t_plain_c = _events_time(torch, plain_cgls, reps)
+    t_batch_c = _events_time(torch, batched_cgls, reps)
     batch.close()
     for p in plans:
         p.close()
+    pairs_c = sum(p.pairs for p in frames) * (2 + 2 * n_iter)
     return {"workload": f"{len(frames)} ragged frames (grids 128^2..512^2, 128-512 ring sensors, "
-                        f"1024-4096 samples, FP16 y), {n_iter} projected Landweber iterations",
+                        f"1024-4096 samples, FP16 y), {n_iter} projected Landweber iterations; "
+                        f"the same frames by {n_iter} CGLS iterations",
             "frames_per_s_batched": len(frames) / t_batch,
             "frames_per_s_plain": len(frames) / t_plain,
             "speedup": t_plain / t_batch,
             "pairs_per_s_batched": pairs / t_batch,
             "launches_batched": 2, "launches_plain": len(frames),
+            "cgls": {"frames_per_s_batched": len(frames) / t_batch_c,
+                     "frames_per_s_plain": len(frames) / t_plain_c,
+                     "speedup": t_plain_c / t_batch_c,
+                     "pairs_per_s_batched": pairs_c / t_batch_c},
             "timing": f"median of {reps}, CUDA events"}
 
 
@@ -379,7 +399,9 @@ def bench_differentiable(torch, reps: int = 3) -> dict:
     t_un = _events_time(torch, unrolled, reps)
     plan.close()
     apps_lg = len(frames) * 3           # A; backward A^T and d/dc, per frame
-    apps_un = len(frames) * 10 * 8      # per step: A, A^T; recomputed A, A^T; backward A^T, A, 2 d/dc
+    # per step and frame: A, A^T; recomputed in backward A, A^T; the step's vector-Jacobian
+    # product A, A^T, A (residual) and two d/dc gathers
+    apps_un = len(frames) * 10 * 9
     return {"workload": "batch of 8 vessel frames, 256^2, 128-sensor ring, 2048 samples, c=1500",
             "loss_grad_ms": t_lg * 1e3, "loss_grad_frames_per_s": len(frames) / t_lg,
             "unrolled10_grad_ms": t_un * 1e3,
@@ -524,8 +546,7 @@ def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
     from paper_2404_10928_gb300.api import Plan
     prob = ph.planar_vessel_tree()
     t = tuner.best(prob)
-    plan = Plan.from_problem(prob, adj_cluster=t["adj_cluster"],
-                             fwd_sensors_per_cta=t["fwd_sensors_per_cta"])
+    plan = Plan.from_problem(prob, **tuner.plan_options(t))
     x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
     y = plan.forward(x_true)
     # operator timings on a dense image (an all-zero tile skips its work, so the
@@ -550,8 +571,7 @@ def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
     return {"workload": "3D 128^3 at 0.2 mm, 32x32 planar array 0.8 mm pitch 5 mm from the "
                         "volume, 1024 samples, vessel tree",
             "pairs_per_application": pairs,
-            "autotuned": {"adj_cluster": t["adj_cluster"],
-                          "fwd_sensors_per_cta": t["fwd_sensors_per_cta"]},
+            "autotuned": tuner.plan_options(t),
             "forward_ms": t_f * 1e3, "adjoint_ms": t_a * 1e3,
             "forward_pairs_per_s": pairs / t_f, "adjoint_pairs_per_s": pairs / t_a,
             "adjoint_frac_fp32": pairs * FLOPS_PER_PAIR / t_a / 1e12 / peak_tflops,
@@ -581,8 +601,7 @@ def run_gpu(args):
     from paper_2404_10928_gb300.autotune import Autotuner
     tuner = Autotuner()  # cache: PA_TUNE_CACHE, else ~/.cache/pa_gb300/autotune.json
     tuned = tuner.best(prob)
-    plan = Plan.from_problem(prob, adj_cluster=tuned["adj_cluster"],
-                             fwd_sensors_per_cta=tuned["fwd_sensors_per_cta"])
+    plan = Plan.from_problem(prob, **tuner.plan_options(tuned))
     x_true = torch.tensor(prob.x_true, dtype=torch.float32, device=dev)
     clean = plan.forward(x_true).cpu().numpy().astype(np.float64)
     y_host = ph.add_noise(clean, noise, prob.noise_level).astype(np.float32)
@@ -730,8 +749,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(y_host.nbytes + prob.n_pixels * 4),
                     "d2h_bytes_per_step": int(prob.n_pixels * 4)},
-            "autotuned": {"adj_cluster": tuned["adj_cluster"],
-                          "fwd_sensors_per_cta": tuned["fwd_sensors_per_cta"]},
+            "autotuned": tuner.plan_options(tuned),
             "gpu_launches": cgls_launches(N_ITER) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
@@ -754,13 +772,30 @@ def run_profile_case(kind: str) -> int:
     each.  "batch": the first 16 frames of the ragged time series (FP16 y) as
     one persistent batched launch of 4 projected Landweber iterations, twice.
     "dc": on the 64^3 planar plan, the speed-of-sound derivative and the
-    smoothed TV with its gradient, three times each.  Prints nothing."""
+    smoothed TV with its gradient, three times each.  "cgls": the benchmark step
+    itself (256x256 ring, 50 CGLS iterations) three times.  Prints nothing."""
     import torch
 
     from paper_2404_10928_gb300 import phantoms as ph
     from paper_2404_10928_gb300.api import Batch, Plan
 
     torch.cuda.set_device(0)
+    if kind == "cgls":
+        # the benchmark step: the 256^2 ring frame, the autotuned decomposition
+        # (8-CTA adjoint clusters, 16 sensors per forward work item), one warm-up
+        # reconstruction (graph capture) and two timed-shape reconstructions of 50
+        # CGLS iterations: 4 + 4 x 50 + 2 = 206 launches each
+        prob = ph.ring_vessels()
+        with Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=16) as plan:
+            x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
+            y = plan.forward(x_true)
+            x = torch.zeros(prob.n_pixels, dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                x.zero_()
+                plan.reconstruct(y, "cgls", N_ITER, out=x)
+            torch.cuda.synchronize()
+            plan.sync_status()
+        return 0
     if kind == "dc":
         prob = ph.planar_vessel_tree(n=64)
         with Plan.from_problem(prob, adj_cluster=2) as plan:
@@ -845,7 +880,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
-    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch", "dc"],
+    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch", "dc", "cgls"],
                     help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
     if args.profile_case:

@@ -31,8 +31,10 @@ def _pow2(n: int) -> int:
     return p
 
 
-def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int) -> str:
-    return f"{gpu}|{dim}d|N{_pow2(n_pixels)}|S{_pow2(n_sensors)}|K{_pow2(n_samples)}"
+def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int,
+             y_dtype: str = "f32") -> str:
+    return (f"{gpu}|{dim}d|N{_pow2(n_pixels)}|S{_pow2(n_sensors)}|K{_pow2(n_samples)}|"
+            f"y{y_dtype}")
 
 
 def candidates(n_sensors: int) -> Iterable[Tuple[int, int]]:
@@ -78,7 +80,14 @@ class Autotuner:
         return self._gpu
 
     def key(self, prob) -> str:
-        return size_key(self.gpu, prob.dim, prob.n_pixels, prob.n_sensors, prob.n_samples)
+        return size_key(self.gpu, prob.dim, prob.n_pixels, prob.n_sensors, prob.n_samples,
+                        prob.extra.get("y_dtype", "f32"))
+
+    @staticmethod
+    def plan_options(entry: dict) -> dict:
+        """The plan keyword arguments of a tuning entry."""
+        return {"adj_cluster": entry["adj_cluster"],
+                "fwd_sensors_per_cta": entry["fwd_sensors_per_cta"]}
 
     def best(self, prob, force: bool = False) -> dict:
         k = self.key(prob)

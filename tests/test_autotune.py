@@ -6,8 +6,9 @@ from paper_2404_10928_gb300 import autotune, phantoms as ph
 
 def test_size_key_buckets():
     k = autotune.size_key("GB300", 2, 65536, 256, 2048)
-    assert k == "GB300|2d|N65536|S256|K2048"
-    assert autotune.size_key("GB300", 2, 65537, 200, 1500) == "GB300|2d|N131072|S256|K2048"
+    assert k == "GB300|2d|N65536|S256|K2048|yf32"
+    assert autotune.size_key("GB300", 2, 65537, 200, 1500, "f16") == \
+        "GB300|2d|N131072|S256|K2048|yf16"
 
 
 def test_candidates_respect_sensor_count():
@@ -28,6 +29,7 @@ def test_selection_and_cache(tmp_path):
     t = autotune.Autotuner(str(path), measure=fake, gpu_name="GB300")
     best = t.best(prob)
     assert (best["adj_cluster"], best["fwd_sensors_per_cta"]) == (4, 16)
+    assert autotune.Autotuner.plan_options(best) == {"adj_cluster": 4, "fwd_sensors_per_cta": 16}
     assert len(calls) == len(autotune.FWD_SENSORS) + 3
     # cached: a second tuner reads the file and does not measure again
     t2 = autotune.Autotuner(str(path), measure=lambda *a: 1 / 0, gpu_name="GB300")
