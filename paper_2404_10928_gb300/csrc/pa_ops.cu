@@ -1147,12 +1147,14 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
       pv[m] = in ? P.p_old[pix[m]] : 0.0f;
     }
     if (warp == 0) {
+      // gamma_old is loaded before the partials are summed, so its latency
+      // overlaps theirs
+      const double g_old = __ldcg(P.gamma_old);
       const DF t = warp_sum_partials(P.s_parts, P.n_s_parts);
       if (lane == 0) {
         // beta = ||s||^2 / gamma_old in double-float (an FP64 division would
         // be a long chain on GB300's FP64 pipe); one CTA records the FP64
         // values
-        const double g_old = *P.gamma_old;
         const DF go = df_from_double(g_old);
         const DF b = go.hi > 0.0f ? df_div(t, go) : df_zero();
         s_beta = b.hi;
