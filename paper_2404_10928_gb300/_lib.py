@@ -10,7 +10,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpa.so")
+# PA_LIB_PATH selects another build of the same library (the index-checked
+# libpa_checked.so, say); it must export the same entry points
+LIB_PATH = os.environ.get("PA_LIB_PATH") or os.path.join(HERE, "libpa.so")
 
 c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
 

@@ -625,15 +625,40 @@ int adjoint_smem_bytes(int L) {
 // Terms of A^T (DC: of the c-derivative's pixel sums) for a pixel pair and one
 // sensor: `base` is the magic_base of the sensor's centred window of packed
 // (mid, slope) samples; the interpolated value is mid + (w - n_c) slope.
+// Index checks of the checked build (compiled with -DPA_CHECKED): a window
+// element outside [0, L) of the staged window, or a combine slice outside its
+// window, latches ERR_INDEX in the plan's error word and the access is
+// skipped (never a trap).  Without PA_CHECKED the checks compile to nothing.
+struct Chk {
+  int L;     // elements of a staged window
+  int* err;  // the plan's device error word
+};
+#ifdef PA_CHECKED
+__device__ __forceinline__ bool chk_elem(const Chk& c, float t, int last) {
+  const int e = __float_as_int(t) - kMagicBits + (c.L >> 1);  // element index in the window
+  if ((unsigned)e <= (unsigned)last) return true;
+  atomicOr(c.err, ERR_INDEX);
+  return false;
+}
+#endif
+
 template <int DIM, bool NEAR, bool DC>
 __device__ __forceinline__ void adj_pair2(const TileRef2& r, uint32_t base, float2 ddx, float2 ddy,
                                           float2 ddz, float2 cm, float2 inv_kappa, float2 hik,
-                                          float& acc0, float& acc1) {
+                                          float& acc0, float& acc1, const Chk& chk) {
   float2 rinv;
   const float2 w = arrival2<DIM, NEAR>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv);
   const float2 t = add2(w, f2(kMagic));
+#ifdef PA_CHECKED
+  const float2 v0 = chk_elem(chk, t.x, chk.L - 1)
+                        ? lds_f2(base + ((uint32_t)__float_as_int(t.x) << 3)) : make_float2(0.f, 0.f);
+  const float2 v1 = chk_elem(chk, t.y, chk.L - 1)
+                        ? lds_f2(base + ((uint32_t)__float_as_int(t.y) << 3)) : make_float2(0.f, 0.f);
+#else
+  (void)chk;
   const float2 v0 = lds_f2(base + ((uint32_t)__float_as_int(t.x) << 3));
   const float2 v1 = lds_f2(base + ((uint32_t)__float_as_int(t.y) << 3));
+#endif
   if (DC) {  // g[k0 + 1] - g[k0]: the hat's derivative at the tap
     acc0 += v0.y;
     acc1 += v1.y;
@@ -705,6 +730,15 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
           if (r.klo != kSkip) {
             bytes = (uint32_t)L * (uint32_t)sizeof(float2);
             src = packed + (int64_t)s * P.Kp + P.pad + window_start(r.klo);
+#ifdef PA_CHECKED
+            const int ws0 = P.pad + window_start(r.klo);
+            if (ws0 < 0 || ws0 + L > P.Kp) {  // the window must lie inside its packed row
+              atomicOr(P.err, ERR_INDEX);
+              bytes = 0;
+              src = nullptr;
+              r.klo = kSkip;
+            }
+#endif
           }
         }
         if (r.klo != kSkip) {
@@ -743,6 +777,7 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
       acc[m] = 0.0f;
     }
     const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
+    const Chk chk{L, P.err};
     const uint32_t trace_u32 = smem_u32(s_trace);
     for (int j = 0; j < n_stages; ++j) {
       const int slot = j % kAdjStages;
@@ -765,12 +800,12 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
 #pragma unroll
           for (int h = 0; h < NPAIR; ++h)
             adj_pair2<DIM, true, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
-                                     acc[2 * h], acc[2 * h + 1]);
+                                     acc[2 * h], acc[2 * h + 1], chk);
         } else {
 #pragma unroll
           for (int h = 0; h < NPAIR; ++h)
             adj_pair2<DIM, false, DC>(r, base, ddx[h], ddy[h], ddz[h], cm[h], inv_kappa, hik,
-                                      acc[2 * h], acc[2 * h + 1]);
+                                      acc[2 * h], acc[2 * h + 1], chk);
         }
       }
       __syncwarp();
@@ -1061,7 +1096,7 @@ constexpr float kFixedScale = 1048576.0f;
 template <int DIM, bool NEAR>
 __device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, float2 ddx, float2 ddy,
                                           float2 ddz, float2 cm, float2 xs_dlo, float2 inv_kappa,
-                                          float2 hik) {
+                                          float2 hik, const Chk& chk) {
   float2 rinv;
   const float2 w = arrival2<DIM, NEAR>(r, ddx, ddy, ddz, cm, inv_kappa, hik, rinv);
   const float2 t = add2(w, f2(kMagic));
@@ -1072,10 +1107,23 @@ __device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, floa
   const float2 tw = add2(ws, f2(kMagic));                  // ws
   const uint32_t a0 = base + ((uint32_t)__float_as_int(t.x) << 2);
   const uint32_t a1 = base + ((uint32_t)__float_as_int(t.y) << 2);
-  reds_add(a0, __float_as_int(ta.x) - kMagicBits);
-  reds_add(a0 + 4u, __float_as_int(tw.x) - __float_as_int(ta.x));
-  reds_add(a1, __float_as_int(ta.y) - kMagicBits);
-  reds_add(a1 + 4u, __float_as_int(tw.y) - __float_as_int(ta.y));
+#ifdef PA_CHECKED
+  if (chk_elem(chk, t.x, chk.L - 2)) {
+#else
+  (void)chk;
+  {
+#endif
+    reds_add(a0, __float_as_int(ta.x) - kMagicBits);
+    reds_add(a0 + 4u, __float_as_int(tw.x) - __float_as_int(ta.x));
+  }
+#ifdef PA_CHECKED
+  if (chk_elem(chk, t.y, chk.L - 2)) {
+#else
+  {
+#endif
+    reds_add(a1, __float_as_int(ta.y) - kMagicBits);
+    reds_add(a1 + 4u, __float_as_int(tw.y) - __float_as_int(ta.y));
+  }
 }
 
 // One (tile, sensor chunk) work item of the forward gather.  The first
@@ -1204,6 +1252,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
 #pragma unroll
   for (int h = 0; h < 2; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
   const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
+  const Chk chk{L, P.err};
 
   // copy 0 of the windows; lane l deposits into copy c(l) of each sensor's
   // table entry, c(l) * CS words further
@@ -1227,12 +1276,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
 #pragma unroll
           for (int h = 0; h < 2; ++h)
             fwd_pair2<DIM, true>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
-                                 inv_kappa, hik);
+                                 inv_kappa, hik, chk);
         } else {
 #pragma unroll
           for (int h = 0; h < 2; ++h)
             fwd_pair2<DIM, false>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
-                                  inv_kappa, hik);
+                                  inv_kappa, hik, chk);
         }
       }
     }
@@ -1301,6 +1350,12 @@ __device__ __forceinline__ void combine_block(const FwdParams& P, int s, int kbl
     for (int j = 0; j < SPT; ++j) v[j] = 0.0f;
     auto add = [&](int2 a) {
       const float* src = ps + (int64_t)a.x * P.L + (k - a.y);
+#ifdef PA_CHECKED
+      if (k - a.y < 0 || k - a.y > P.L - SPT || a.x < 0 || a.x >= P.ntiles) {
+        atomicOr(P.err, ERR_INDEX);
+        return;
+      }
+#endif
       if (SPT == 4) {
         const float4 w = __ldcg(reinterpret_cast<const float4*>(src));
         v[0] += w.x;
