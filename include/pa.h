@@ -62,7 +62,7 @@ typedef enum {
   PA_ERR_UNSUPPORTED = 7    /* valid request this build does not handle */
 } pa_status;
 
-typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1, PA_FISTA = 2 } pa_method;
+typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1, PA_FISTA = 2, PA_PCGLS = 3 } pa_method;
 typedef enum { PA_F32 = 0, PA_F16 = 1, PA_F64 = 2 } pa_dtype;
 
 /* Regular grid of pixel centres (Sec. 3.4: r_ij, the Cartesian pixel
@@ -111,7 +111,9 @@ typedef struct {
  *   kernel_timing 1: CUDA events bracket every A and A^T gather launch; read the
  *                totals with pa_plan_kernel_times after the stream finished.
  *   l1_weight, tv_weight, tv_eps  FISTA only: the alpha and beta of Eq. 8 and the
- *                smoothing of its TV term (defaults 0, 0, 1e-4). */
+ *                smoothing of its TV term (defaults 0, 0, 1e-4).
+ *   restart      PCGLS only: the direction restarts (p = A^T r) every `restart`
+ *                iterations (>= 1; 0, the default: never). */
 typedef struct {
   double omega;
   int nonneg;
@@ -123,6 +125,7 @@ typedef struct {
   double l1_weight;
   double tv_weight;
   double tv_eps;
+  int restart;
 } pa_recon_opts;
 
 /* Facts about a plan (sizes, tiling, memory), for logging and benchmarks. */
@@ -345,7 +348,13 @@ pa_status pa_tv(pa_plan *plan, const float *x_dev, double eps, double *tv_dev, f
                 pa_stream stream);
 
 /* Iterative reconstruction.  PA_LANDWEBER and PA_CGLS minimise ||A x - y||^2
- * (the data term of Eq. 8).  PA_FISTA minimises the full objective of Eq. 8
+ * (the data term of Eq. 8).  PA_PCGLS minimises it over x >= 0 (with nonneg;
+ * without, it is CGLS with the residual recomputed from x every step) by CGLS
+ * with the iterate projected onto x >= 0 after every step and the direction
+ * restarted every opts->restart iterations: per iteration q = A p,
+ * alpha = ||A^T r||^2 / ||q||^2, x = max(0, x + alpha p), r = y - A x,
+ * s = A^T r, p = s (restart) or s + (||s||^2 / ||s_old||^2) p -- two
+ * applications of A and one of A^T.  PA_FISTA minimises the full objective of Eq. 8
  * with Phi = A and Psi' = identity,
  *     F(x) = ||A x - y||^2 + l1_weight ||x||_1 + tv_weight TV_eps(x)
  * (TV_eps as in pa_tv), by the fast iterative shrinkage-thresholding

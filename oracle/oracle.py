@@ -18,6 +18,8 @@ What is computed, and where it comes from:
   plus a non-negativity projection.
 * ``cgls``: conjugate gradients on the normal equations of the same data term
   (Hestenes-Stiefel recursion for least squares), then a final clamp x >= 0.
+* ``pcgls``: the same recursion projected onto x >= 0 after every step, with
+  restarts (the non-negative data term by CG).
 * ``power_iteration``: largest eigenvalue of A^T A (step size for Landweber).
 * ``tv`` / ``tv_grad``: smoothed isotropic total variation (the TV term of
   Eq. 8 with Psi' = identity), 2D and 3D.
@@ -339,6 +341,46 @@ def cgls(geo: Geometry, y, n_iter: int, x0=None, nonneg: bool = True, round_fp32
             iterates.append(x.copy())
     if nonneg:
         x = np.maximum(x, 0.0)
+    return x, np.array(hist)
+
+
+def pcgls(geo: Geometry, y, n_iter: int, restart: int = 0, x0=None, project: bool = True):
+    """Projected, restarted CGLS for min ||A x - y||^2 over x >= 0 (the CGLS
+    recursion of ``cgls`` with the iterate projected onto x >= 0 after every
+    step; reading: the paper's Eq. 8 with non-negativity and no L1/TV terms).
+
+    The projection breaks the residual recurrence, so r is recomputed from x:
+      x = max(0, x0); r = y - A x; s = A^T r; p = s; gamma = ||s||^2; then
+      q = A p; alpha = gamma / ||q||^2; x = max(0, x + alpha p); r = y - A x;
+      s = A^T r; gamma' = ||s||^2; p = s every ``restart``-th iteration
+      (restart >= 1; 0: never), else p = s + (gamma'/gamma) p.
+    ``project`` False keeps every step unconstrained (then the iterates are those
+    of plain CGLS).  Returns (x, history) with history[n] = ||r_n||^2."""
+    y = _f64(y).reshape(geo.n_sensors, geo.n_samples)
+    x = np.zeros(geo.n_pixels) if x0 is None else _f64(x0).ravel().copy()
+    if project:
+        x = np.maximum(x, 0.0)
+    r = y - forward(geo, x)
+    s = adjoint(geo, r)
+    p = s.copy()
+    gamma = float(np.sum(s * s))
+    hist = [float(np.sum(r * r))]
+    for k in range(n_iter):
+        q = forward(geo, p)
+        delta = float(np.sum(q * q))
+        alpha = gamma / delta if delta > 0.0 else 0.0
+        x = x + alpha * p
+        if project:
+            x = np.maximum(x, 0.0)
+        r = y - forward(geo, x)
+        hist.append(float(np.sum(r * r)))
+        s = adjoint(geo, r)
+        gamma_new = float(np.sum(s * s))
+        if restart > 0 and (k + 1) % restart == 0:
+            p = s.copy()
+        else:
+            p = s + (gamma_new / gamma if gamma > 0.0 else 0.0) * p
+        gamma = gamma_new
     return x, np.array(hist)
 
 

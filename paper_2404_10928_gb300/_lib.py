@@ -28,6 +28,7 @@ PA_ERR_UNSUPPORTED = 7
 PA_LANDWEBER = 0
 PA_CGLS = 1
 PA_FISTA = 2
+PA_PCGLS = 3
 PA_BP_NONE = 0
 PA_BP_UBP = 1
 PA_F32 = 0
@@ -50,7 +51,7 @@ class pa_recon_opts(ctypes.Structure):
     _fields_ = [("omega", c_double), ("nonneg", c_int), ("power_iters", c_int),
                 ("power_v0_dev", c_void_p), ("residual_history_host", ctypes.POINTER(c_double)),
                 ("use_graph", c_int), ("kernel_timing", c_int), ("l1_weight", c_double),
-                ("tv_weight", c_double), ("tv_eps", c_double)]
+                ("tv_weight", c_double), ("tv_eps", c_double), ("restart", c_int)]
 
 
 class pa_plan_info(ctypes.Structure):

@@ -14,9 +14,9 @@ import torch
 
 from . import _lib
 from ._lib import (PA_BP_NONE, PA_BP_UBP, PA_CGLS, PA_F16, PA_F32, PA_F64, PA_FISTA,
-                   PA_LANDWEBER, check)
+                   PA_LANDWEBER, PA_PCGLS, check)
 
-METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS, "fista": PA_FISTA}
+METHODS = {"landweber": PA_LANDWEBER, "cgls": PA_CGLS, "fista": PA_FISTA, "pcgls": PA_PCGLS}
 BP_FILTERS = {"none": PA_BP_NONE, "ubp": PA_BP_UBP}
 _DENSE_DTYPES = {torch.float64: PA_F64, torch.float32: PA_F32}
 
@@ -393,9 +393,10 @@ class Plan:
         return out.value
 
     def _opts(self, omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing,
-              l1=0.0, tv=0.0, tv_eps=1e-4):
+              l1=0.0, tv=0.0, tv_eps=1e-4, restart=0):
         o = _lib.pa_recon_opts()
         self._lib.pa_recon_opts_default(ctypes.byref(o))
+        o.restart = int(restart)
         o.l1_weight = float(l1)
         o.tv_weight = float(tv)
         o.tv_eps = float(tv_eps)
@@ -414,9 +415,11 @@ class Plan:
                     power_iters: int = 50, power_v0: Optional[torch.Tensor] = None,
                     history: bool = False, use_graph: bool = True, kernel_timing: bool = False,
                     out: Optional[torch.Tensor] = None, l1: float = 0.0, tv: float = 0.0,
-                    tv_eps: float = 1e-4):
-        """Minimise ||A x - y||^2 (Landweber with projection, or CGLS + final clamp),
-        or with method "fista" ||A x - y||^2 + l1 ||x||_1 + tv TV_eps(x) (Eq. 8).
+                    tv_eps: float = 1e-4, restart: int = 0):
+        """Minimise ||A x - y||^2 (Landweber with projection, CGLS + final clamp, or
+        "pcgls": CGLS projected onto x >= 0 every step, restarted every ``restart``
+        iterations), or with method "fista" ||A x - y||^2 + l1 ||x||_1 + tv TV_eps(x)
+        (Eq. 8).
 
         Returns x (and the residual history ||y - A x_n||^2, n = 0..n_iter, when
         ``history`` is set).  ``out`` (if given) is used in place: its contents
@@ -433,7 +436,7 @@ class Plan:
             self._check_tensor(power_v0, self.n_pixels, "power_v0")
         hist = np.zeros(n_iter + 1) if history else None
         o = self._opts(omega, nonneg, power_iters, power_v0, hist, use_graph, kernel_timing,
-                       l1, tv, tv_eps)
+                       l1, tv, tv_eps, restart)
         check(self._lib.pa_reconstruct(self._h, METHODS[method], int(n_iter), y.data_ptr(),
                                        out.data_ptr(), ctypes.byref(o),
                                        _stream_handle(self.device)), "pa_reconstruct")

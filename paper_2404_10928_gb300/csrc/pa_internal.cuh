@@ -202,6 +202,7 @@ struct FwdParams {
   const double* gamma_old;
   double* beta;
   double* gamma_new;
+  int beta_zero;          // 1: a restart, p = s (beta = 0)
   int* err;
   // frames of one launch (blockIdx.z): strides between consecutive frames (0
   // for a single frame; the CGLS direction update is single-frame only)
@@ -304,6 +305,10 @@ pa_status validate_grid(const pa_grid* g);
 cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float* r_out,
                            const float* q, float2* packed, const CglsAlpha& ca, int N, int S,
                            int K, int Kp, int pad, const Reduce& red, cudaStream_t st);
+// projected CGLS: alpha from the partials and x = x + alpha p, with
+// max(0, .) when clamp_x (the residual is then recomputed from x)
+cudaError_t launch_cgls_x(float* x, const float* pvec, const CglsAlpha& ca, int N, int S, int K,
+                          int clamp_x, cudaStream_t st);
 // hist[r] = sum of row r of `parts` (row stride `stride`; n_first partials in
 // row 0, n_rest in the others), rows = n_iter + 1
 cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,
@@ -412,7 +417,7 @@ struct pa_plan {
     std::vector<cudaEvent_t> fwd_ev, adj_ev;  // pairs (start, stop)
   };
   std::map<std::tuple<int, int, const void*, float*, double, int, int, const float*, int, double,
-                      double, double>,
+                      double, double, int>,
            GraphEntry>
       graphs;
   GraphEntry direct;                 // timing events of runs without a graph

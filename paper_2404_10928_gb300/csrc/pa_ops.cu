@@ -1204,12 +1204,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
         // be a long chain on GB300's FP64 pipe); one CTA records the FP64
         // values
         const DF go = df_from_double(g_old);
-        const DF b = go.hi > 0.0f ? df_div(t, go) : df_zero();
+        const DF b = (go.hi > 0.0f && !P.beta_zero) ? df_div(t, go) : df_zero();
         s_beta = b.hi;
         s_beta_lo = b.lo;
         if (tile == 0 && chunk == 0) {
           const double g_new = df_to_double(t);
-          *P.beta = g_old > 0.0 ? g_new / g_old : 0.0;
+          *P.beta = (g_old > 0.0 && !P.beta_zero) ? g_new / g_old : 0.0;
           *P.gamma_new = g_new;
         }
       }
@@ -1471,11 +1471,12 @@ constexpr int kVecThreads = 128;
 // per thread, work item b = s * kblocks + sample block of NT threads), with the
 // packed residual and the double-float partial of ||r_out||^2 (one per item).
 // Threads NT.. of a larger block only take part in the barriers.
-template <int NT>
+template <int NT, bool XONLY = false>
 __device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const float* r_in,
                                               float* r_out, const float* q, float2* packed,
                                               const CglsAlpha& ca, int N, int S, int K, int Kp,
-                                              int pad, const Reduce& red, int b, int nb) {
+                                              int pad, const Reduce& red, int b, int nb,
+                                              int clamp_x = 0) {
   __shared__ DF s_red[32];
   __shared__ float s_alpha, s_alpha_lo;
   __shared__ DF s_dg[2][32];
@@ -1505,7 +1506,7 @@ __device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const f
   float qv[5], rv[5];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {  // sample 4 = the next group's first (0 past the row)
-    const bool use = worker && k < K && j <= n && k + j < K;
+    const bool use = !XONLY && worker && k < K && j <= n && k + j < K;
     qv[j] = use ? q[o + j] : 0.0f;
     rv[j] = use ? r_in[o + j] : 0.0f;
   }
@@ -1543,7 +1544,14 @@ __device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const f
   __syncthreads();
   const DF alpha{s_alpha, s_alpha_lo};
   const DF malpha{-s_alpha, -s_alpha_lo};
-  // x += alpha p over this item's image slice
+  // x += alpha p over this item's image slice (then max(0, .) with clamp_x)
+  if (XONLY) {
+    auto proj = [&](float v) { return clamp_x ? fmaxf(v, 0.0f) : v; };
+    if (xin) x[xi] = proj(df_axpy(alpha, pv0, xv0));
+    if (worker)
+      for (int64_t i = xi + NT; i < x1; i += NT) x[i] = proj(df_axpy(alpha, pv[i], x[i]));
+    return;  // the residual is recomputed from x
+  }
   if (xin) x[xi] = df_axpy(alpha, pv0, xv0);
   if (worker)
     for (int64_t i = xi + NT; i < x1; i += NT) x[i] = df_axpy(alpha, pv[i], x[i]);
@@ -1581,6 +1589,19 @@ __global__ void __launch_bounds__(kVecThreads) k_cgls_xr(
     const CglsAlpha ca, int N, int S, int K, int Kp, int pad, const Reduce red) {
   cgls_xr_block<kVecThreads>(x, pv, r_in, r_out, q, packed, ca, N, S, K, Kp, pad, red, blockIdx.x,
                              gridDim.x);
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_cgls_x(float* x, const float* pv,
+                                                         const CglsAlpha ca, int N, int S, int K,
+                                                         int clamp_x) {
+  cgls_xr_block<kVecThreads, true>(x, pv, nullptr, nullptr, nullptr, nullptr, ca, N, S, K, 0, 0,
+                                   Reduce{}, blockIdx.x, gridDim.x, clamp_x);
+}
+
+cudaError_t launch_cgls_x(float* x, const float* pvec, const CglsAlpha& ca, int N, int S, int K,
+                          int clamp_x, cudaStream_t st) {
+  return launch_k(k_cgls_x, dim3(cgls_r_blocks(S, K)), dim3(kVecThreads), 0, st, 0, x, pvec, ca,
+                  N, S, K, clamp_x);
 }
 
 // number of r blocks of k_cgls_xr for S x K traces

@@ -234,6 +234,7 @@ void pa_recon_opts_default(pa_recon_opts* o) {
   o->l1_weight = 0.0;
   o->tv_weight = 0.0;
   o->tv_eps = 1e-4;
+  o->restart = 0;
 }
 
 pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors,

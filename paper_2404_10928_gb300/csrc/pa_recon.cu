@@ -135,6 +135,7 @@ struct DirUpdate {
   const double* gamma_old = nullptr;
   double* beta = nullptr;           // records
   double* gamma_new = nullptr;
+  int restart = 0;                  // 1: p = s (beta = 0)
 };
 
 // A reduction whose per-CTA partials are only stored (into `parts`); the
@@ -159,6 +160,7 @@ pa_status fwd(pa_plan* p, const float* x, float* out, int mode, const void* y, c
   f.gamma_old = du.gamma_old;
   f.beta = du.beta;
   f.gamma_new = du.gamma_new;
+  f.beta_zero = du.restart;
   PA_CUDA(launch_forward(p->dim, f, st));
   PA_TRY(mark(t, true, st));
   return PA_OK;
@@ -280,6 +282,57 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
   return PA_OK;
 }
 
+// Projected, restarted CGLS for min ||A x - y||^2 over x >= 0 (projection with
+// nonneg): per iteration q = A p (p = s + beta p fused into the gather, beta = 0
+// on a restart), x = max(0, x + alpha p), r = y - A x recomputed (the
+// projection breaks the recurrence; ||r||^2 -> history), s = A^T r.
+pa_status enqueue_pcgls(pa_plan* p, int n_iter, const void* y, float* x, const pa_recon_opts& o,
+                        const Scalars& sc, Timing& t, cudaStream_t st) {
+  const int N = p->grid.nx * p->grid.ny * p->grid.nz;
+  float* r = p->d_ra;
+  float* p_cur = p->d_pv;
+  float* p_prev = p->d_pb;
+  const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
+  const int n_adj = p->ntiles;
+  if (o.nonneg) PA_CUDA(launch_clamp(x, N, st));
+  PA_TRY(fwd(p, x, r, FWD_RESID, y, stored(p->d_parts_h), t, st));
+  PA_CUDA(launch_pack(r, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+  for (int it = 0; it < n_iter; ++it) {
+    if (it == 0) {
+      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
+    } else {
+      DirUpdate du;
+      du.s = p->d_sv;
+      du.p_old = p_prev;
+      du.p_new = p_cur;
+      du.s_parts = p->d_parts_s;
+      du.n_s_parts = n_adj;
+      du.gamma_old = sc.gamma + it - 1;
+      du.beta = sc.beta + it - 1;
+      du.gamma_new = sc.gamma + it;
+      du.restart = o.restart > 0 && it % o.restart == 0;
+      PA_TRY(fwd(p, nullptr, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st, du));
+    }
+    CglsAlpha ca;
+    ca.q_parts = p->d_parts_q;
+    ca.n_q_parts = n_comb;
+    ca.s_parts = p->d_parts_s;
+    ca.n_s_parts = n_adj;
+    ca.alpha = sc.alpha + it;
+    ca.gamma = sc.gamma + it;
+    ca.delta = sc.delta + it;
+    PA_CUDA(launch_cgls_x(x, p_cur, ca, N, p->S, p->K, o.nonneg, st));
+    PA_TRY(fwd(p, x, r, FWD_RESID, y, stored(p->d_parts_h + (size_t)(it + 1) * p->n_partials), t,
+               st));
+    PA_CUDA(launch_pack(r, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
+    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+    std::swap(p_cur, p_prev);
+  }
+  PA_CUDA(launch_hist(p->d_parts_h, p->n_partials, n_comb, n_comb, n_iter + 1, sc.hist, st));
+  return PA_OK;
+}
+
 // FISTA on F(x) = ||A x - y||^2 + alpha ||x||_1 + beta TV_eps(x) (Eq. 8 with
 // Phi = A, Psi' = I): per iteration r = y - A z (||r||^2 -> history), the TV
 // gradient at z, then A^T r with the proximal step and the extrapolation in the
@@ -329,6 +382,7 @@ pa_status enqueue_recon(pa_plan* p, pa_method method, int n_iter, const void* y,
   const Scalars sc = scalars(p, n_iter);
   if (method == PA_LANDWEBER) return enqueue_landweber(p, n_iter, y, x, o, sc, t, st);
   if (method == PA_FISTA) return enqueue_fista(p, n_iter, y, x, o, sc, t, st);
+  if (method == PA_PCGLS) return enqueue_pcgls(p, n_iter, y, x, o, sc, t, st);
   return enqueue_cgls(p, n_iter, y, x, o, sc, t, st);
 }
 
@@ -373,7 +427,8 @@ pa_status pa_power_iteration(pa_plan* plan, int n_iter, const float* v0_dev, dou
 pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void* y_dev,
                          float* x_dev, const pa_recon_opts* opts, pa_stream stream) {
   if (!plan || !y_dev || !x_dev || n_iter < 0 ||
-      (method != PA_LANDWEBER && method != PA_CGLS && method != PA_FISTA)) {
+      (method != PA_LANDWEBER && method != PA_CGLS && method != PA_FISTA &&
+       method != PA_PCGLS)) {
     set_error("pa_reconstruct: invalid argument");
     return PA_ERR_INVALID_ARG;
   }
@@ -382,7 +437,7 @@ pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void
   if (opts) o = *opts;
   if (!std::isfinite(o.omega) || o.power_iters < 0 || !std::isfinite(o.l1_weight) ||
       o.l1_weight < 0.0 || !std::isfinite(o.tv_weight) || o.tv_weight < 0.0 ||
-      !(o.tv_eps > 0.0) || !std::isfinite(o.tv_eps)) {
+      !(o.tv_eps > 0.0) || !std::isfinite(o.tv_eps) || o.restart < 0) {
     set_error("pa_reconstruct: invalid options");
     return PA_ERR_INVALID_ARG;
   }
@@ -395,7 +450,7 @@ pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void
   if (o.use_graph) {
     const auto key = std::make_tuple((int)method, n_iter, y_dev, x_dev, o.omega, o.nonneg,
                                      o.power_iters, o.power_v0_dev, o.kernel_timing,
-                                     o.l1_weight, o.tv_weight, o.tv_eps);
+                                     o.l1_weight, o.tv_weight, o.tv_eps, o.restart);
     auto it = plan->graphs.find(key);
     if (it == plan->graphs.end()) {
       pa_plan::GraphEntry entry;

@@ -50,9 +50,9 @@ int main(void) {
   printf("pa_grid %zu %zu %zu\n", sizeof(pa_grid), offsetof(pa_grid, dx), offsetof(pa_grid, origin));
   printf("pa_plan_opts %zu %zu %zu\n", sizeof(pa_plan_opts), offsetof(pa_plan_opts, y_dtype),
          offsetof(pa_plan_opts, fwd_sensors_per_cta));
-  printf("pa_recon_opts %zu %zu %zu %zu %zu\n", sizeof(pa_recon_opts), offsetof(pa_recon_opts, power_v0_dev),
+  printf("pa_recon_opts %zu %zu %zu %zu %zu %zu\n", sizeof(pa_recon_opts), offsetof(pa_recon_opts, power_v0_dev),
          offsetof(pa_recon_opts, residual_history_host), offsetof(pa_recon_opts, kernel_timing),
-         offsetof(pa_recon_opts, tv_eps));
+         offsetof(pa_recon_opts, tv_eps), offsetof(pa_recon_opts, restart));
   printf("pa_plan_info %zu %zu %zu\n", sizeof(pa_plan_info), offsetof(pa_plan_info, tile),
          offsetof(pa_plan_info, device_bytes));
   return 0;
@@ -70,7 +70,7 @@ int main(void) {
     assert rows["pa_recon_opts"] == [ctypes.sizeof(S.pa_recon_opts), S.pa_recon_opts.power_v0_dev.offset,
                                      S.pa_recon_opts.residual_history_host.offset,
                                      S.pa_recon_opts.kernel_timing.offset,
-                                     S.pa_recon_opts.tv_eps.offset]
+                                     S.pa_recon_opts.tv_eps.offset, S.pa_recon_opts.restart.offset]
     assert rows["pa_plan_info"] == [ctypes.sizeof(S.pa_plan_info), S.pa_plan_info.tile.offset,
                                     S.pa_plan_info.device_bytes.offset]
 

@@ -166,3 +166,37 @@ def test_batch_cgls_3d_and_fista_rejected(torch_cuda):
     finally:
         for p in plans:
             p.close()
+
+
+def test_batch_time_series_frames_full_size_against_oracle(torch_cuda):
+    """Four frames of the 64-frame ragged time series at their full sizes (grids up
+    to 512^2, up to 512 sensors and 4096 samples, FP16 traces), batched Landweber
+    (the persistent launch the benchmark times) and batched CGLS, 5 iterations,
+    against the FP64 oracle at the reconstruction tolerance."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300.api import Batch, Plan
+    frames = ph.ragged_time_series(n_frames=4)
+    plans = [Plan.from_problem(p, adj_cluster=1) for p in frames]
+    try:
+        ys, omegas, geos = [], [], []
+        for prob in frames:
+            geo = orc.Geometry.of(prob)
+            y16 = orc.forward(geo, prob.x_true).astype(np.float16)
+            ys.append(y16)
+            omegas.append(1.0 / orc.power_iteration(geo, ph.power_start(prob.n_pixels), 20))
+            geos.append(geo)
+        yd = [torch.tensor(y, dtype=torch.float16, device="cuda") for y in ys]
+        xl = [torch.zeros(p.n_pixels, dtype=torch.float32, device="cuda") for p in frames]
+        xc = [torch.zeros(p.n_pixels, dtype=torch.float32, device="cuda") for p in frames]
+        with Batch(plans) as batch:
+            batch.reconstruct(yd, xl, "landweber", 5, omegas=omegas)
+            batch.reconstruct(yd, xc, "cgls", 5)
+        for f, geo in enumerate(geos):
+            y64 = ys[f].astype(np.float64)
+            ref_l, _ = orc.landweber(geo, y64, 5, omega=omegas[f])
+            ref_c, _ = orc.cgls(geo, y64, 5)
+            assert rel_l2(xl[f].cpu().numpy(), ref_l) <= RECON_TOL, f
+            assert rel_l2(xc[f].cpu().numpy(), ref_c) <= RECON_TOL, f
+    finally:
+        for p in plans:
+            p.close()

@@ -248,3 +248,40 @@ def test_fista_default_step_from_power_iteration(torch_cuda, disks):
                              power_v0=_dev(torch, v0), l1=alpha, tv=beta, tv_eps=eps)
         x = x.cpu().numpy()
     assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+
+
+@pytest.mark.parametrize("restart,nonneg", [(0, True), (3, True), (1, True), (0, False)])
+def test_pcgls_matches_oracle(torch_cuda, disks, restart, nonneg):
+    """Projected, restarted CGLS (x >= 0 every step, r recomputed from x) on the
+    linear-array disk workload: 5 iterations against the oracle at 1e-4."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    x_ref, h_ref = orc.pcgls(geo, y, 5, restart=restart, project=nonneg)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "pcgls", 5, nonneg=nonneg, restart=restart,
+                                history=True)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL, atol=RECON_TOL * h_ref[0])
+    if nonneg:
+        assert x.min() >= 0.0
+
+
+def test_pcgls_reaches_nnls_on_a_small_system(torch_cuda):
+    """With a restart every step the projected iteration converges to the
+    non-negative least-squares solution (scipy's Lawson-Hanson NNLS on the
+    explicit matrix), to FP32 accuracy."""
+    torch = torch_cuda
+    from scipy.optimize import nnls
+    prob = ph.custom(2, (6, 5), (1e-4, 1e-4), ph.ring_sensors(9, 1.5e-3), 80, seed=51)
+    geo = orc.Geometry.of(prob)
+    m = orc.matrix(geo)
+    rng = np.random.default_rng(52)
+    truth = np.where(rng.uniform(size=prob.n_pixels) < 0.5, rng.uniform(0.2, 1.0, prob.n_pixels),
+                     0.0)
+    y = f32(m @ truth + 0.05 * rng.standard_normal(m.shape[0]))
+    ref = nnls(m, y)[0]
+    with _plan(prob) as plan:
+        x = plan.reconstruct(_dev(torch, y), "pcgls", 3000, restart=1).cpu().numpy()
+    assert np.all(x >= 0.0)
+    assert rel_l2(x, ref) <= 1e-3, rel_l2(x, ref)

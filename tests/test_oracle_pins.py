@@ -557,3 +557,48 @@ def test_fista_3d_tv_meets_the_optimality_conditions():
     assert active.any()
     assert np.all(np.abs(g[active] + alpha) <= 1e-6 * scale)
     assert np.all(g[~active] + alpha >= -1e-6 * scale)
+
+
+def test_pcgls_one_pixel_hand_values():
+    """One pixel, operator = the column (1/d at sample 80): m = A^T A = 1/d^2 and
+    g = A^T y.  From x = 0 the first CG step is the exact line search along
+    s = g: alpha = g^2 / (m g^2) = 1/m, so x1 = max(0, g/m), the non-negative
+    least-squares solution; with a negative measurement the projection stops at
+    0 and the residual stays ||y||^2."""
+    geo = orc.Geometry(2, (1, 1, 1), (1e-4, 1e-4, 1e-4), (0.0, 0.0, 0.0),
+                       np.array([[0.0, 3e-3]]), 1500.0, 4e7, 128)
+    d = 3e-3
+    for y80, expect in ((0.02, 0.02 * d), (-0.02, 0.0)):
+        y = np.zeros((1, 128))
+        y[0, 80] = y80
+        x, h = orc.pcgls(geo, y, 1)
+        assert abs(x[0] - expect) <= 1e-15
+        assert abs(h[0] - y80 * y80) <= 1e-18
+        assert abs(h[1] - (0.0 if y80 > 0 else y80 * y80)) <= 1e-18
+
+
+def test_pcgls_unprojected_is_cgls_and_projected_reaches_nnls():
+    prob = ph.custom(2, (6, 5), (1e-4, 1e-4), ph.ring_sensors(9, 1.5e-3), 80, seed=51)
+    geo = orc.Geometry.of(prob)
+    m = orc.matrix(geo)
+    rng = np.random.default_rng(52)
+    truth = np.where(rng.uniform(size=prob.n_pixels) < 0.5, rng.uniform(0.2, 1.0, prob.n_pixels),
+                     0.0)
+    y = m @ truth + 0.05 * rng.standard_normal(m.shape[0])
+    # without the projection the recursion is plain CGLS (r recomputed from x
+    # instead of by the recurrence: the same iterates up to rounding)
+    xu, hu = orc.pcgls(geo, y, 12, project=False)
+    xc, hc = orc.cgls(geo, y, 12, nonneg=False)
+    assert np.allclose(xu, xc, rtol=1e-9, atol=1e-12 * np.abs(xc).max())
+    assert np.allclose(hu, hc, rtol=1e-9)
+    # with the projection and a restart every step (projected steepest descent
+    # with the exact line search) and every 3rd step, the iterates reach the
+    # non-negative least-squares solution
+    from scipy.optimize import nnls
+    ref = nnls(m, y)[0]
+    assert (ref == 0).any() and (ref > 0).any()  # active constraints exercised
+    for restart in (1, 3):
+        x, h = orc.pcgls(geo, y, 3000, restart=restart)
+        assert np.all(x >= 0.0)
+        assert np.allclose(x, ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max()), restart
+        assert h[-1] <= h[0]
