@@ -567,6 +567,18 @@ def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
     t_c = _events_time(torch, cgls, reps)
     t_d = _events_time(torch, lambda: plan.dc(x, y), reps)
     plan.close()
+    # the same 30 CGLS iterations with the sensors split into two shards of 512
+    # (pa_shard_cgls_*, host-driven, the two sums formed by the library's
+    # accumulate mode): the cost of the split's extra launches on one GPU
+    from paper_2404_10928_gb300 import shard
+    ranges = shard.sensor_ranges(prob.n_sensors, 2)
+    shards = shard.shard_plans(prob, ranges, **tuner.plan_options(t))
+    yr = y.reshape(prob.n_sensors, -1)
+    ys = [yr[b:e].contiguous() for b, e in ranges]
+    shard.sharded_cgls(shards, ys, 30)
+    t_s = _events_time(torch, lambda: shard.sharded_cgls(shards, ys, 30), reps)
+    for sp in shards:
+        sp.close()
     pairs = prob.pairs
     return {"workload": "3D 128^3 at 0.2 mm, 32x32 planar array 0.8 mm pitch 5 mm from the "
                         "volume, 1024 samples, vessel tree",
@@ -577,6 +589,7 @@ def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
             "adjoint_frac_fp32": pairs * FLOPS_PER_PAIR / t_a / 1e12 / peak_tflops,
             "forward_frac_fp32": pairs * FLOPS_PER_PAIR / t_f / 1e12 / peak_tflops,
             "cgls30_ms": t_c * 1e3, "cgls30_frames_per_s": 1.0 / t_c, "dc_ms": t_d * 1e3,
+            "cgls30_two_sensor_shards_ms": t_s * 1e3,
             "timing": f"median of {reps}, CUDA events (inputs far larger than L2)"}
 
 

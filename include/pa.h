@@ -373,6 +373,45 @@ pa_status pa_reconstruct(pa_plan *plan, pa_method method, int n_iter, const void
 pa_status pa_reconstruct_host(pa_plan *plan, pa_method method, int n_iter, const void *y_host,
                               float *x_host, const pa_recon_opts *opts, pa_stream stream);
 
+/* ---- Sensor-sharded CGLS: one frame's sensors split over several plans ----
+ * The rows of A (Eq. 6 evaluated at every sensor and sample) split by sensor:
+ * A = [A_1; ...; A_R], y = [y_1; ...; y_R], and ||A x - y||^2 is the sum of the
+ * shards' ||A_r x - y_r||^2, so CGLS on the data term of Eq. 8 runs with each
+ * shard applying A_r and A_r^T to its own sensors.  Each shard is a plan over
+ * its sensors and the WHOLE image grid (same grid, c, f_s, t0 and amp_scale on
+ * every shard).  Two sums over all shards per iteration are the caller's: the
+ * partial images A_r^T r_r (N float32) and the scalars ||A_r p||^2 (FP64), e.g.
+ * an all-reduce between ranks; every shard then sees the same s, delta, alpha,
+ * beta and x.  Within one process several shards may add into one buffer in
+ * turn (accumulate = 1 for every shard after the first); only one of them
+ * updates a given x (the others pass x_dev = NULL).
+ * Call order per plan: begin, then for it = 0..n_iter-1: direction(it) and
+ * update(it), then finish (after any whole number of iterations); any other
+ * order returns PA_ERR_INVALID_ARG.  The plan's workspace holds the state: no
+ * other call may run on the plan between begin and finish.  All calls are
+ * asynchronous on `stream`.
+ *
+ * begin: r_0 = y - A_r x_0, s_part = A_r^T r_0 (+= with accumulate).
+ *   y_dev: [S_r][K] traces of this plan's sensors (the plan's y dtype); x_dev:
+ *   [N] float32 start image; s_part_dev: [N] float32.  n_iter >= 0.
+ * direction(it): s_dev = the sum over shards of s_part (read only):
+ *   p_it = s (it = 0) or s + (||s||^2 / ||s_prev||^2) p_{it-1}; q = A_r p_it;
+ *   *delta_part_dev = ||q||^2 (FP64, device; += with accumulate).
+ * update(it): *delta_dev = the sum over shards of the delta parts (FP64,
+ *   device): alpha = ||s||^2 / delta, x += alpha p_it (x_dev NULL: x left
+ *   alone), r = r - alpha q, s_part = A_r^T r (+= with accumulate).
+ * finish: hist_dev (NULL or [n_done + 1] FP64, device) receives this shard's
+ *   ||r_n||^2, n = 0..n_done (+= with accumulate: the sum over shards is the
+ *   full residual); with nonneg, x = max(0, x) (x_dev required). */
+pa_status pa_shard_cgls_begin(pa_plan *plan, int n_iter, const void *y_dev, const float *x_dev,
+                              float *s_part_dev, int accumulate, pa_stream stream);
+pa_status pa_shard_cgls_direction(pa_plan *plan, int it, const float *s_dev,
+                                  double *delta_part_dev, int accumulate, pa_stream stream);
+pa_status pa_shard_cgls_update(pa_plan *plan, int it, const double *delta_dev, float *x_dev,
+                               float *s_part_dev, int accumulate, pa_stream stream);
+pa_status pa_shard_cgls_finish(pa_plan *plan, float *x_dev, int nonneg, double *hist_dev,
+                               int accumulate, pa_stream stream);
+
 /* Device time of the two gathers in the form a CGLS iteration runs them, for
  * benchmarks and roofline figures: after one warm-up of each, `reps`
  * back-to-back applications of A to x_dev (the tile gather and the window

@@ -87,6 +87,10 @@ SIGNATURES = {
                                     ctypes.POINTER(pa_recon_opts), _STREAM]),
     "pa_plan_kernel_times": (c_int, [_P, _DP, ctypes.POINTER(c_int), _DP, ctypes.POINTER(c_int)]),
     "pa_plan_time_gathers": (c_int, [_P, c_int, c_void_p, c_void_p, _DP, _DP, _STREAM]),
+    "pa_shard_cgls_begin": (c_int, [_P, c_int, c_void_p, c_void_p, c_void_p, c_int, _STREAM]),
+    "pa_shard_cgls_direction": (c_int, [_P, c_int, c_void_p, c_void_p, c_int, _STREAM]),
+    "pa_shard_cgls_update": (c_int, [_P, c_int, c_void_p, c_void_p, c_void_p, c_int, _STREAM]),
+    "pa_shard_cgls_finish": (c_int, [_P, c_void_p, c_int, c_void_p, c_int, _STREAM]),
     "pa_dc": (c_int, [_P, c_void_p, c_void_p, c_void_p, _STREAM]),
     "pa_batch_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int]),
     "pa_batch_destroy": (c_int, [c_void_p]),

@@ -472,6 +472,50 @@ class Plan:
                                              _stream_handle(self.device)), "pa_plan_time_gathers")
         return {"fwd_ms": fm.value, "adj_ms": am.value, "reps": int(reps)}
 
+    # -- sensor-sharded CGLS (pa_shard_cgls_*; the driver is shard.sharded_cgls) --
+    def shard_cgls_begin(self, n_iter: int, y: torch.Tensor, x: torch.Tensor,
+                         s_part: torch.Tensor, accumulate: bool = False) -> None:
+        ydt = torch.float16 if self.y_dtype == "f16" else torch.float32
+        self._check_tensor(y, self.n_sensors * self.n_samples, "y", ydt)
+        self._check_tensor(x, self.n_pixels, "x")
+        self._check_tensor(s_part, self.n_pixels, "s_part")
+        check(self._lib.pa_shard_cgls_begin(self._h, int(n_iter), y.data_ptr(), x.data_ptr(),
+                                            s_part.data_ptr(), int(bool(accumulate)),
+                                            _stream_handle(self.device)), "pa_shard_cgls_begin")
+
+    def shard_cgls_direction(self, it: int, s: torch.Tensor, delta_part: torch.Tensor,
+                             accumulate: bool = False) -> None:
+        self._check_tensor(s, self.n_pixels, "s")
+        self._check_tensor(delta_part, 1, "delta_part", torch.float64)
+        check(self._lib.pa_shard_cgls_direction(self._h, int(it), s.data_ptr(),
+                                                delta_part.data_ptr(), int(bool(accumulate)),
+                                                _stream_handle(self.device)),
+              "pa_shard_cgls_direction")
+
+    def shard_cgls_update(self, it: int, delta: torch.Tensor, x: Optional[torch.Tensor],
+                          s_part: torch.Tensor, accumulate: bool = False) -> None:
+        self._check_tensor(delta, 1, "delta", torch.float64)
+        if x is not None:
+            self._check_tensor(x, self.n_pixels, "x")
+        self._check_tensor(s_part, self.n_pixels, "s_part")
+        check(self._lib.pa_shard_cgls_update(self._h, int(it), delta.data_ptr(),
+                                             x.data_ptr() if x is not None else None,
+                                             s_part.data_ptr(), int(bool(accumulate)),
+                                             _stream_handle(self.device)), "pa_shard_cgls_update")
+
+    def shard_cgls_finish(self, x: Optional[torch.Tensor], nonneg: bool,
+                          hist: Optional[torch.Tensor], accumulate: bool = False) -> None:
+        if x is not None:
+            self._check_tensor(x, self.n_pixels, "x")
+        if hist is not None and (hist.device != self.device or hist.dtype != torch.float64
+                                 or not hist.is_contiguous()):
+            raise ValueError(f"hist must be a contiguous float64 tensor on {self.device}")
+        check(self._lib.pa_shard_cgls_finish(self._h, x.data_ptr() if x is not None else None,
+                                             int(bool(nonneg)),
+                                             hist.data_ptr() if hist is not None else None,
+                                             int(bool(accumulate)), _stream_handle(self.device)),
+              "pa_shard_cgls_finish")
+
     def kernel_times(self) -> dict:
         fm, am = ctypes.c_double(), ctypes.c_double()
         fn, an = ctypes.c_int(), ctypes.c_int()

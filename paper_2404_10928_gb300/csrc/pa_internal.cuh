@@ -312,7 +312,7 @@ cudaError_t launch_cgls_x(float* x, const float* pvec, const CglsAlpha& ca, int 
 // hist[r] = sum of row r of `parts` (row stride `stride`; n_first partials in
 // row 0, n_rest in the others), rows = n_iter + 1
 cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,
-                        double* hist, cudaStream_t st);
+                        double* hist, cudaStream_t st, int accumulate = 0);
 int cgls_r_blocks(int S, int K);
 cudaError_t launch_scale(float* v, const float* w, const double* factor, int N,
                          cudaStream_t st);
@@ -327,6 +327,8 @@ cudaError_t launch_affine_sum(const double* a, int n, const double* b, int m, do
 cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
+// parts[0] = the double-float form (hi, lo) of *v
+cudaError_t launch_df_of(const double* v, float2* parts, cudaStream_t st);
 cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,
                       const Reduce& red, cudaStream_t st);
 int tv_blocks(int64_t n);
@@ -397,6 +399,9 @@ struct pa_plan {
   int scal_cap = 0;
   void* d_yhost = nullptr;    // device copies for pa_reconstruct_host
   float* d_xhost = nullptr;
+  // sensor-sharded CGLS (pa_shard_cgls_*): iterations of the current run, the
+  // next iteration and the phase expected next (0 none, 1 direction, 2 update)
+  int shard_n = 0, shard_it = 0, shard_phase = 0;
   // workspace of the multi-frame entry points (pa_*_frames), for up to
   // frames_cap frames: windows, packed traces, partials, per-frame sums and
   // the temporaries of the vector-Jacobian products

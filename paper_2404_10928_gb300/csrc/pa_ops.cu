@@ -1511,7 +1511,7 @@ __device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const f
     rv[j] = use ? r_in[o + j] : 0.0f;
   }
   const int64_t xi = x0 + tid;
-  const bool xin = worker && xi < x1;
+  const bool xin = x != nullptr && worker && xi < x1;
   const float xv0 = xin ? x[xi] : 0.0f, pv0 = xin ? pv[xi] : 0.0f;
 #pragma unroll
   for (int sh = 16; sh > 0; sh >>= 1) {
@@ -1548,12 +1548,12 @@ __device__ __forceinline__ void cgls_xr_block(float* x, const float* pv, const f
   if (XONLY) {
     auto proj = [&](float v) { return clamp_x ? fmaxf(v, 0.0f) : v; };
     if (xin) x[xi] = proj(df_axpy(alpha, pv0, xv0));
-    if (worker)
+    if (worker && x)
       for (int64_t i = xi + NT; i < x1; i += NT) x[i] = proj(df_axpy(alpha, pv[i], x[i]));
     return;  // the residual is recomputed from x
   }
   if (xin) x[xi] = df_axpy(alpha, pv0, xv0);
-  if (worker)
+  if (worker && x)  // x == nullptr: the step leaves x alone (a second shard of one process)
     for (int64_t i = xi + NT; i < x1; i += NT) x[i] = df_axpy(alpha, pv[i], x[i]);
   DF part = df_zero();
   if (worker && k < K) {
@@ -1617,17 +1617,18 @@ cudaError_t launch_cgls_xr(float* x, const float* pvec, const float* r_in, float
 // The residual history of a reconstruction: one CTA per iteration sums that
 // iteration's partials (stored by the producing kernels with OP_STORE).
 __global__ void __launch_bounds__(kVecThreads) k_hist(const float2* parts, int stride,
-                                                     int n_first, int n_rest, double* hist) {
+                                                     int n_first, int n_rest, double* hist,
+                                                     int accumulate) {
   __shared__ DF s_red[kVecThreads / 32];
   const int row = blockIdx.x;
   const DF t = sum_partials(parts + (int64_t)row * stride, row == 0 ? n_first : n_rest, s_red);
-  if (threadIdx.x == 0) hist[row] = df_to_double(t);
+  if (threadIdx.x == 0) hist[row] = accumulate ? hist[row] + df_to_double(t) : df_to_double(t);
 }
 
 cudaError_t launch_hist(const float2* parts, int stride, int n_first, int n_rest, int rows,
-                        double* hist, cudaStream_t st) {
+                        double* hist, cudaStream_t st, int accumulate) {
   return launch_k(k_hist, dim3(rows), dim3(kVecThreads), 0, st, 0, parts, stride, n_first,
-                  n_rest, hist);
+                  n_rest, hist, accumulate);
 }
 
 __global__ void k_scale(float* v, const float* w,
@@ -1646,6 +1647,12 @@ __global__ void k_clamp(float* x, int N) {
 
 __global__ void k_set_scalar(double* dst, double v) {
   *dst = v;
+}
+
+__global__ void k_df_of(const double* v, float2* parts) {
+  const double d = *v;
+  const float hi = (float)d;
+  parts[0] = make_float2(hi, (float)(d - (double)hi));
 }
 
 __global__ void k_fill(float* dst, float v, int64_t n) {
@@ -1724,6 +1731,9 @@ cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cu
 }
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st) {
   return launch_k(k_fill, dim3(vec_blocks(n)), dim3(kVecThreads), 0, st, 0, dst, value, n);
+}
+cudaError_t launch_df_of(const double* v, float2* parts, cudaStream_t st) {
+  return launch_k(k_df_of, dim3(1), dim3(1), 0, st, 0, v, parts);
 }
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st) {
   return launch_k(k_norm, dim3(nblk), dim3(kVecThreads), 0, st, 0, v, n, red);

@@ -580,3 +580,160 @@ pa_status pa_plan_kernel_times(pa_plan* plan, double* fwd_ms, int* n_fwd, double
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sensor-sharded CGLS: the sensors of one frame split over several plans (one
+// per rank, or several in one process).  Iteration it keeps p_it in
+// shard_p(it) and r_it in shard_r(it) of the plan's workspace; the caller forms
+// the sums over shards (the partial images A_r^T r_r and the scalars
+// ||A_r p||^2) between the calls.
+// ---------------------------------------------------------------------------
+namespace pa {
+namespace {
+float* shard_p(pa_plan* p, int it) { return (it & 1) ? p->d_pb : p->d_pv; }
+float* shard_r(pa_plan* p, int it) { return (it & 1) ? p->d_rb : p->d_ra; }
+
+// s_part = A^T r (r packed in d_packed), or s_part += A^T r with accumulate
+pa_status shard_adjoint(pa_plan* p, float* s_part, int accumulate, cudaStream_t st) {
+  AdjParams a = adjoint_params(p, s_part, accumulate ? ADJ_AXPY : ADJ_STORE, nullptr, 0);
+  if (accumulate) {
+    a.xin = s_part;
+    a.coef = 1.0f;
+  }
+  PA_CUDA(launch_adjoint(p->dim, a, p->cluster, p->ntiles, st));
+  return PA_OK;
+}
+
+pa_status shard_order(pa_plan* p, const char* fn, int phase, int it) {
+  if (p->shard_phase != phase || it != p->shard_it || it >= p->shard_n) {
+    set_error("%s: called out of order (iteration %d; next expected: %s of iteration %d of %d)",
+              fn, it, p->shard_phase == 1 ? "direction" : p->shard_phase == 2 ? "update" : "begin",
+              p->shard_it, p->shard_n);
+    return PA_ERR_INVALID_ARG;
+  }
+  return PA_OK;
+}
+}  // namespace
+}  // namespace pa
+
+extern "C" {
+
+pa_status pa_shard_cgls_begin(pa_plan* plan, int n_iter, const void* y_dev, const float* x_dev,
+                              float* s_part_dev, int accumulate, pa_stream stream) {
+  if (!plan || !y_dev || !x_dev || !s_part_dev || n_iter < 0) {
+    set_error("pa_shard_cgls_begin: NULL argument or n_iter < 0");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  plan->shard_phase = 0;
+  PA_TRY(ensure_workspace(plan, n_iter));
+  cudaStream_t st = (cudaStream_t)stream;
+  Timing none;
+  float* r0 = shard_r(plan, 0);
+  // r_0 = y - A x_0 (||r_0||^2 -> history row 0); s_part = A^T r_0
+  PA_TRY(fwd(plan, x_dev, r0, FWD_RESID, y_dev, stored(plan->d_parts_h), none, st));
+  PA_CUDA(launch_pack(r0, plan->d_packed, plan->S, plan->K, plan->Kp, plan->pad, st));
+  PA_TRY(shard_adjoint(plan, s_part_dev, accumulate, st));
+  plan->shard_n = n_iter;
+  plan->shard_it = 0;
+  plan->shard_phase = 1;
+  return PA_OK;
+}
+
+pa_status pa_shard_cgls_direction(pa_plan* plan, int it, const float* s_dev,
+                                  double* delta_part_dev, int accumulate, pa_stream stream) {
+  if (!plan || !s_dev || !delta_part_dev) {
+    set_error("pa_shard_cgls_direction: NULL argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  PA_TRY(shard_order(plan, "pa_shard_cgls_direction", 1, it));
+  DeviceScope scope(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Timing none;
+  const int64_t N = (int64_t)plan->grid.nx * plan->grid.ny * plan->grid.nz;
+  const Scalars sc = scalars(plan, plan->shard_n);
+  // partials of gamma_it = ||s_it||^2 from the summed image (identical on every shard)
+  const int n_s = vec_blocks_r(N);
+  PA_CUDA(launch_norm(s_dev, N, stored(plan->d_parts_s), n_s, st));
+  // q = A p_it; ||q||^2 over this plan's sensors -> *delta_part_dev (+= with accumulate)
+  Reduce rq = make_reduce(plan, OP_SUM, delta_part_dev, nullptr, nullptr);
+  rq.accumulate = accumulate ? 1 : 0;
+  if (it == 0) {  // p_0 = s_0
+    PA_CUDA(cudaMemcpyAsync(shard_p(plan, 0), s_dev, (size_t)N * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st));
+    PA_TRY(fwd(plan, shard_p(plan, 0), plan->d_q, FWD_NORM, nullptr, rq, none, st));
+  } else {  // p_it = s_it + (gamma_it / gamma_{it-1}) p_{it-1}, fused into the gather
+    DirUpdate du;
+    du.s = s_dev;
+    du.p_old = shard_p(plan, it - 1);
+    du.p_new = shard_p(plan, it);
+    du.s_parts = plan->d_parts_s;
+    du.n_s_parts = n_s;
+    du.gamma_old = sc.gamma + it - 1;
+    du.beta = sc.beta + it - 1;
+    du.gamma_new = sc.gamma + it;
+    PA_TRY(fwd(plan, nullptr, plan->d_q, FWD_NORM, nullptr, rq, none, st, du));
+  }
+  plan->shard_phase = 2;
+  return PA_OK;
+}
+
+pa_status pa_shard_cgls_update(pa_plan* plan, int it, const double* delta_dev, float* x_dev,
+                               float* s_part_dev, int accumulate, pa_stream stream) {
+  if (!plan || !delta_dev || !s_part_dev) {
+    set_error("pa_shard_cgls_update: NULL argument");
+    return PA_ERR_INVALID_ARG;
+  }
+  PA_TRY(shard_order(plan, "pa_shard_cgls_update", 2, it));
+  DeviceScope scope(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Timing none;
+  const int64_t N = (int64_t)plan->grid.nx * plan->grid.ny * plan->grid.nz;
+  const Scalars sc = scalars(plan, plan->shard_n);
+  // alpha = gamma_it / delta (delta summed over all shards); x += alpha p_it;
+  // r_{it+1} = r_it - alpha q (packed; ||r||^2 -> history row it + 1)
+  PA_CUDA(launch_df_of(delta_dev, plan->d_parts_q, st));
+  CglsAlpha ca;
+  ca.q_parts = plan->d_parts_q;
+  ca.n_q_parts = 1;
+  ca.s_parts = plan->d_parts_s;
+  ca.n_s_parts = vec_blocks_r(N);
+  ca.alpha = sc.alpha + it;
+  ca.gamma = sc.gamma + it;
+  ca.delta = sc.delta + it;
+  PA_CUDA(launch_cgls_xr(x_dev, shard_p(plan, it), shard_r(plan, it), shard_r(plan, it + 1),
+                         plan->d_q, plan->d_packed, ca, (int)N, plan->S, plan->K, plan->Kp,
+                         plan->pad, stored(plan->d_parts_h + (size_t)(it + 1) * plan->n_partials),
+                         st));
+  // s_part = A^T r_{it+1}
+  PA_TRY(shard_adjoint(plan, s_part_dev, accumulate, st));
+  plan->shard_it = it + 1;
+  plan->shard_phase = 1;
+  return PA_OK;
+}
+
+pa_status pa_shard_cgls_finish(pa_plan* plan, float* x_dev, int nonneg, double* hist_dev,
+                               int accumulate, pa_stream stream) {
+  if (!plan) {
+    set_error("pa_shard_cgls_finish: plan is NULL");
+    return PA_ERR_INVALID_ARG;
+  }
+  if (plan->shard_phase != 1 || (nonneg && !x_dev)) {
+    set_error("pa_shard_cgls_finish: no sharded run between iterations, or nonneg without x");
+    return PA_ERR_INVALID_ARG;
+  }
+  DeviceScope scope(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n_done = plan->shard_it;
+  if (hist_dev) {
+    const int n_comb = forward_combine_blocks(plan->S, plan->K, plan->comb_spt);
+    const int n_xr = cgls_r_blocks(plan->S, plan->K);
+    PA_CUDA(launch_hist(plan->d_parts_h, plan->n_partials, n_comb, n_xr, n_done + 1, hist_dev, st,
+                        accumulate ? 1 : 0));
+  }
+  if (nonneg) PA_CUDA(launch_clamp(x_dev, plan->grid.nx * plan->grid.ny * plan->grid.nz, st));
+  plan->shard_phase = 0;
+  return PA_OK;
+}
+
+}  // extern "C"

@@ -75,76 +75,119 @@ def test_reference_arm_runs_on_rank0_only(tmp_path):
 
 
 # ----------------------------------------------------------------------------
-# Sensor sharding of one large frame, checked with the oracle on two gloo ranks:
-# each rank owns half of the sensors, applies A to its own rows (no exchange)
-# and A^T to its own traces; the partial images are all-reduced, and so is the
-# one scalar ||A p||^2 that CGLS needs per iteration (||A^T r||^2 follows from
-# the reduced image on every rank).  The sharded recursion must reproduce the
-# unsharded oracle CGLS: the partition changes only the order of sums.
+# Sensor sharding of one large frame: the product's driver
+# (paper_2404_10928_gb300.shard.sharded_cgls) on two gloo ranks, each holding
+# one or two shards, with the library's shard steps restated on the oracle's
+# operators (FP64, CPU).  Each shard applies A to its own rows (no exchange) and
+# A^T to its own traces; the partial images and the scalar ||A p||^2 are summed
+# over the process's shards and all-reduced over the ranks.  The sharded
+# recursion must reproduce the unsharded oracle CGLS: the partition changes
+# only the order of sums.
 # ----------------------------------------------------------------------------
 def _sharded_problem():
     from paper_2404_10928_gb300 import phantoms as ph
     return ph.custom(2, (24, 20), (1e-4, 1e-4), ph.ring_sensors(14, 3e-3), 200, seed=91)
 
 
-def _sharded_rank(rank, world, port, out_dir, n_iter):
+class _OracleShard:
+    """The four pa_shard_cgls_* steps of one shard on the oracle's operators."""
+
+    def __init__(self, geo):
+        import torch
+        self.geo = geo
+        self.n_pixels = geo.n_pixels
+        self.device = torch.device("cpu")
+        self.image_dtype = torch.float64
+
+    def _out(self, t, v, accumulate):
+        a = t.numpy()
+        a[...] = a + v if accumulate else v
+
+    def shard_cgls_begin(self, n_iter, y, x, s_part, accumulate):
+        from oracle import oracle as orc
+        self.r = y.numpy().reshape(self.geo.n_sensors, -1) - orc.forward(self.geo, x.numpy())
+        self.hist = [float(np.sum(self.r * self.r))]
+        self._out(s_part, orc.adjoint(self.geo, self.r), accumulate)
+
+    def shard_cgls_direction(self, it, s, delta_part, accumulate):
+        from oracle import oracle as orc
+        sv = s.numpy()
+        gamma = float(np.sum(sv * sv))
+        self.p = sv.copy() if it == 0 else sv + (gamma / self.gamma) * self.p
+        self.gamma = gamma
+        self.q = orc.forward(self.geo, self.p)
+        self._out(delta_part, np.array([np.sum(self.q * self.q)]), accumulate)
+
+    def shard_cgls_update(self, it, delta, x, s_part, accumulate):
+        from oracle import oracle as orc
+        alpha = self.gamma / float(delta[0])
+        if x is not None:
+            x.numpy()[...] += alpha * self.p
+        self.r = self.r - alpha * self.q
+        self.hist.append(float(np.sum(self.r * self.r)))
+        self._out(s_part, orc.adjoint(self.geo, self.r), accumulate)
+
+    def shard_cgls_finish(self, x, nonneg, hist, accumulate):
+        if hist is not None:
+            self._out(hist, np.array(self.hist), accumulate)
+        if nonneg:
+            x.numpy()[...] = np.maximum(x.numpy(), 0.0)
+
+
+def _sharded_rank(rank, world, port, out_dir, n_iter, per_rank):
     import torch
     import torch.distributed as dist
     from oracle import oracle as orc
+    from paper_2404_10928_gb300 import shard
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     prob = _sharded_problem()
-    full = orc.Geometry.of(prob)
-    y_full = orc.forward(full, prob.x_true)
-    mine = np.array_split(np.arange(prob.n_sensors), world)[rank]
-    geo = orc.Geometry(prob.dim, prob.shape, prob.spacing, prob.origin, prob.sensors[mine],
-                       prob.c, prob.fs, prob.n_samples, prob.t0, prob.amp_scale)
-    y = y_full[mine]
-
-    def allreduce(a):
-        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
-        dist.all_reduce(t)
-        return t.numpy()
-
-    x = np.zeros(prob.n_pixels)
-    r = y - orc.forward(geo, x)
-    s = allreduce(orc.adjoint(geo, r))           # the image all-reduce after A^T
-    p = s.copy()
-    gamma = float(np.sum(s * s))
-    deltas = []
-    for _ in range(n_iter):
-        q = orc.forward(geo, p)                   # own rows, no exchange
-        delta = float(allreduce(np.array([np.sum(q * q)]))[0])  # the scalar all-reduce
-        deltas.append(delta)
-        alpha = gamma / delta
-        x = x + alpha * p
-        r = r - alpha * q
-        s = allreduce(orc.adjoint(geo, r))
-        gamma_new = float(np.sum(s * s))
-        p = s + (gamma_new / gamma) * p
-        gamma = gamma_new
+    y_full = orc.forward(orc.Geometry.of(prob), prob.x_true)
+    ranges = shard.sensor_ranges(prob.n_sensors, world * per_rank)[rank * per_rank:
+                                                                   (rank + 1) * per_rank]
+    shards, ys = [], []
+    for b, e in ranges:
+        shards.append(_OracleShard(orc.Geometry(prob.dim, prob.shape, prob.spacing, prob.origin,
+                                                prob.sensors[b:e], prob.c, prob.fs,
+                                                prob.n_samples, prob.t0, prob.amp_scale)))
+        ys.append(torch.from_numpy(np.ascontiguousarray(y_full[b:e])))
+    x, hist = shard.sharded_cgls(shards, ys, n_iter, nonneg=False,
+                                 process_group=dist.group.WORLD, history=True)
     dist.barrier()
     dist.destroy_process_group()
-    np.savez(os.path.join(out_dir, f"shard{rank}.npz"), x=x, deltas=np.array(deltas))
+    np.savez(os.path.join(out_dir, f"shard{rank}.npz"), x=x.numpy(), hist=hist)
 
 
-def test_sensor_sharded_cgls_matches_unsharded_oracle(tmp_path):
+@pytest.mark.parametrize("per_rank", [1, 2])
+def test_sensor_sharded_cgls_matches_unsharded_oracle(tmp_path, per_rank):
     import torch.multiprocessing as mp
     from oracle import oracle as orc
     world, n_iter = 2, 6
-    mp.spawn(_sharded_rank, args=(world, _free_port(), str(tmp_path), n_iter), nprocs=world,
-             join=True)
+    mp.spawn(_sharded_rank, args=(world, _free_port(), str(tmp_path), n_iter, per_rank),
+             nprocs=world, join=True)
     prob = _sharded_problem()
     geo = orc.Geometry.of(prob)
     y = orc.forward(geo, prob.x_true)
     ref = []
-    orc.cgls(geo, y, n_iter, nonneg=False, iterates=ref)
+    x_ref, h_ref = orc.cgls(geo, y, n_iter, nonneg=False, iterates=ref)
     res = [np.load(tmp_path / f"shard{r}.npz") for r in range(world)]
     # every rank holds the same image, equal to the unsharded CGLS iterate
     assert np.array_equal(res[0]["x"], res[1]["x"])
     err = np.linalg.norm(res[0]["x"] - ref[-1]) / np.linalg.norm(ref[-1])
     assert err <= 1e-10, err
-    # and ||A p||^2 summed over the two shards is the full operator's (first
-    # iteration: p = A^T y)
-    q = orc.forward(geo, orc.adjoint(geo, y))
-    assert abs(res[0]["deltas"][0] - np.sum(q * q)) <= 1e-12 * np.sum(q * q)
+    # the residual history summed over the shards is the full problem's
+    np.testing.assert_allclose(res[0]["hist"], h_ref, rtol=1e-10)
+    assert np.array_equal(res[0]["hist"], res[1]["hist"])
+
+
+def test_sensor_ranges():
+    from paper_2404_10928_gb300 import shard
+    assert shard.sensor_ranges(10, 3) == [(0, 4), (4, 7), (7, 10)]
+    assert shard.sensor_ranges(4, 4) == [(0, 1), (1, 2), (2, 3), (3, 4)]
+    for n, k in [(256, 2), (1024, 8), (14, 4)]:
+        r = shard.sensor_ranges(n, k)
+        assert r[0][0] == 0 and r[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
+        assert max(e - b for b, e in r) - min(e - b for b, e in r) <= 1
+    with pytest.raises(ValueError):
+        shard.sensor_ranges(3, 4)
