@@ -86,13 +86,17 @@ typedef struct {
  *               or 8; 0 = chosen from the grid size).  Results are identical up
  *               to the order of the final per-pixel sum.
  *   fwd_sensors_per_cta  sensors per forward-gather work item (1..256; 0 = 32).
- * The last two are the tile shapes an autotuner may pick. */
+ *   fwd_threads  threads per forward-gather CTA: 64, 128 or 256, each owning
+ *               1024 / fwd_threads pixels of the tile (0 = 128).
+ * The last three are the tile shapes an autotuner may pick; none changes a
+ * result bit of the forward (its window sums are exact integer sums). */
 typedef struct {
   double t0;
   double amp_scale;
   int y_dtype;
   int adj_cluster;
   int fwd_sensors_per_cta;
+  int fwd_threads;
 } pa_plan_opts;
 
 /* Reconstruction settings (fill with pa_recon_opts_default first).
@@ -139,6 +143,7 @@ typedef struct {
   int cluster;              /* CTAs per tile in the adjoint (sensor split) */
   int fwd_sensors;          /* sensors per forward-gather CTA */
   int64_t device_bytes;     /* device memory owned by the plan */
+  int fwd_threads;          /* threads per forward-gather CTA */
 } pa_plan_info;
 
 void pa_recon_opts_default(pa_recon_opts *opts);

@@ -1,11 +1,13 @@
 """Autotuner for the gathers' work decomposition ("tile shapes" at run time).
 
-Two plan options change how the work of A and A^T is cut into CTAs without
+Three plan options change how the work of A and A^T is cut into CTAs without
 changing what is computed:
 
 * ``adj_cluster``: how many CTAs (a thread-block cluster) split one pixel
   tile's sensors in the adjoint;
-* ``fwd_sensors_per_cta``: how many sensors one forward tile work item covers.
+* ``fwd_sensors_per_cta``: how many sensors one forward tile work item covers;
+* ``fwd_threads``: how many threads share a forward work item's 1024 pixels
+  (64, 128 or 256: 16, 8 or 4 pixels each).
 
 For a size class (GPU, dimension, and the pixel / sensor / sample counts
 rounded up to powers of two) the tuner builds a plan per candidate, times a
@@ -21,7 +23,9 @@ import statistics
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 ADJ_CLUSTERS = (1, 2, 4, 8)
-FWD_SENSORS = (8, 12, 16, 20, 24, 32, 48, 64)
+FWD_SENSORS = (8, 12, 16, 20, 24, 32, 48, 64, 96, 128)
+FWD_THREADS = (64, 128, 256)
+DEFAULT = (1, 32, 128)  # (adj_cluster, fwd_sensors_per_cta, fwd_threads) held fixed while another varies
 
 
 def _pow2(n: int) -> int:
@@ -37,14 +41,17 @@ def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int,
             f"y{y_dtype}")
 
 
-def candidates(n_sensors: int) -> Iterable[Tuple[int, int]]:
-    """adj_cluster only changes the adjoint and fwd_sensors_per_cta only the
-    forward, so each is varied with the other at its default."""
-    for spc in FWD_SENSORS:
-        yield 1, spc
+def candidates(n_sensors: int) -> Iterable[Tuple[int, int, int]]:
+    """(adj_cluster, fwd_sensors_per_cta, fwd_threads) triples.  adj_cluster
+    only changes the adjoint and the other two only the forward, so the forward
+    pair is searched jointly with the cluster at its default, and the cluster
+    with the forward pair at its default."""
+    for nt in FWD_THREADS:
+        for spc in FWD_SENSORS:
+            yield 1, spc, nt
     for c in ADJ_CLUSTERS[1:]:
         if 2 * c <= n_sensors:
-            yield c, 32
+            yield c, DEFAULT[1], DEFAULT[2]
 
 
 def default_cache_path() -> str:
@@ -54,10 +61,10 @@ def default_cache_path() -> str:
 
 
 class Autotuner:
-    """Pick (adj_cluster, fwd_sensors_per_cta) per size class.
+    """Pick (adj_cluster, fwd_sensors_per_cta, fwd_threads) per size class.
 
-    ``measure(prob, adj_cluster, spc) -> seconds`` defaults to timing real plans
-    on the current GPU; tests inject their own."""
+    ``measure(prob, adj_cluster, spc, fwd_threads) -> seconds`` defaults to
+    timing real plans on the current GPU; tests inject their own."""
 
     def __init__(self, cache_path: Optional[str] = None,
                  measure: Optional[Callable] = None, gpu_name: Optional[str] = None):
@@ -87,20 +94,24 @@ class Autotuner:
     def plan_options(entry: dict) -> dict:
         """The plan keyword arguments of a tuning entry."""
         return {"adj_cluster": entry["adj_cluster"],
-                "fwd_sensors_per_cta": entry["fwd_sensors_per_cta"]}
+                "fwd_sensors_per_cta": entry["fwd_sensors_per_cta"],
+                "fwd_threads": entry.get("fwd_threads", 0)}
 
     def best(self, prob, force: bool = False) -> dict:
         k = self.key(prob)
         if not force and k in self.cache:
             return self.cache[k]
         timings = {}
-        for c, spc in candidates(prob.n_sensors):
-            timings[f"{c},{spc}"] = float(self.measure(prob, c, spc))
-        by_spc = {int(k.split(",")[1]): t for k, t in timings.items() if k.startswith("1,")}
-        by_c = {int(k.split(",")[0]): t for k, t in timings.items() if k.endswith(",32")}
-        spc = min(by_spc, key=lambda v: (by_spc[v], v))
-        c = min(by_c, key=lambda v: (by_c[v], v))
-        entry = {"adj_cluster": c, "fwd_sensors_per_cta": spc, "timings_s": timings}
+        for c, spc, nt in candidates(prob.n_sensors):
+            timings[(c, spc, nt)] = float(self.measure(prob, c, spc, nt))
+        # the forward pair at the default cluster; ties to fewer threads, then
+        # fewer sensors
+        fwd = {(spc, nt): t for (c, spc, nt), t in timings.items() if c == DEFAULT[0]}
+        spc, nt = min(fwd, key=lambda v: (fwd[v], v[1], v[0]))
+        adj = {c: t for (c, s, n), t in timings.items() if (s, n) == DEFAULT[1:]}
+        c = min(adj, key=lambda v: (adj[v], v))
+        entry = {"adj_cluster": c, "fwd_sensors_per_cta": spc, "fwd_threads": nt,
+                 "timings_s": {f"{a},{b},{d}": t for (a, b, d), t in timings.items()}}
         self.cache[k] = entry
         self._save()
         return entry
@@ -113,13 +124,14 @@ class Autotuner:
         os.replace(tmp, self.cache_path)
 
 
-def _measure_gpu(prob, adj_cluster: int, spc: int, reps: int = 5) -> float:
+def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, reps: int = 5) -> float:
     """Median time (s) of one forward + one adjoint application on the GPU."""
     import torch
 
     from .api import Plan
 
-    with Plan.from_problem(prob, adj_cluster=adj_cluster, fwd_sensors_per_cta=spc) as plan:
+    with Plan.from_problem(prob, adj_cluster=adj_cluster, fwd_sensors_per_cta=spc,
+                           fwd_threads=fwd_threads) as plan:
         g = torch.Generator(device="cuda").manual_seed(0)
         x = torch.rand(prob.n_pixels, device="cuda", generator=g)
         y = torch.randn(prob.n_sensors, prob.n_samples, device="cuda", generator=g)

@@ -182,6 +182,7 @@ struct FwdParams {
   const int* upper;       // [S][K + L]: at k + L, how many sorted tiles have klo <= k
   int S, K, L, ntiles;
   int spc;                // sensors per forward tile work item
+  int threads;            // threads per forward tile work item (k_fwd_tile's block)
   int comb_spt;           // samples per combine thread: 4, or 1 when many windows cover a sample
   GridF g;
   float kappa, inv_kappa, half_inv_kappa, amp;
@@ -269,7 +270,8 @@ constexpr int kAdjSB = 8;                    // sensors per pipeline stage
 constexpr int kAdjStages = 4;
 
 // forward kernel shape
-constexpr int kFwdThreads = 256;             // 4 pixels of the tile per thread
+constexpr int kFwdThreads = 256;             // pixel owners of the batched kernels' forward (4 each)
+constexpr int kFwdThreadsDefault = 128;      // k_fwd_tile's default block (8 pixels per thread)
 constexpr int kFwdSPC = 32;                  // default sensors per tile work item
 constexpr int kFwdSB = 8;                    // sensors per accumulation stage
 constexpr int kCombThreads = 256;            // samples per combine CTA
@@ -365,6 +367,7 @@ struct pa_plan {
   int Kp = 0;       // packed row length (even)
   int cluster = 1;  // adjoint CTAs per tile
   int fwd_spc = 32; // sensors per forward tile work item
+  int fwd_threads = pa::kFwdThreadsDefault;  // threads per forward tile work item (64, 128, 256)
   int comb_spt = 4; // samples per combine thread (1 when many windows cover a sample)
 
   // device memory owned by the plan

@@ -9,6 +9,8 @@
 // results are bitwise reproducible.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "pa_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -1126,14 +1128,15 @@ __device__ __forceinline__ void fwd_pair2(const TileRef2& r, uint32_t base, floa
   }
 }
 
-// One (tile, sensor chunk) work item of the forward gather.  The first
-// kFwdThreads threads own four pixels each (two packed pairs); any further
+// One (tile, sensor chunk) work item of the forward gather.  The first NT
+// threads own kTilePixels / NT pixels each (as packed pairs); any further
 // threads of the block only help with the copies and barriers.
-template <int DIM, bool DIR>
+template <int DIM, bool DIR, int NT = kFwdThreads>
 __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int chunk,
                                                unsigned char* smem, int frame = 0) {
-  constexpr int PPT = kTilePixels / kFwdThreads;
-  static_assert(PPT == 4, "two packed pixel pairs per thread");
+  constexpr int PPT = kTilePixels / NT;
+  constexpr int NPAIR = PPT / 2;
+  static_assert(PPT % 2 == 0 && NT % 32 == 0, "whole warps, packed pixel pairs");
   TileRef2* refs = reinterpret_cast<TileRef2*>(smem);
   int* win = reinterpret_cast<int*>(refs + P.spc);
   __shared__ float s_max[32];
@@ -1143,7 +1146,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   const int ns = min(P.spc, P.S - s0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = blockDim.x;
-  const bool owner = tid < kFwdThreads;
+  const bool owner = tid < NT;
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
   int nvx, nvy, nvz;
   tile_valid<DIM>(tx, ty, tz, P.g, nvx, nvy, nvz);
@@ -1173,7 +1176,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
     for (int i = tid; i < (2 * kFwdSB * WS) / 4; i += nt) w4[i] = make_int4(0, 0, 0, 0);
   }
 
-  float2 ddx[2], ddy[2], ddz[2], cm[2], xs[2];
+  float2 ddx[NPAIR], ddy[NPAIR], ddz[NPAIR], cm[NPAIR], xs[NPAIR];
   float amax = 0.0f;
   int nonfinite = 0;
   // CGLS direction p = s + beta p_old (stored once, by sensor chunk 0): s and
@@ -1187,7 +1190,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
 #pragma unroll
     for (int m = 0; m < PPT; ++m) {
       int lx, ly, lz;
-      pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
+      pixel_local<DIM>(tid + m * NT, lx, ly, lz);
       const bool in = owner && lx < nvx && ly < nvy && lz < nvz;
       pix[m] = in ? ((int64_t)(tz * TZ + lz) * P.g.ny + (ty * TY + ly)) * P.g.nx + (tx * TX + lx)
                   : -1;
@@ -1220,7 +1223,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
 #pragma unroll
   for (int m = 0; m < PPT; ++m) {
     int lx, ly, lz;
-    pixel_local<DIM>(tid + m * kFwdThreads, lx, ly, lz);
+    pixel_local<DIM>(tid + m * NT, lx, ly, lz);
     float xv = 0.0f;
     if (DIR) {
       if (pix[m] >= 0) {
@@ -1250,7 +1253,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   for (int w = 0; w < (nt >> 5); ++w) xmax = fmaxf(xmax, s_max[w]);
   const float xscale = (xmax > 0.0f && finite) ? kFixedScale / xmax : 0.0f;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
+  for (int h = 0; h < NPAIR; ++h) xs[h] = mul2(xs[h], f2(xscale));  // |xs| <= 2^20
   const float2 inv_kappa = f2(P.inv_kappa), hik = f2(P.half_inv_kappa);
   const Chk chk{L, P.err};
 
@@ -1274,29 +1277,30 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
             base + (((copy_hi ? r.copy_hi : r.copy_lo) >> copy_sh) & 3u) * copy_bytes;
         if (r.klo & kNear) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < NPAIR; ++h)
             fwd_pair2<DIM, true>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
                                  inv_kappa, hik, chk);
         } else {
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < NPAIR; ++h)
             fwd_pair2<DIM, false>(r, cbase, ddx[h], ddy[h], ddz[h], cm[h], mul2(xs[h], dlo),
                                   inv_kappa, hik, chk);
         }
       }
     }
     __syncthreads();  // all taps of the stage are in the windows
-    // warp w rescales sensor g0 + w's window to float, stores it and clears it
-    // for the stage after next (whose deposits follow the next stage's barrier)
-    if (warp < nsb) {
-      const int klo = refs[g0 + warp].klo;
+    // warp w rescales sensor g0 + w's window (and g0 + w + warps, ...) to
+    // float, stores it and clears it for the stage after next (whose deposits
+    // follow the next stage's barrier)
+    for (int sw = warp; sw < nsb; sw += nt >> 5) {
+      const int klo = refs[g0 + sw].klo;
       if (klo != kSkip) {
         const float u = !finite ? __int_as_float(0x7fc00000)
-                        : (xscale > 0.0f ? __fdiv_rn(xmax, kFixedScale * refs[g0 + warp].dlo)
+                        : (xscale > 0.0f ? __fdiv_rn(xmax, kFixedScale * refs[g0 + sw].dlo)
                                          : 0.0f);
-        int4* src = reinterpret_cast<int4*>(wb + warp * WS);
+        int4* src = reinterpret_cast<int4*>(wb + sw * WS);
         float4* dst = reinterpret_cast<float4*>(
-            P.part + frame * P.fs_part + ((int64_t)(s0 + g0 + warp) * P.ntiles + tile) * L);
+            P.part + frame * P.fs_part + ((int64_t)(s0 + g0 + sw) * P.ntiles + tile) * L);
         for (int k4 = lane; k4 < L / 4; k4 += 32) {
           int4 v = make_int4(0, 0, 0, 0);
 #pragma unroll
@@ -1316,11 +1320,12 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   __syncthreads();  // the block's shared memory is free for the next work item
 }
 
-// DIR: the image is the CGLS direction s + beta p_old (P.s_in != nullptr)
-template <int DIM, bool DIR>
-__global__ void __launch_bounds__(kFwdThreads) k_fwd_tile(const FwdParams P) {
+// DIR: the image is the CGLS direction s + beta p_old (P.s_in != nullptr);
+// NT threads, each owning kTilePixels / NT pixels
+template <int DIM, bool DIR, int NT>
+__global__ void __launch_bounds__(NT) k_fwd_tile(const FwdParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
-  fwd_tile_block<DIM, DIR>(P, blockIdx.y, blockIdx.x, smem, blockIdx.z);
+  fwd_tile_block<DIM, DIR, NT>(P, blockIdx.y, blockIdx.x, smem, blockIdx.z);
 }
 
 // One (sensor, block of SPT blockDim samples) work item of the combine: p[s,k]
@@ -1415,9 +1420,16 @@ cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st, int fra
   const int smem = forward_smem_bytes(p.L, p.spc);
   dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, frames);
   const bool dir = p.s_in != nullptr;
-  auto tile_kernel = dim == 2 ? (dir ? k_fwd_tile<2, true> : k_fwd_tile<2, false>)
-                              : (dir ? k_fwd_tile<3, true> : k_fwd_tile<3, false>);
-  const cudaError_t e = launch_k(tile_kernel, grid1, dim3(kFwdThreads), smem, st, 0, p);
+  auto pick = [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    return dim == 2 ? (dir ? k_fwd_tile<2, true, NT> : k_fwd_tile<2, false, NT>)
+                    : (dir ? k_fwd_tile<3, true, NT> : k_fwd_tile<3, false, NT>);
+  };
+  const int nt = p.threads == 64 || p.threads == 256 ? p.threads : 128;
+  auto tile_kernel = nt == 64    ? pick(std::integral_constant<int, 64>())
+                     : nt == 256 ? pick(std::integral_constant<int, 256>())
+                                 : pick(std::integral_constant<int, 128>());
+  const cudaError_t e = launch_k(tile_kernel, grid1, dim3(nt), smem, st, 0, p);
   if (e != cudaSuccess) return e;
   const dim3 grid2(combine_kblocks(p.K, kCombThreads, p.comb_spt), p.S, frames);
   auto combine = p.comb_spt == 4
@@ -1446,17 +1458,18 @@ cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
   if ((e = cudaFuncSetAttribute(k_adjoint<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem_adj)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_tile<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_fwd)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_tile<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_fwd)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_fwd_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_fwd)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_fwd_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_fwd);
+  const void* fwd[] = {
+      (const void*)k_fwd_tile<2, false, 64>,  (const void*)k_fwd_tile<2, true, 64>,
+      (const void*)k_fwd_tile<3, false, 64>,  (const void*)k_fwd_tile<3, true, 64>,
+      (const void*)k_fwd_tile<2, false, 128>, (const void*)k_fwd_tile<2, true, 128>,
+      (const void*)k_fwd_tile<3, false, 128>, (const void*)k_fwd_tile<3, true, 128>,
+      (const void*)k_fwd_tile<2, false, 256>, (const void*)k_fwd_tile<2, true, 256>,
+      (const void*)k_fwd_tile<3, false, 256>, (const void*)k_fwd_tile<3, true, 256>};
+  for (const void* k : fwd)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd)) !=
+        cudaSuccess)
+      return e;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

@@ -267,9 +267,11 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   const int ydt = opts ? opts->y_dtype : PA_F32;
   if (opts && (opts->adj_cluster < 0 || opts->adj_cluster > 8 ||
                (opts->adj_cluster & (opts->adj_cluster - 1)) != 0 ||
-               opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256)) {
-    set_error("invalid plan options: adj_cluster must be 0, 1, 2, 4 or 8 and "
-              "fwd_sensors_per_cta in [0, 256]");
+               opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256 ||
+               (opts->fwd_threads != 0 && opts->fwd_threads != 64 && opts->fwd_threads != 128 &&
+                opts->fwd_threads != 256))) {
+    set_error("invalid plan options: adj_cluster must be 0, 1, 2, 4 or 8, "
+              "fwd_sensors_per_cta in [0, 256] and fwd_threads 0, 64, 128 or 256");
     return PA_ERR_INVALID_ARG;
   }
   if (!std::isfinite(t0) || !std::isfinite(amp) || (ydt != PA_F32 && ydt != PA_F16)) {
@@ -360,6 +362,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     p->cluster = C;
     if (opts && opts->adj_cluster > 0) p->cluster = std::min(opts->adj_cluster, p->S);
     if (opts && opts->fwd_sensors_per_cta > 0) p->fwd_spc = opts->fwd_sensors_per_cta;
+    if (opts && opts->fwd_threads > 0) p->fwd_threads = opts->fwd_threads;
     // the 4-sample combine reads 16-byte window slices per lane, and its warps span
     // 128 samples; once more than 16 windows cover a sample on average, lanes of a
     // warp mostly read different windows and one sample per lane (coalesced) wins
@@ -506,6 +509,7 @@ pa_status pa_plan_query(const pa_plan* plan, pa_plan_info* info) {
   info->window = plan->L;
   info->cluster = plan->cluster;
   info->fwd_sensors = plan->fwd_spc;
+  info->fwd_threads = plan->fwd_threads;
   info->device_bytes = plan->bytes;
   return PA_OK;
 }
@@ -530,6 +534,7 @@ FwdParams forward_params(const pa_plan* p, const float* x, float* out, int mode,
   f.L = p->L;
   f.ntiles = p->ntiles;
   f.spc = p->fwd_spc;
+  f.threads = p->fwd_threads;
   f.comb_spt = p->comb_spt;
   f.g = p->g;
   f.kappa = (float)(p->fs / p->c);

@@ -100,14 +100,21 @@ def test_full_size_operators(torch_cuda, factory):
     p_ref, g_ref = orc.forward(geo, x), orc.adjoint(geo, y)
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     yt = torch.tensor(y, dtype=torch.float32, device="cuda")
-    shapes = [(0, 0)] + list(candidates(prob.n_sensors))
-    for c, spc in shapes:
-        with Plan.from_problem(prob, adj_cluster=c, fwd_sensors_per_cta=spc) as plan:
+    shapes = [(0, 0, 0)] + list(candidates(prob.n_sensors))
+    p_first = None
+    for c, spc, nt in shapes:
+        with Plan.from_problem(prob, adj_cluster=c, fwd_sensors_per_cta=spc,
+                               fwd_threads=nt) as plan:
             p_gpu = plan.forward(xt).cpu().numpy()
             g_gpu = plan.adjoint(yt).cpu().numpy()
             plan.sync_status()
-        assert rel_l2(p_gpu, p_ref) <= OP_TOL, (c, spc, rel_l2(p_gpu, p_ref))
-        assert rel_l2(g_gpu, g_ref) <= OP_TOL, (c, spc, rel_l2(g_gpu, g_ref))
+        assert rel_l2(p_gpu, p_ref) <= OP_TOL, (c, spc, nt, rel_l2(p_gpu, p_ref))
+        assert rel_l2(g_gpu, g_ref) <= OP_TOL, (c, spc, nt, rel_l2(g_gpu, g_ref))
+        # the forward's window sums are exact integer sums: every decomposition
+        # gives the same bits
+        if p_first is None:
+            p_first = p_gpu
+        assert np.array_equal(p_gpu, p_first), (c, spc, nt)
 
 
 def test_sound_speed_change(torch_cuda):
@@ -148,9 +155,9 @@ def test_autotuned_plan_matches_default(torch_cuda, tmp_path):
     x, y = _inputs(prob, seed=9)
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    assert best["fwd_threads"] in (64, 128, 256)
     with Plan.from_problem(prob) as a, Plan.from_problem(
-            prob, adj_cluster=best["adj_cluster"],
-            fwd_sensors_per_cta=best["fwd_sensors_per_cta"]) as b:
+            prob, **Autotuner.plan_options(best)) as b:
         assert torch.equal(a.forward(xt), b.forward(xt))
         assert rel_l2(a.adjoint(yt).cpu().numpy(), b.adjoint(yt).cpu().numpy()) <= 1e-6
 
