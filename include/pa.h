@@ -88,8 +88,11 @@ typedef struct {
  *   fwd_sensors_per_cta  sensors per forward-gather work item (1..256; 0 = 32).
  *   fwd_threads  threads per forward-gather CTA: 64, 128 or 256, each owning
  *               1024 / fwd_threads pixels of the tile (0 = 128).
- * The last three are the tile shapes an autotuner may pick; none changes a
- * result bit of the forward (its window sums are exact integer sums). */
+ *   adj_warps    compute warps per adjoint CTA: 4 or 8, each thread owning
+ *               1024 / (32 adj_warps) pixels of the tile (0 = 8).
+ * The last four are the tile shapes an autotuner may pick; none changes a
+ * result bit of the forward (its window sums are exact integer sums), and
+ * adj_warps none of the adjoint (each pixel sums its sensors in order). */
 typedef struct {
   double t0;
   double amp_scale;
@@ -97,6 +100,7 @@ typedef struct {
   int adj_cluster;
   int fwd_sensors_per_cta;
   int fwd_threads;
+  int adj_warps;
 } pa_plan_opts;
 
 /* Reconstruction settings (fill with pa_recon_opts_default first).
@@ -144,6 +148,7 @@ typedef struct {
   int fwd_sensors;          /* sensors per forward-gather CTA */
   int64_t device_bytes;     /* device memory owned by the plan */
   int fwd_threads;          /* threads per forward-gather CTA */
+  int adj_warps;            /* compute warps per adjoint CTA */
 } pa_plan_info;
 
 void pa_recon_opts_default(pa_recon_opts *opts);

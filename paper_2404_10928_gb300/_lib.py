@@ -44,7 +44,8 @@ class pa_grid(ctypes.Structure):
 
 class pa_plan_opts(ctypes.Structure):
     _fields_ = [("t0", c_double), ("amp_scale", c_double), ("y_dtype", c_int),
-                ("adj_cluster", c_int), ("fwd_sensors_per_cta", c_int), ("fwd_threads", c_int)]
+                ("adj_cluster", c_int), ("fwd_sensors_per_cta", c_int), ("fwd_threads", c_int),
+                ("adj_warps", c_int)]
 
 
 class pa_recon_opts(ctypes.Structure):
@@ -57,7 +58,8 @@ class pa_recon_opts(ctypes.Structure):
 class pa_plan_info(ctypes.Structure):
     _fields_ = [("n_pixels", c_int64), ("n_sensors", c_int64), ("n_samples", c_int64),
                 ("pairs", c_int64), ("tile", c_int * 3), ("window", c_int), ("cluster", c_int),
-                ("fwd_sensors", c_int), ("device_bytes", c_int64), ("fwd_threads", c_int)]
+                ("fwd_sensors", c_int), ("device_bytes", c_int64), ("fwd_threads", c_int),
+                ("adj_warps", c_int)]
 
 
 _P = c_void_p  # opaque pa_plan*

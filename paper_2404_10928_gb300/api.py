@@ -31,7 +31,7 @@ class Plan:
     def __init__(self, sensors, shape, spacing, origin, c: float, fs: float, n_samples: int,
                  t0: float = 0.0, amp_scale: float = 1.0, y_dtype: str = "f32",
                  dim: Optional[int] = None, device=None, adj_cluster: int = 0,
-                 fwd_sensors_per_cta: int = 0, fwd_threads: int = 0):
+                 fwd_sensors_per_cta: int = 0, fwd_threads: int = 0, adj_warps: int = 0):
         self._lib = _lib.load()
         sensors = np.ascontiguousarray(sensors, dtype=np.float64)
         dim = int(dim if dim is not None else sensors.shape[1])
@@ -50,7 +50,8 @@ class Plan:
         grid = _lib.pa_grid(dim, shape[0], shape[1], shape[2], spacing[0], spacing[1], spacing[2],
                             (ctypes.c_double * 3)(*origin))
         opts = _lib.pa_plan_opts(self.t0, self.amp_scale, PA_F16 if y_dtype == "f16" else PA_F32,
-                                 int(adj_cluster), int(fwd_sensors_per_cta), int(fwd_threads))
+                                 int(adj_cluster), int(fwd_sensors_per_cta), int(fwd_threads),
+                                 int(adj_warps))
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = self._lib.pa_plan_create(ctypes.byref(handle),
@@ -100,7 +101,8 @@ class Plan:
         return {"n_pixels": inf.n_pixels, "n_sensors": inf.n_sensors, "n_samples": inf.n_samples,
                 "pairs": inf.pairs, "tile": tuple(inf.tile), "window": inf.window,
                 "cluster": inf.cluster, "fwd_sensors": inf.fwd_sensors,
-                "fwd_threads": inf.fwd_threads, "device_bytes": inf.device_bytes}
+                "fwd_threads": inf.fwd_threads, "adj_warps": inf.adj_warps,
+                "device_bytes": inf.device_bytes}
 
     def set_sound_speed(self, c: float):
         check(self._lib.pa_plan_set_sound_speed(self._h, float(c)), "pa_plan_set_sound_speed")

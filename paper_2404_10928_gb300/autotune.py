@@ -1,10 +1,12 @@
 """Autotuner for the gathers' work decomposition ("tile shapes" at run time).
 
-Three plan options change how the work of A and A^T is cut into CTAs without
+Four plan options change how the work of A and A^T is cut into CTAs without
 changing what is computed:
 
 * ``adj_cluster``: how many CTAs (a thread-block cluster) split one pixel
   tile's sensors in the adjoint;
+* ``adj_warps``: how many compute warps share an adjoint CTA's 1024 pixels
+  (4 or 8: 8 or 4 pixels per thread);
 * ``fwd_sensors_per_cta``: how many sensors one forward tile work item covers;
 * ``fwd_threads``: how many threads share a forward work item's 1024 pixels
   (64, 128 or 256: 16, 8 or 4 pixels each).
@@ -25,7 +27,10 @@ from typing import Callable, Dict, Iterable, Optional, Tuple
 ADJ_CLUSTERS = (1, 2, 4, 8)
 FWD_SENSORS = (8, 12, 16, 20, 24, 32, 48, 64, 96, 128)
 FWD_THREADS = (64, 128, 256)
-DEFAULT = (1, 32, 128)  # (adj_cluster, fwd_sensors_per_cta, fwd_threads) held fixed while another varies
+ADJ_WARPS = (4, 8)
+# (adj_cluster, fwd_sensors_per_cta, fwd_threads, adj_warps) held fixed while
+# the other operator's options vary
+DEFAULT = (1, 32, 128, 8)
 
 
 def _pow2(n: int) -> int:
@@ -41,17 +46,18 @@ def size_key(gpu: str, dim: int, n_pixels: int, n_sensors: int, n_samples: int,
             f"y{y_dtype}")
 
 
-def candidates(n_sensors: int) -> Iterable[Tuple[int, int, int]]:
-    """(adj_cluster, fwd_sensors_per_cta, fwd_threads) triples.  adj_cluster
-    only changes the adjoint and the other two only the forward, so the forward
-    pair is searched jointly with the cluster at its default, and the cluster
-    with the forward pair at its default."""
+def candidates(n_sensors: int) -> Iterable[Tuple[int, int, int, int]]:
+    """(adj_cluster, fwd_sensors_per_cta, fwd_threads, adj_warps).  The
+    cluster and warps only change the adjoint, the other two only the forward,
+    so the forward pair is searched jointly with the adjoint at its defaults,
+    and the adjoint pair with the forward at its defaults."""
     for nt in FWD_THREADS:
         for spc in FWD_SENSORS:
-            yield 1, spc, nt
-    for c in ADJ_CLUSTERS[1:]:
-        if 2 * c <= n_sensors:
-            yield c, DEFAULT[1], DEFAULT[2]
+            yield DEFAULT[0], spc, nt, DEFAULT[3]
+    for c in ADJ_CLUSTERS:
+        for aw in ADJ_WARPS:
+            if (c, aw) != (DEFAULT[0], DEFAULT[3]) and (c == 1 or 2 * c <= n_sensors):
+                yield c, DEFAULT[1], DEFAULT[2], aw
 
 
 def default_cache_path() -> str:
@@ -61,10 +67,11 @@ def default_cache_path() -> str:
 
 
 class Autotuner:
-    """Pick (adj_cluster, fwd_sensors_per_cta, fwd_threads) per size class.
+    """Pick (adj_cluster, fwd_sensors_per_cta, fwd_threads, adj_warps) per
+    size class.
 
-    ``measure(prob, adj_cluster, spc, fwd_threads) -> seconds`` defaults to
-    timing real plans on the current GPU; tests inject their own."""
+    ``measure(prob, adj_cluster, spc, fwd_threads, adj_warps) -> seconds``
+    defaults to timing real plans on the current GPU; tests inject their own."""
 
     def __init__(self, cache_path: Optional[str] = None,
                  measure: Optional[Callable] = None, gpu_name: Optional[str] = None):
@@ -95,23 +102,28 @@ class Autotuner:
         """The plan keyword arguments of a tuning entry."""
         return {"adj_cluster": entry["adj_cluster"],
                 "fwd_sensors_per_cta": entry["fwd_sensors_per_cta"],
-                "fwd_threads": entry.get("fwd_threads", 0)}
+                "fwd_threads": entry.get("fwd_threads", 0),
+                "adj_warps": entry.get("adj_warps", 0)}
 
     def best(self, prob, force: bool = False) -> dict:
         k = self.key(prob)
         if not force and k in self.cache:
             return self.cache[k]
         timings = {}
-        for c, spc, nt in candidates(prob.n_sensors):
-            timings[(c, spc, nt)] = float(self.measure(prob, c, spc, nt))
-        # the forward pair at the default cluster; ties to fewer threads, then
-        # fewer sensors
-        fwd = {(spc, nt): t for (c, spc, nt), t in timings.items() if c == DEFAULT[0]}
+        for cand in candidates(prob.n_sensors):
+            timings[cand] = float(self.measure(prob, *cand))
+        # the forward pair with the adjoint at its defaults (ties to fewer
+        # threads, then fewer sensors); the adjoint pair with the forward at
+        # its defaults (ties to the smaller cluster, then fewer warps)
+        fwd = {(spc, nt): t for (c, spc, nt, aw), t in timings.items()
+               if (c, aw) == (DEFAULT[0], DEFAULT[3])}
         spc, nt = min(fwd, key=lambda v: (fwd[v], v[1], v[0]))
-        adj = {c: t for (c, s, n), t in timings.items() if (s, n) == DEFAULT[1:]}
-        c = min(adj, key=lambda v: (adj[v], v))
+        adj = {(c, aw): t for (c, spc_, nt_, aw), t in timings.items()
+               if (spc_, nt_) == DEFAULT[1:3]}
+        c, aw = min(adj, key=lambda v: (adj[v], v))
         entry = {"adj_cluster": c, "fwd_sensors_per_cta": spc, "fwd_threads": nt,
-                 "timings_s": {f"{a},{b},{d}": t for (a, b, d), t in timings.items()}}
+                 "adj_warps": aw,
+                 "timings_s": {",".join(map(str, k)): t for k, t in timings.items()}}
         self.cache[k] = entry
         self._save()
         return entry
@@ -124,14 +136,15 @@ class Autotuner:
         os.replace(tmp, self.cache_path)
 
 
-def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, reps: int = 5) -> float:
+def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, adj_warps: int,
+                 reps: int = 5) -> float:
     """Median time (s) of one forward + one adjoint application on the GPU."""
     import torch
 
     from .api import Plan
 
     with Plan.from_problem(prob, adj_cluster=adj_cluster, fwd_sensors_per_cta=spc,
-                           fwd_threads=fwd_threads) as plan:
+                           fwd_threads=fwd_threads, adj_warps=adj_warps) as plan:
         g = torch.Generator(device="cuda").manual_seed(0)
         x = torch.rand(prob.n_pixels, device="cuda", generator=g)
         y = torch.randn(prob.n_sensors, prob.n_samples, device="cuda", generator=g)

@@ -159,6 +159,7 @@ struct AdjParams {
   Reduce red;             // ||out||^2 (ADJ_NORM)
   int* err;
   int sensors_per_rank;
+  int warps;              // compute warps of k_adjoint: 4 or 8 (0 = 8)
   // ADJ_FISTA (out = x_k, updated in place; omega = the step tau): with g =
   // A^T r, r = y - A z, v = z + tau (2 g - tv_beta tvg), x_new = prox(v), and
   // z = x_new + mu (x_new - x_k), both in place
@@ -368,6 +369,7 @@ struct pa_plan {
   int cluster = 1;  // adjoint CTAs per tile
   int fwd_spc = 32; // sensors per forward tile work item
   int fwd_threads = pa::kFwdThreadsDefault;  // threads per forward tile work item (64, 128, 256)
+  int adj_warps = pa::kAdjWarps;             // compute warps per adjoint CTA (4 or 8)
   int comb_spt = 4; // samples per combine thread (1 when many windows cover a sample)
 
   // device memory owned by the plan

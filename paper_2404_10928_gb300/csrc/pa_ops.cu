@@ -833,11 +833,13 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
   return s_acc;
 }
 
-template <int DIM, bool DC>
-__global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
+// NW compute warps (kTilePixels / (32 NW) pixels per thread) and one producer warp
+template <int DIM, bool DC, int NW>
+__global__ void __launch_bounds__(32 * (NW + 1), 2) k_adjoint(const AdjParams P) {
+  constexpr int NT = 32 * (NW + 1);
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ DF s_red[kAdjWarps + 1];
+  __shared__ DF s_red[NW + 1];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int C = (int)cluster.num_blocks();
@@ -846,7 +848,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   const int tid = threadIdx.x;
   const int s_begin = rank * P.sensors_per_rank;
   const int s_end = min(P.S, s_begin + P.sensors_per_rank);
-  float* s_acc = adj_accumulate<DIM, DC, kAdjWarps>(P, P.packed + frame * P.fs_packed, tile,
+  float* s_acc = adj_accumulate<DIM, DC, NW>(P, P.packed + frame * P.fs_packed, tile,
                                                     s_begin, s_end, smem);
   float* out = P.out ? P.out + frame * P.fs_img : nullptr;
   const float* xin = P.xin ? P.xin + frame * P.fs_img : nullptr;
@@ -857,7 +859,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
   const int p0 = rank * per, p1 = min(kTilePixels, p0 + per);
   const int tx = tile % P.g.ntx, ty = (tile / P.g.ntx) % P.g.nty, tz = tile / (P.g.ntx * P.g.nty);
   DF part = df_zero();
-  for (int p = p0 + tid; p < p1; p += kAdjThreads) {
+  for (int p = p0 + tid; p < p1; p += NT) {
     // the C <= 8 remote loads are issued together, then summed in rank order
     float part_q[8];
 #pragma unroll
@@ -901,7 +903,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
     }
   }
   if (P.mode == ADJ_NORM || DC) {
-    const DF t = block_sum<kAdjWarps + 1>(part, s_red);
+    const DF t = block_sum<NW + 1>(part, s_red);
     if (P.red.op == OP_STORE) {
       // one partial per tile: rank 0 sums the cluster's C CTA totals in rank order
       __shared__ DF s_cta;
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
       }
     } else {
       // one total over every frame of the launch
-      reduce_across_ctas<kAdjWarps + 1>(P.red, t, (frame * gridDim.y + tile) * C + rank,
+      reduce_across_ctas<NW + 1>(P.red, t, (frame * gridDim.y + tile) * C + rank,
                                         gridDim.x * gridDim.y * gridDim.z, s_red);
     }
   }
@@ -925,8 +927,14 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adjoint(const AdjParams P) {
 cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles, cudaStream_t st,
                            int frames) {
   const bool dc = p.mode == ADJ_DC;
-  auto kernel = dim == 2 ? (dc ? k_adjoint<2, true> : k_adjoint<2, false>)
-                         : (dc ? k_adjoint<3, true> : k_adjoint<3, false>);
+  if (p.warps == 4) {
+    auto kernel = dim == 2 ? (dc ? k_adjoint<2, true, 4> : k_adjoint<2, false, 4>)
+                           : (dc ? k_adjoint<3, true, 4> : k_adjoint<3, false, 4>);
+    return launch_k(kernel, dim3(cluster, ntiles, frames), dim3(32 * 5), adjoint_smem_bytes(p.L),
+                    st, cluster, p);
+  }
+  auto kernel = dim == 2 ? (dc ? k_adjoint<2, true, kAdjWarps> : k_adjoint<2, false, kAdjWarps>)
+                         : (dc ? k_adjoint<3, true, kAdjWarps> : k_adjoint<3, false, kAdjWarps>);
   return launch_k(kernel, dim3(cluster, ntiles, frames), dim3(kAdjThreads), adjoint_smem_bytes(p.L),
                   st, cluster, p);
 }
@@ -1446,18 +1454,15 @@ cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st, int fra
 // plan is created, outside any stream capture).
 cudaError_t configure_kernels(int smem_adj, int smem_fwd) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_adj)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_adj)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_adj)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_adjoint<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_adj)) != cudaSuccess)
-    return e;
+  const void* adj[] = {
+      (const void*)k_adjoint<2, false, 4>, (const void*)k_adjoint<2, true, 4>,
+      (const void*)k_adjoint<3, false, 4>, (const void*)k_adjoint<3, true, 4>,
+      (const void*)k_adjoint<2, false, kAdjWarps>, (const void*)k_adjoint<2, true, kAdjWarps>,
+      (const void*)k_adjoint<3, false, kAdjWarps>, (const void*)k_adjoint<3, true, kAdjWarps>};
+  for (const void* k : adj)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_adj)) !=
+        cudaSuccess)
+      return e;
   const void* fwd[] = {
       (const void*)k_fwd_tile<2, false, 64>,  (const void*)k_fwd_tile<2, true, 64>,
       (const void*)k_fwd_tile<3, false, 64>,  (const void*)k_fwd_tile<3, true, 64>,

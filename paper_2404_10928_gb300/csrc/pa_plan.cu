@@ -269,9 +269,11 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
                (opts->adj_cluster & (opts->adj_cluster - 1)) != 0 ||
                opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256 ||
                (opts->fwd_threads != 0 && opts->fwd_threads != 64 && opts->fwd_threads != 128 &&
-                opts->fwd_threads != 256))) {
+                opts->fwd_threads != 256) ||
+               (opts->adj_warps != 0 && opts->adj_warps != 4 && opts->adj_warps != 8))) {
     set_error("invalid plan options: adj_cluster must be 0, 1, 2, 4 or 8, "
-              "fwd_sensors_per_cta in [0, 256] and fwd_threads 0, 64, 128 or 256");
+              "fwd_sensors_per_cta in [0, 256], fwd_threads 0, 64, 128 or 256 and adj_warps 0, 4 "
+              "or 8");
     return PA_ERR_INVALID_ARG;
   }
   if (!std::isfinite(t0) || !std::isfinite(amp) || (ydt != PA_F32 && ydt != PA_F16)) {
@@ -363,6 +365,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     if (opts && opts->adj_cluster > 0) p->cluster = std::min(opts->adj_cluster, p->S);
     if (opts && opts->fwd_sensors_per_cta > 0) p->fwd_spc = opts->fwd_sensors_per_cta;
     if (opts && opts->fwd_threads > 0) p->fwd_threads = opts->fwd_threads;
+    if (opts && opts->adj_warps > 0) p->adj_warps = opts->adj_warps;
     // the 4-sample combine reads 16-byte window slices per lane, and its warps span
     // 128 samples; once more than 16 windows cover a sample on average, lanes of a
     // warp mostly read different windows and one sample per lane (coalesced) wins
@@ -510,6 +513,7 @@ pa_status pa_plan_query(const pa_plan* plan, pa_plan_info* info) {
   info->cluster = plan->cluster;
   info->fwd_sensors = plan->fwd_spc;
   info->fwd_threads = plan->fwd_threads;
+  info->adj_warps = plan->adj_warps;
   info->device_bytes = plan->bytes;
   return PA_OK;
 }
@@ -572,6 +576,7 @@ AdjParams adjoint_params(const pa_plan* p, float* out, int mode, const double* o
   a.red = Reduce{};
   a.err = p->d_err;
   a.sensors_per_rank = (p->S + p->cluster - 1) / p->cluster;
+  a.warps = p->adj_warps;
   return a;
 }
 

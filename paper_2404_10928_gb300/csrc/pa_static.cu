@@ -59,17 +59,18 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   const double t0 = opts ? opts->t0 : 0.0;
   const double amp = (opts && opts->amp_scale != 0.0) ? opts->amp_scale : 1.0;
   // the options are validated as pa_plan_create validates them; adj_cluster is
-  // honoured, y_dtype, fwd_sensors_per_cta and fwd_threads concern entry
-  // points this one does not run
+  // and adj_warps are honoured, y_dtype, fwd_sensors_per_cta and fwd_threads
+  // concern entry points this one does not run
   if (!std::isfinite(t0) || !std::isfinite(amp) ||
       (opts && ((opts->y_dtype != PA_F32 && opts->y_dtype != PA_F16) || opts->adj_cluster < 0 ||
                 opts->adj_cluster > 8 || (opts->adj_cluster & (opts->adj_cluster - 1)) != 0 ||
                 opts->fwd_sensors_per_cta < 0 || opts->fwd_sensors_per_cta > 256 ||
                 (opts->fwd_threads != 0 && opts->fwd_threads != 64 && opts->fwd_threads != 128 &&
-                 opts->fwd_threads != 256)))) {
+                 opts->fwd_threads != 256) ||
+                (opts->adj_warps != 0 && opts->adj_warps != 4 && opts->adj_warps != 8)))) {
     set_error("pa_adjoint_static: invalid options (adj_cluster must be 0, 1, 2, 4 or 8, "
-              "fwd_sensors_per_cta in [0, 256], fwd_threads 0, 64, 128 or 256, y_dtype PA_F32 "
-              "or PA_F16, t0 and amp_scale finite)");
+              "fwd_sensors_per_cta in [0, 256], fwd_threads 0, 64, 128 or 256, adj_warps 0, 4 "
+              "or 8, y_dtype PA_F32 or PA_F16, t0 and amp_scale finite)");
     return PA_ERR_INVALID_ARG;
   }
   const int dim = grid->dim;

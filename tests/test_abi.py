@@ -48,13 +48,15 @@ def test_struct_layouts_match_header(tmp_path):
 #include "pa.h"
 int main(void) {
   printf("pa_grid %zu %zu %zu\n", sizeof(pa_grid), offsetof(pa_grid, dx), offsetof(pa_grid, origin));
-  printf("pa_plan_opts %zu %zu %zu %zu\n", sizeof(pa_plan_opts), offsetof(pa_plan_opts, y_dtype),
-         offsetof(pa_plan_opts, fwd_sensors_per_cta), offsetof(pa_plan_opts, fwd_threads));
+  printf("pa_plan_opts %zu %zu %zu %zu %zu\n", sizeof(pa_plan_opts), offsetof(pa_plan_opts, y_dtype),
+         offsetof(pa_plan_opts, fwd_sensors_per_cta), offsetof(pa_plan_opts, fwd_threads),
+         offsetof(pa_plan_opts, adj_warps));
   printf("pa_recon_opts %zu %zu %zu %zu %zu %zu\n", sizeof(pa_recon_opts), offsetof(pa_recon_opts, power_v0_dev),
          offsetof(pa_recon_opts, residual_history_host), offsetof(pa_recon_opts, kernel_timing),
          offsetof(pa_recon_opts, tv_eps), offsetof(pa_recon_opts, restart));
-  printf("pa_plan_info %zu %zu %zu %zu\n", sizeof(pa_plan_info), offsetof(pa_plan_info, tile),
-         offsetof(pa_plan_info, device_bytes), offsetof(pa_plan_info, fwd_threads));
+  printf("pa_plan_info %zu %zu %zu %zu %zu\n", sizeof(pa_plan_info), offsetof(pa_plan_info, tile),
+         offsetof(pa_plan_info, device_bytes), offsetof(pa_plan_info, fwd_threads),
+         offsetof(pa_plan_info, adj_warps));
   return 0;
 }
 ''')
@@ -67,14 +69,16 @@ int main(void) {
     assert rows["pa_grid"] == [ctypes.sizeof(S.pa_grid), S.pa_grid.dx.offset, S.pa_grid.origin.offset]
     assert rows["pa_plan_opts"] == [ctypes.sizeof(S.pa_plan_opts), S.pa_plan_opts.y_dtype.offset,
                                     S.pa_plan_opts.fwd_sensors_per_cta.offset,
-                                    S.pa_plan_opts.fwd_threads.offset]
+                                    S.pa_plan_opts.fwd_threads.offset,
+                                    S.pa_plan_opts.adj_warps.offset]
     assert rows["pa_recon_opts"] == [ctypes.sizeof(S.pa_recon_opts), S.pa_recon_opts.power_v0_dev.offset,
                                      S.pa_recon_opts.residual_history_host.offset,
                                      S.pa_recon_opts.kernel_timing.offset,
                                      S.pa_recon_opts.tv_eps.offset, S.pa_recon_opts.restart.offset]
     assert rows["pa_plan_info"] == [ctypes.sizeof(S.pa_plan_info), S.pa_plan_info.tile.offset,
                                     S.pa_plan_info.device_bytes.offset,
-                                    S.pa_plan_info.fwd_threads.offset]
+                                    S.pa_plan_info.fwd_threads.offset,
+                                    S.pa_plan_info.adj_warps.offset]
 
 
 def _create(lib, sensors, grid, c=1500.0, fs=40e6, K=64, opts=None):
@@ -108,10 +112,11 @@ def test_argument_validation_without_gpu(lib):
     bad_opts = _lib.pa_plan_opts(0.0, 1.0, 7, 0, 0)
     assert _create(lib, far, _grid(), opts=bad_opts)[0] == _lib.PA_ERR_INVALID_ARG
     # adjoint clusters of 1, 2, 4 or 8 CTAs only; 1..256 sensors per forward work
-    # item; 64, 128 or 256 threads per forward work item
-    for cluster, spc, nt in ((3, 0, 0), (9, 0, 0), (-1, 0, 0), (0, 257, 0), (0, -2, 0),
-                             (0, 0, 96), (0, 0, 512), (0, 0, -1), (0, 0, 32)):
-        opts = _lib.pa_plan_opts(0.0, 1.0, _lib.PA_F32, cluster, spc, nt)
+    # item; 64, 128 or 256 threads per forward work item; 4 or 8 adjoint warps
+    for cluster, spc, nt, aw in ((3, 0, 0, 0), (9, 0, 0, 0), (-1, 0, 0, 0), (0, 257, 0, 0),
+                                 (0, -2, 0, 0), (0, 0, 96, 0), (0, 0, 512, 0), (0, 0, -1, 0),
+                                 (0, 0, 32, 0), (0, 0, 0, 2), (0, 0, 0, 16), (0, 0, 0, -4)):
+        opts = _lib.pa_plan_opts(0.0, 1.0, _lib.PA_F32, cluster, spc, nt, aw)
         assert _create(lib, far, _grid(), opts=opts)[0] == _lib.PA_ERR_INVALID_ARG
         assert b"adj_cluster" in lib.pa_last_error()
     # the dense, frequency-domain and back-projection entry points reject NULL plans

@@ -100,16 +100,16 @@ def test_full_size_operators(torch_cuda, factory):
     p_ref, g_ref = orc.forward(geo, x), orc.adjoint(geo, y)
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     yt = torch.tensor(y, dtype=torch.float32, device="cuda")
-    shapes = [(0, 0, 0)] + list(candidates(prob.n_sensors))
+    shapes = [(0, 0, 0, 0)] + list(candidates(prob.n_sensors))
     p_first = None
-    for c, spc, nt in shapes:
+    for c, spc, nt, aw in shapes:
         with Plan.from_problem(prob, adj_cluster=c, fwd_sensors_per_cta=spc,
-                               fwd_threads=nt) as plan:
+                               fwd_threads=nt, adj_warps=aw) as plan:
             p_gpu = plan.forward(xt).cpu().numpy()
             g_gpu = plan.adjoint(yt).cpu().numpy()
             plan.sync_status()
-        assert rel_l2(p_gpu, p_ref) <= OP_TOL, (c, spc, nt, rel_l2(p_gpu, p_ref))
-        assert rel_l2(g_gpu, g_ref) <= OP_TOL, (c, spc, nt, rel_l2(g_gpu, g_ref))
+        assert rel_l2(p_gpu, p_ref) <= OP_TOL, (c, spc, nt, aw, rel_l2(p_gpu, p_ref))
+        assert rel_l2(g_gpu, g_ref) <= OP_TOL, (c, spc, nt, aw, rel_l2(g_gpu, g_ref))
         # the forward's window sums are exact integer sums: every decomposition
         # gives the same bits
         if p_first is None:
@@ -135,6 +135,26 @@ def test_bad_tensor_arguments(torch_cuda):
             plan.forward(torch.zeros(prob.n_pixels + 1, device="cuda"))
         with pytest.raises(ValueError):
             plan.forward(torch.zeros(prob.n_pixels, device="cuda", dtype=torch.float64))
+
+
+@pytest.mark.parametrize("name", ["ragged-37x53-ring13-k301", "3d-20x17x12-planar"])
+def test_thread_layouts_give_the_same_bits(torch_cuda, name):
+    """Threads per forward tile and compute warps per adjoint CTA only change
+    which thread holds which pixels: A and A^T are bitwise the same."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300.api import Plan
+    prob = CASES[name]
+    x, y = _inputs(prob, seed=12)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    outs = []
+    for nt, aw in ((64, 4), (128, 8), (256, 4), (128, 4)):
+        with Plan.from_problem(prob, adj_cluster=2, fwd_threads=nt, adj_warps=aw) as plan:
+            assert plan.info()["fwd_threads"] == nt and plan.info()["adj_warps"] == aw
+            outs.append((plan.forward(xt), plan.adjoint(yt)))
+            plan.sync_status()
+    for p, g in outs[1:]:
+        assert torch.equal(p, outs[0][0]) and torch.equal(g, outs[0][1])
 
 
 def autotune_sizes():
