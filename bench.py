@@ -777,8 +777,9 @@ def run_gpu(args):
 
 def run_profile_case(kind: str) -> int:
     """Small fixed workloads for ncu captures.  "2d" / "3d": one plan (the
-    256x256 ring with 8 CTAs per adjoint cluster and 16 sensors per forward CTA,
-    or a 64^3 planar array with 2 and 64), then A on a dense random image and
+    256x256 ring with 8 CTAs of 4 compute warps per adjoint cluster and 24
+    sensors on 128 threads per forward CTA, or a 64^3 planar array with 2 CTAs
+    of 8 warps and 64 sensors on 128 threads), then A on a dense random image and
     A^T on random traces, three times each.  "dense": the 6144 x 16384 matrix
     (FP64 and FP32), M x and M^T r twice each.  "freq": the frequency-domain
     model on the 256x256 ring at 256 frequencies, forward and adjoint twice
@@ -795,11 +796,13 @@ def run_profile_case(kind: str) -> int:
     torch.cuda.set_device(0)
     if kind == "cgls":
         # the benchmark step: the 256^2 ring frame, the autotuned decomposition
-        # (8-CTA adjoint clusters, 16 sensors per forward work item), one warm-up
-        # reconstruction (graph capture) and two timed-shape reconstructions of 50
-        # CGLS iterations: 4 + 4 x 50 + 2 = 206 launches each
+        # (8-CTA adjoint clusters of 4 compute warps, 24 sensors and 128 threads
+        # per forward work item), one warm-up reconstruction (graph capture) and
+        # two timed-shape reconstructions of 50 CGLS iterations: 4 + 4 x 50 + 2 =
+        # 206 launches each
         prob = ph.ring_vessels()
-        with Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=16) as plan:
+        with Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=24, fwd_threads=128,
+                               adj_warps=4) as plan:
             x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
             y = plan.forward(x_true)
             x = torch.zeros(prob.n_pixels, dtype=torch.float32, device="cuda")
@@ -866,10 +869,12 @@ def run_profile_case(kind: str) -> int:
         return 0
     if kind == "2d":
         prob = ph.ring_vessels()
-        plan = Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=16)
+        plan = Plan.from_problem(prob, adj_cluster=8, fwd_sensors_per_cta=24, fwd_threads=128,
+                                 adj_warps=4)
     else:
         prob = ph.planar_vessel_tree(n=64)
-        plan = Plan.from_problem(prob, adj_cluster=2, fwd_sensors_per_cta=64)
+        plan = Plan.from_problem(prob, adj_cluster=2, fwd_sensors_per_cta=64, fwd_threads=128,
+                                 adj_warps=8)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand(plan.n_pixels, device="cuda", generator=g)
     y = torch.randn(plan.n_sensors * plan.n_samples, device="cuda", generator=g)

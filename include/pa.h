@@ -487,7 +487,10 @@ pa_status pa_adjoint_static(const double *sensors_xyz, int n_sensors, const pa_g
  * n_frames*(n_iter+1) doubles (frame-major) receiving ||y_f - A_f x_{f,n}||^2;
  * when given the call waits for the stream and reports PA_ERR_TIMEOUT if a
  * device wait gave up.  The arithmetic of every frame is that of pa_reconstruct
- * with a plan whose adj_cluster is 1. */
+ * with a plan whose adj_cluster is 1.  The batch cuts every frame's work into
+ * items of its own block shape (forward items of 32 sensors on 256 threads,
+ * adjoint items of one tile), whatever the plans' fwd_sensors_per_cta,
+ * fwd_threads and adj_warps; none of these changes a result bit. */
 pa_status pa_batch_create(pa_batch **out, pa_plan *const *plans, int n_frames);
 pa_status pa_batch_destroy(pa_batch *batch);
 pa_status pa_batch_landweber(pa_batch *batch, int n_iter, const void *const *y_dev,

@@ -138,7 +138,9 @@ class Autotuner:
 
 def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, adj_warps: int,
                  reps: int = 5) -> float:
-    """Median time (s) of one forward + one adjoint application on the GPU."""
+    """Median time (s) of one forward + one adjoint application on the GPU,
+    each sample timing enough back-to-back applications (at least ~2 ms) that
+    launch and event overheads do not decide between close candidates."""
     import torch
 
     from .api import Plan
@@ -150,16 +152,17 @@ def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, adj_warps: 
         y = torch.randn(prob.n_sensors, prob.n_samples, device="cuda", generator=g)
         p = torch.empty_like(y)
         z = torch.empty_like(x)
-        for _ in range(2):
-            plan.forward(x, out=p)
-            plan.adjoint(y, out=z)
-        times = []
-        for _ in range(reps):
+
+        def run(n: int) -> float:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            plan.forward(x, out=p)
-            plan.adjoint(y, out=z)
+            for _ in range(n):
+                plan.forward(x, out=p)
+                plan.adjoint(y, out=z)
             b.record()
             b.synchronize()
-            times.append(a.elapsed_time(b) * 1e-3)
-        return statistics.median(times)
+            return a.elapsed_time(b) * 1e-3 / n
+
+        run(2)
+        inner = max(1, min(200, int(2e-3 / max(run(1), 1e-6))))
+        return statistics.median(run(inner) for _ in range(reps))

@@ -98,10 +98,10 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
   // item counts per frame: forward (tile x sensor chunk), combine (sensor x
   // block of 4 kBatchThreads samples), adjoint (tile)
   std::vector<int> pre(4 * (n_frames + 1), 0);
-  int Lmax = 0, spc_max = 0;
+  int Lmax = 0;
   for (int f = 0; f < n_frames; ++f) {
     const pa_plan* p = plans[f];
-    const int chunks = (p->S + p->fwd_spc - 1) / p->fwd_spc;
+    const int chunks = (p->S + kBatchFwdSensors - 1) / kBatchFwdSensors;
     const int nk = combine_kblocks(p->K, kBatchThreads, 4);
     pre[f + 1] = pre[f] + p->ntiles * chunks;
     pre[(n_frames + 1) + f + 1] = pre[(n_frames + 1) + f] + p->S * nk;
@@ -109,9 +109,8 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
     pre[3 * (n_frames + 1) + f + 1] =
         pre[3 * (n_frames + 1) + f] + p->S * combine_kblocks(p->K, kBatchXrThreads, 4);
     Lmax = std::max(Lmax, p->L);
-    spc_max = std::max(spc_max, p->fwd_spc);
   }
-  b->smem = (size_t)std::max(adjoint_smem_bytes(Lmax), forward_smem_bytes(Lmax, spc_max));
+  b->smem = (size_t)std::max(adjoint_smem_bytes(Lmax), forward_smem_bytes(Lmax, kBatchFwdSensors));
   int per_sm = 0, sms = 0;
   cudaError_t e = batch_kernel_config(b->dim, b->smem, &per_sm);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -333,7 +332,8 @@ pa_status pa_batch_landweber(pa_batch* b, int n_iter, const void* const* y_dev,
     F.f = forward_params(p, x_dev[f], b->d_r[f], FWD_RESID, y_dev[f]);
     F.f.red = make_reduce(p, OP_SUM, nullptr, nullptr, nullptr);
     F.a = adjoint_params(p, x_dev[f], ADJ_LANDWEBER, b->d_omega + f, nonneg);
-    F.fwd_chunks = (p->S + p->fwd_spc - 1) / p->fwd_spc;
+    F.f.spc = kBatchFwdSensors;  // the batch's own forward items (see kBatchFwdSensors)
+    F.fwd_chunks = (p->S + kBatchFwdSensors - 1) / kBatchFwdSensors;
     F.n_kblk = combine_kblocks(p->K, kBatchThreads, 4);
     F.hist = b->d_hist + (size_t)f * (n_iter + 1);
   }
@@ -390,7 +390,8 @@ pa_status pa_batch_reconstruct(pa_batch* b, pa_method method, int n_iter,
     F.nonneg = nonneg;
     F.f = forward_params(p, x_dev[f], F.rbuf[0], FWD_RESID, y_dev[f]);
     F.a = adjoint_params(p, F.s, ADJ_NORM, nullptr, 0);
-    F.fwd_chunks = (p->S + p->fwd_spc - 1) / p->fwd_spc;
+    F.f.spc = kBatchFwdSensors;  // the batch's own forward items (see kBatchFwdSensors)
+    F.fwd_chunks = (p->S + kBatchFwdSensors - 1) / kBatchFwdSensors;
     F.n_kblk = combine_kblocks(p->K, kBatchThreads, 4);
     F.hist = b->d_hist + (size_t)f * (n_iter + 1);
   }

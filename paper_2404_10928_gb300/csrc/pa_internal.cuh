@@ -267,11 +267,16 @@ constexpr int kAdjPPT = kTilePixels / (32 * kAdjWarps);  // pixels per compute t
 // compute warps (four pixels per thread) and one producer warp
 constexpr int kBatchThreads = 288;
 constexpr int kBatchAdjWarps = 8;
+constexpr int kBatchFwdThreads = 256;       // pixel owners of the batched forward items
+// sensors per batched forward item: the batch cuts every frame's forward into
+// items of its own block shape, whatever the plan's single-launch options
+// (fwd_sensors_per_cta, fwd_threads); the windows, and so the results, are the same
+constexpr int kBatchFwdSensors = 32;
 constexpr int kAdjSB = 8;                    // sensors per pipeline stage
 constexpr int kAdjStages = 4;
 
 // forward kernel shape
-constexpr int kFwdThreads = 256;             // pixel owners of the batched kernels' forward (4 each)
+constexpr int kFwdThreads = 256;             // fwd_tile_block's default pixel owners (4 pixels each)
 constexpr int kFwdThreadsDefault = 128;      // k_fwd_tile's default block (8 pixels per thread)
 constexpr int kFwdSPC = 32;                  // default sensors per tile work item
 constexpr int kFwdSB = 8;                    // sensors per accumulation stage

@@ -1926,7 +1926,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_landweber(
       const int f = frame_of(pf, nf, gi);
       const int li = gi - pf[f];
       const int chunks = frames[f].fwd_chunks;
-      fwd_tile_block<DIM, false>(frames[f].f, li / chunks, li % chunks, smem);
+      fwd_tile_block<DIM, false, kBatchFwdThreads>(frames[f].f, li / chunks, li % chunks, smem);
     }
     grid_barrier(state, nb, err, state + 2, wait_ns);
     for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
@@ -2020,7 +2020,8 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_cgls(
     const int f = frame_of(pf, nf, gi), li = gi - pf[f];
     FwdParams P = frames[f].f;
     P.x = frames[f].x;
-    fwd_tile_block<DIM, false>(P, li / frames[f].fwd_chunks, li % frames[f].fwd_chunks, smem);
+    const int chunks = frames[f].fwd_chunks;
+    fwd_tile_block<DIM, false, kBatchFwdThreads>(P, li / chunks, li % chunks, smem);
   }
   grid_barrier(state, nb, err, state + 2, wait_ns);
   for (int gi = grab_item(state + 3); gi < pc[nf]; gi = grab_item(state + 3)) {
@@ -2063,7 +2064,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_cgls(
       const int tile = li / B.fwd_chunks, chunk = li % B.fwd_chunks;
       if (it == 0) {
         P.x = B.pbuf[0];
-        fwd_tile_block<DIM, false>(P, tile, chunk, smem);
+        fwd_tile_block<DIM, false, kBatchFwdThreads>(P, tile, chunk, smem);
       } else {
         P.x = nullptr;
         P.s_in = B.s;
@@ -2074,7 +2075,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_cgls(
         P.gamma_old = B.rec + (it - 1);
         P.beta = B.rec + 3 * nrec + (it - 1);
         P.gamma_new = B.rec + it;
-        fwd_tile_block<DIM, true>(P, tile, chunk, smem);
+        fwd_tile_block<DIM, true, kBatchFwdThreads>(P, tile, chunk, smem);
       }
     }
     grid_barrier(state, nb, err, state + 2, wait_ns);
