@@ -456,8 +456,9 @@ pa_status pa_plan_kernel_times(pa_plan *plan, double *fwd_ms, int *n_fwd, double
  * than that, or a staged trace window of more than 48 KiB of shared memory,
  * return PA_ERR_UNSUPPORTED with a message (use a plan instead).
  *   - opts is validated as pa_plan_create validates it; of its fields, t0,
- *     amp_scale and adj_cluster are used (y_dtype and fwd_sensors_per_cta
- *     concern entry points this one does not run).
+ *     amp_scale, adj_cluster and adj_warps are used (y_dtype,
+ *     fwd_sensors_per_cta and fwd_threads concern entry points this one does
+ *     not run).
  *   - Every call looks up the array's address on the current device (a runtime
  *     symbol query, not an allocation), rebuilds the geometry tables in the
  *     array and blocks until they are built; the adjoint itself is then

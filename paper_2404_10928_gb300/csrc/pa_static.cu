@@ -203,6 +203,7 @@ extern "C" pa_status pa_adjoint_static(const double* sensors_xyz, int n_sensors,
   a.red = Reduce{};
   a.err = d_err;
   a.sensors_per_rank = (n_sensors + C - 1) / C;
+  a.warps = (opts && opts->adj_warps > 0) ? opts->adj_warps : kAdjWarps;
   PA_CUDA(launch_adjoint(dim, a, C, (int)ntiles, st));
   return PA_OK;
 }

@@ -47,8 +47,9 @@ def test_static_adjoint_matches_plan_adjoint_twice():
             ref = plan.adjoint(p).cpu().numpy()
         sensors = np.ascontiguousarray(prob.sensors, dtype=np.float64)
         grid = _grid(prob)
-        opts = _lib.pa_plan_opts(prob.t0, prob.amp_scale, _lib.PA_F32, 0, 0)
-        for _ in range(2):
+        # plan defaults, then 2-CTA clusters of 4 compute warps
+        for opts in (_lib.pa_plan_opts(prob.t0, prob.amp_scale, _lib.PA_F32, 0, 0),
+                     _lib.pa_plan_opts(prob.t0, prob.amp_scale, _lib.PA_F32, 2, 0, 0, 4)):
             x = torch.full((prob.n_pixels,), float("nan"), dtype=torch.float32, device="cuda")
             st = lib.pa_adjoint_static(sensors.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        prob.n_sensors, ctypes.byref(grid), prob.c, prob.fs,
