@@ -44,6 +44,8 @@ UNIT = "pixel·sensor updates/s"
 WORKLOAD = "2D 256x256 0.1mm, 256-sensor ring R=20mm, 2048 samples @40MHz, c=1500, vessel phantom + 1% noise, 50 CGLS (FP64 reductions)"
 N_ITER = 50
 FLOPS_PER_PAIR = 18  # 9 FP32 instructions per pair (FFMA-equivalent, 2 flop each)
+MUFU_PER_PAIR = 2    # rsqrt (1/d) and rcp (the difference form of the arrival) per pair
+SFU_PER_SM_CLK = 16  # MUFU results per SM per clock
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -588,6 +590,10 @@ def bench_volume(torch, tuner, peak_tflops: float, reps: int = 3) -> dict:
             "forward_pairs_per_s": pairs / t_f, "adjoint_pairs_per_s": pairs / t_a,
             "adjoint_frac_fp32": pairs * FLOPS_PER_PAIR / t_a / 1e12 / peak_tflops,
             "forward_frac_fp32": pairs * FLOPS_PER_PAIR / t_f / 1e12 / peak_tflops,
+            "adjoint_frac_sfu": pairs * MUFU_PER_PAIR / t_a / 1e12
+                                / (peak_tflops / (2 * 128) * SFU_PER_SM_CLK),
+            "forward_frac_sfu": pairs * MUFU_PER_PAIR / t_f / 1e12
+                                / (peak_tflops / (2 * 128) * SFU_PER_SM_CLK),
             "cgls30_ms": t_c * 1e3, "cgls30_frames_per_s": 1.0 / t_c, "dc_ms": t_d * 1e3,
             "cgls30_two_sensor_shards_ms": t_s * 1e3,
             "timing": f"median of {reps}, CUDA events (inputs far larger than L2)"}
@@ -731,6 +737,14 @@ def run_gpu(args):
         kname = "k_adjoint<2>" if dom_is_adj else "k_fwd_tile<2>+k_fwd_combine"
         peak_src = (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                     f"{sm_max:.0f} MHz (MEASURED_PEAKS.json has no FP32 figure)")
+        sfu_peak = props.multi_processor_count * SFU_PER_SM_CLK * sm_max * 1e6  # results/s
+
+        def sfu(ms):  # the SFU (XU pipe) roofline of a gather: two MUFU results per pair
+            got = prob.pairs * MUFU_PER_PAIR / (ms * 1e-3)
+            return {"achieved": got, "peak": sfu_peak, "unit": "MUFU results/s",
+                    "frac": got / sfu_peak, "ops_per_pair": MUFU_PER_PAIR,
+                    "peak_source": f"derived: {props.multi_processor_count} SMs x "
+                                   f"{SFU_PER_SM_CLK} MUFU results x {sm_max:.0f} MHz"}
         clk = clocks.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -744,12 +758,13 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": read_traffic(kname), "peak_source": peak_src,
-                         "flops_per_launch": flops},
+                         "flops_per_launch": flops, "sfu": sfu(adj_ms if dom_is_adj else fwd_ms)},
             "roofline_adjoint": {"bound": "alu", "kernel": "k_adjoint<2>", "achieved": adj_tf,
                                  "peak": peak_tflops, "unit": "TFLOP/s",
                                  "frac": adj_tf / peak_tflops,
                                  "traffic": read_traffic("k_adjoint<2>"),
-                                 "peak_source": peak_src, "flops_per_launch": flops},
+                                 "peak_source": peak_src, "flops_per_launch": flops,
+                                 "sfu": sfu(adj_ms)},
             "kernels": {"adjoint_ms_per_launch": adj_ms, "forward_ms_per_application": fwd_ms,
                         "adjoint_pairs_per_s": prob.pairs / (adj_ms * 1e-3),
                         "forward_pairs_per_s": prob.pairs / (fwd_ms * 1e-3),
