@@ -13,7 +13,9 @@ changing what is computed:
 
 For a size class (GPU, dimension, and the pixel / sensor / sample counts
 rounded up to powers of two) the tuner builds a plan per candidate, times a
-few forward + adjoint applications with CUDA events and keeps the fastest.
+short graph-captured CGLS reconstruction (the forward with its direction
+update, the combine, the vector step and the adjoint, as a reconstruction runs
+them) with CUDA events and keeps the fastest.
 Results are cached in a JSON file (``PA_TUNE_CACHE``, default
 ``~/.cache/pa_gb300/autotune.json``).
 """
@@ -137,10 +139,13 @@ class Autotuner:
 
 
 def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, adj_warps: int,
-                 reps: int = 5) -> float:
-    """Median time (s) of one forward + one adjoint application on the GPU,
-    each sample timing enough back-to-back applications (at least ~2 ms) that
-    launch and event overheads do not decide between close candidates."""
+                 reps: int = 5, n_iter: int = 4) -> float:
+    """Median time (s) of one CGLS iteration on the GPU: the mix a reconstruction
+    runs (the forward gather with its direction update, the combine, the vector
+    step, the adjoint with its norm), from an n_iter-iteration graph-captured
+    reconstruction of random traces, each sample timing enough back-to-back
+    reconstructions (at least ~2 ms) that launch and event overheads do not
+    decide between close candidates."""
     import torch
 
     from .api import Plan
@@ -148,21 +153,19 @@ def _measure_gpu(prob, adj_cluster: int, spc: int, fwd_threads: int, adj_warps: 
     with Plan.from_problem(prob, adj_cluster=adj_cluster, fwd_sensors_per_cta=spc,
                            fwd_threads=fwd_threads, adj_warps=adj_warps) as plan:
         g = torch.Generator(device="cuda").manual_seed(0)
-        x = torch.rand(prob.n_pixels, device="cuda", generator=g)
-        y = torch.randn(prob.n_sensors, prob.n_samples, device="cuda", generator=g)
-        p = torch.empty_like(y)
-        z = torch.empty_like(x)
+        ydt = torch.float16 if plan.y_dtype == "f16" else torch.float32
+        y = torch.randn(prob.n_sensors * prob.n_samples, device="cuda", generator=g).to(ydt)
+        x = torch.zeros(prob.n_pixels, device="cuda")
 
         def run(n: int) -> float:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             for _ in range(n):
-                plan.forward(x, out=p)
-                plan.adjoint(y, out=z)
+                plan.reconstruct(y, "cgls", n_iter, out=x)
             b.record()
             b.synchronize()
-            return a.elapsed_time(b) * 1e-3 / n
+            return a.elapsed_time(b) * 1e-3 / (n * n_iter)
 
         run(2)
-        inner = max(1, min(200, int(2e-3 / max(run(1), 1e-6))))
+        inner = max(1, min(100, int(2e-3 / max(run(1) * n_iter, 1e-6))))
         return statistics.median(run(inner) for _ in range(reps))
