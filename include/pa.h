@@ -92,7 +92,9 @@ typedef struct {
  *               1024 / (32 adj_warps) pixels of the tile (0 = 8).
  * The last four are the tile shapes an autotuner may pick; none changes a
  * result bit of the forward (its window sums are exact integer sums), and
- * adj_warps none of the adjoint (each pixel sums its sensors in order). */
+ * adj_warps none of the adjoint's image (each pixel sums its sensors in
+ * order); the norm partials a reconstruction takes in the adjoint regroup
+ * their terms with adj_warps and adj_cluster. */
 typedef struct {
   double t0;
   double amp_scale;
@@ -491,7 +493,7 @@ pa_status pa_adjoint_static(const double *sensors_xyz, int n_sensors, const pa_g
  * with a plan whose adj_cluster is 1.  The batch cuts every frame's work into
  * items of its own block shape (forward items of 32 sensors on 256 threads,
  * adjoint items of one tile), whatever the plans' fwd_sensors_per_cta,
- * fwd_threads and adj_warps; none of these changes a result bit. */
+ * fwd_threads and adj_warps, which therefore do not enter its results. */
 pa_status pa_batch_create(pa_batch **out, pa_plan *const *plans, int n_frames);
 pa_status pa_batch_destroy(pa_batch *batch);
 pa_status pa_batch_landweber(pa_batch *batch, int n_iter, const void *const *y_dev,

@@ -285,3 +285,40 @@ def test_pcgls_reaches_nnls_on_a_small_system(torch_cuda):
         x = plan.reconstruct(_dev(torch, y), "pcgls", 3000, restart=1).cpu().numpy()
     assert np.all(x >= 0.0)
     assert rel_l2(x, ref) <= 1e-3, rel_l2(x, ref)
+
+
+def test_pcgls_warm_start_is_projected_first(torch_cuda, disks):
+    """A start image with negative entries is projected onto x >= 0 before the
+    first residual (oracle: x = max(0, x0) first), then 4 projected steps."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    rng = np.random.default_rng(71)
+    x0 = f32(rng.standard_normal(prob.n_pixels) * 0.05)
+    x_ref, h_ref = orc.pcgls(geo, y, 4, restart=2, x0=x0)
+    with _plan(prob) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "pcgls", 4, x0=_dev(torch, x0), restart=2,
+                                history=True)
+        x = x.cpu().numpy()
+    assert rel_l2(x, x_ref) <= RECON_TOL, rel_l2(x, x_ref)
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL, atol=RECON_TOL * h_ref[0])
+
+
+def test_cgls_bits_do_not_depend_on_thread_layouts(torch_cuda):
+    """Threads and sensors per forward item only move pixels between threads
+    and split the sensors differently: 6 CGLS iterations (the forward's
+    direction prologue included) give the same bits for every forward layout.
+    (The adjoint's warp count regroups the terms of its norm partials, so it is
+    held fixed here.)"""
+    torch = torch_cuda
+    from paper_2404_10928_gb300.api import Plan
+    prob = ph.custom(2, (70, 45), (1e-4, 1e-4), ph.ring_sensors(33, 4e-3), 400, seed=73)
+    y = _dev(torch, f32(orc.forward(orc.Geometry.of(prob), prob.x_true)))
+    outs = []
+    for nt, aw, spc in ((128, 4, 0), (64, 4, 12), (256, 4, 8), (128, 4, 20)):
+        with Plan.from_problem(prob, adj_cluster=2, fwd_threads=nt, adj_warps=aw,
+                               fwd_sensors_per_cta=spc) as plan:
+            x, h = plan.reconstruct(y, "cgls", 6, history=True)
+            outs.append((x, h))
+    for x, h in outs[1:]:
+        assert torch.equal(x, outs[0][0])
+        np.testing.assert_array_equal(h, outs[0][1])
