@@ -311,7 +311,7 @@ def test_cgls_bits_do_not_depend_on_thread_layouts(torch_cuda):
     held fixed here.)"""
     torch = torch_cuda
     from paper_2404_10928_gb300.api import Plan
-    prob = ph.custom(2, (70, 45), (1e-4, 1e-4), ph.ring_sensors(33, 4e-3), 400, seed=73)
+    prob = ph.custom(2, (70, 45), (1e-4, 1e-4), ph.ring_sensors(33, 5e-3), 400, seed=73)
     y = _dev(torch, f32(orc.forward(orc.Geometry.of(prob), prob.x_true)))
     outs = []
     for nt, aw, spc in ((128, 4, 0), (64, 4, 12), (256, 4, 8), (128, 4, 20)):
