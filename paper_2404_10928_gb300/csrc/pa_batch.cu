@@ -110,7 +110,8 @@ pa_status pa_batch_create(pa_batch** out, pa_plan* const* plans, int n_frames) {
         pre[3 * (n_frames + 1) + f] + p->S * combine_kblocks(p->K, kBatchXrThreads, 4);
     Lmax = std::max(Lmax, p->L);
   }
-  b->smem = (size_t)std::max(adjoint_smem_bytes(Lmax), forward_smem_bytes(Lmax, kBatchFwdSensors));
+  b->smem = (size_t)std::max(adjoint_smem_bytes(Lmax),
+                             forward_smem_bytes(b->dim, Lmax, kBatchFwdSensors));
   int per_sm = 0, sms = 0;
   cudaError_t e = batch_kernel_config(b->dim, b->smem, &per_sm);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);

@@ -949,7 +949,7 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // sensor) so that a window sum stays below 2^31, see k_fwd_copies): integer
 // addition is associative, so the shared-memory atomics give the same bits in
 // any order.  Windows are written
-// out (rescaled to float) once per stage of kFwdSB sensors.
+// out (rescaled to float) once per stage of fwd_sb(DIM) sensors.
 //
 // A, stage 2 (k_fwd_combine): p[s,k] = sum over the tiles whose window covers
 // k, in a fixed order (by window start), plus the residual / norm epilogue.
@@ -967,9 +967,9 @@ constexpr int kFwdCopies = 4;
 constexpr int kFwdCopyRes = 12;  // copy stride mod 32 (a multiple of 4: 16-byte aligned copies)
 __host__ __device__ inline int fwd_copy_stride(int L) { return L + ((kFwdCopyRes - L) & 31); }
 
-int forward_smem_bytes(int L, int spc) {
+int forward_smem_bytes(int dim, int L, int spc) {
   return spc * (int)sizeof(TileRef2) +
-         2 * kFwdSB * kFwdCopies * fwd_copy_stride(L) * (int)sizeof(int);
+         2 * fwd_sb(dim) * kFwdCopies * fwd_copy_stride(L) * (int)sizeof(int);
 }
 
 // Copy assignment and tap scale of the forward windows.  One warp per (tile,
@@ -1144,6 +1144,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
                                                unsigned char* smem, int frame = 0) {
   constexpr int PPT = kTilePixels / NT;
   constexpr int NPAIR = PPT / 2;
+  constexpr int SB = fwd_sb(DIM);
   static_assert(PPT % 2 == 0 && NT % 32 == 0, "whole warps, packed pixel pairs");
   TileRef2* refs = reinterpret_cast<TileRef2*>(smem);
   int* win = reinterpret_cast<int*>(refs + P.spc);
@@ -1181,7 +1182,7 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   const int WS = kFwdCopies * CS;              // words per (tile, sensor) window
   {
     int4* w4 = reinterpret_cast<int4*>(win);  // 16-byte aligned: refs are 64-byte entries
-    for (int i = tid; i < (2 * kFwdSB * WS) / 4; i += nt) w4[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < (2 * SB * WS) / 4; i += nt) w4[i] = make_int4(0, 0, 0, 0);
   }
 
   float2 ddx[NPAIR], ddy[NPAIR], ddz[NPAIR], cm[NPAIR], xs[NPAIR];
@@ -1271,11 +1272,11 @@ __device__ __forceinline__ void fwd_tile_block(const FwdParams& P, int tile, int
   const bool copy_hi = lane >= 16;
   const int copy_sh = 2 * (lane & 15);
   const uint32_t copy_bytes = 4u * (uint32_t)CS;
-  for (int g0 = 0, buf = 0; g0 < ns; g0 += kFwdSB, buf ^= 1) {
-    int* wb = win + buf * kFwdSB * WS;
-    const int nsb = min(kFwdSB, ns - g0);
+  for (int g0 = 0, buf = 0; g0 < ns; g0 += SB, buf ^= 1) {
+    int* wb = win + buf * SB * WS;
+    const int nsb = min(SB, ns - g0);
     if (owner && xscale > 0.0f) {
-      uint32_t base = magic_base(win_u32 + (uint32_t)(buf * kFwdSB * WS + L / 2) * 4u, 2);
+      uint32_t base = magic_base(win_u32 + (uint32_t)(buf * SB * WS + L / 2) * 4u, 2);
 #pragma unroll 1
       for (int sb = 0; sb < nsb; ++sb, base += 4u * (uint32_t)WS) {
         const TileRef2 r = refs[g0 + sb];
@@ -1425,7 +1426,7 @@ __global__ void __launch_bounds__(kCombThreads) k_fwd_combine(const FwdParams P)
 int forward_combine_blocks(int S, int K, int spt) { return S * combine_kblocks(K, kCombThreads, spt); }
 
 cudaError_t launch_forward(int dim, const FwdParams& p, cudaStream_t st, int frames) {
-  const int smem = forward_smem_bytes(p.L, p.spc);
+  const int smem = forward_smem_bytes(dim, p.L, p.spc);
   dim3 grid1((p.S + p.spc - 1) / p.spc, p.ntiles, frames);
   const bool dir = p.s_in != nullptr;
   auto pick = [&](auto nt) {

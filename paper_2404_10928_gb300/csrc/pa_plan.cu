@@ -372,7 +372,8 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     p->comb_spt = (int64_t)p->ntiles * p->L <= 16 * (int64_t)p->K ? 4 : 1;
   }
   const size_t smem_adj = (size_t)adjoint_smem_bytes(p->L);
-  if (smem_adj > 200 * 1024 || (size_t)forward_smem_bytes(p->L, p->fwd_spc) > 200 * 1024) {
+  const size_t smem_fwd = (size_t)forward_smem_bytes(p->dim, p->L, p->fwd_spc);
+  if (smem_adj > 200 * 1024 || smem_fwd > 200 * 1024) {
     set_error("geometry needs too much shared memory (window %d samples, %d tiles)", p->L,
               p->ntiles);
     delete p;
@@ -385,7 +386,7 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
     static int configured_adj[64] = {0}, configured_fwd[64] = {0};
     const int dv = p->device & 63;
     const int want_adj = std::max<int>((int)smem_adj, configured_adj[dv]);
-    const int want_fwd = std::max<int>(forward_smem_bytes(p->L, p->fwd_spc), configured_fwd[dv]);
+    const int want_fwd = std::max<int>((int)smem_fwd, configured_fwd[dv]);
     cudaError_t e = configure_kernels(want_adj, want_fwd);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
