@@ -92,6 +92,41 @@ def test_cgls_ring_vessels_early(torch_cuda, vessels):
     np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL)
 
 
+def test_pcgls_ring_vessels_early(torch_cuda, vessels):
+    """Projected CGLS (restart every 3) on the full 256^2 ring workload with 1%
+    noise, 5 iterations, with the benchmark's decomposition: parity with the
+    FP64 oracle at 1e-4."""
+    torch = torch_cuda
+    prob, geo, y = vessels
+    x_ref, h_ref = orc.pcgls(geo, y, 5, restart=3)
+    with _plan(prob, adj_cluster=8, fwd_sensors_per_cta=24, fwd_threads=128,
+               adj_warps=4) as plan:
+        x, h = plan.reconstruct(_dev(torch, y), "pcgls", 5, restart=3, history=True)
+    assert rel_l2(x.cpu().numpy(), x_ref) <= RECON_TOL
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL)
+
+
+def test_sharded_cgls_ring_vessels_early(torch_cuda, vessels):
+    """The full 256^2 ring workload with its 256 sensors split into 4 shards
+    (sensor-sharded CGLS, one process): 5 iterations against the oracle's
+    unsharded CGLS at 1e-4."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300 import shard
+    prob, geo, y = vessels
+    x_ref, h_ref = orc.cgls(geo, y, 5)
+    ranges = shard.sensor_ranges(prob.n_sensors, 4)
+    plans = shard.shard_plans(prob, ranges)
+    yr = y.reshape(prob.n_sensors, -1)
+    try:
+        x, h = shard.sharded_cgls(plans, [_dev(torch, np.ascontiguousarray(yr[b:e]))
+                                          for b, e in ranges], 5, history=True)
+    finally:
+        for p in plans:
+            p.close()
+    assert rel_l2(x.cpu().numpy(), x_ref) <= RECON_TOL
+    np.testing.assert_allclose(h, h_ref, rtol=RECON_TOL)
+
+
 def test_cgls_ring_vessels_full(torch_cuda, vessels):
     """CGLS on the full 256^2 ring workload with 1% noise, at 10, 20 and 50
     iterations.  Past the semi-convergence knee FP32-level perturbations move
