@@ -263,8 +263,8 @@ constexpr int kAdjWarps = 8;                 // compute warps (+1 producer warp)
 constexpr int kAdjThreads = 32 * (kAdjWarps + 1);
 constexpr int kAdjPPT = kTilePixels / (32 * kAdjWarps);  // pixels per compute thread
 // the persistent batch kernel runs every phase with one block size: the
-// forward's kFwdThreads pixel owners plus a warp; its adjoint phase uses eight
-// compute warps (four pixels per thread) and one producer warp
+// forward's kBatchFwdThreads pixel owners plus a warp; its adjoint phase uses
+// eight compute warps (four pixels per thread) and one producer warp
 constexpr int kBatchThreads = 288;
 constexpr int kBatchAdjWarps = 8;
 constexpr int kBatchFwdThreads = 256;       // pixel owners of the batched forward items

@@ -612,9 +612,9 @@ cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, in
 // One cluster of C CTAs per 1024-pixel tile; CTA rank r loops over its share of
 // the sensors.  A producer warp stages, per pipeline stage, the reference
 // entries of kAdjSB sensors and each sensor's window of L packed trace samples
-// (one cp.async.bulk per sensor, completion tracked by an mbarrier); eight
-// compute warps evaluate four pixels per thread per sensor from shared memory,
-// as two packed pixel pairs.  The C partial images are summed through
+// (one cp.async.bulk per sensor, completion tracked by an mbarrier); NW = 8 (or
+// 4) compute warps evaluate 4 (or 8) pixels per thread per sensor from shared
+// memory, as packed pixel pairs.  The C partial images are summed through
 // distributed shared memory in rank order, then the epilogue (store /
 // Landweber update / norm) runs once.
 // ---------------------------------------------------------------------------
@@ -942,8 +942,8 @@ cudaError_t launch_adjoint(int dim, const AdjParams& p, int cluster, int ntiles,
 // ---------------------------------------------------------------------------
 // A, stage 1: pixel-tile gather of per-(tile, sensor) trace windows.
 //
-// A CTA owns one 1024-pixel tile and kFwdSPC sensors: four pixels per thread,
-// kept in registers with their offsets.  For each sensor, every pixel adds its
+// A CTA owns one 1024-pixel tile and a chunk of sensors: NT threads (128 by
+// default) of 1024 / NT pixels each, kept in registers with their offsets.  For each sensor, every pixel adds its
 // two taps x (1-f)/d and x f/d to the (tile, sensor) window of L samples in
 // shared memory.  The taps are added as fixed-point integers (scaled per (tile,
 // sensor) so that a window sum stays below 2^31, see k_fwd_copies): integer
