@@ -117,7 +117,9 @@ typedef struct {
  *   power_v0_dev start vector [N] float32 on the device, or NULL for all ones.
  *   residual_history_host  NULL, or n_iter+1 doubles receiving ||y - A x_n||^2
  *                for n = 0..n_iter; when given, the call waits for the stream.
- *   use_graph    1: the iteration is captured once as a CUDA graph and replayed.
+ *   use_graph    1: the iteration is captured once as a CUDA graph and replayed
+ *                (per plan and distinct argument set; a plan keeps up to 64 such
+ *                graphs and starts its cache again past that).
  *   kernel_timing 1: CUDA events bracket every A and A^T gather launch; read the
  *                totals with pa_plan_kernel_times after the stream finished.
  *   l1_weight, tv_weight, tv_eps  FISTA only: the alpha and beta of Eq. 8 and the

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <new>
 
 #include "pa_internal.cuh"
@@ -383,6 +384,10 @@ pa_status pa_plan_create(pa_plan** out, const double* sensors_xyz, int n_sensors
   DeviceGuard guard(p->device);
   pa_status st = PA_OK;
   {
+    // the kernels' shared-memory limits only grow; plans created on several host
+    // threads at once take turns
+    static std::mutex configure_mutex;
+    std::lock_guard<std::mutex> lock(configure_mutex);
     static int configured_adj[64] = {0}, configured_fwd[64] = {0};
     const int dv = p->device & 63;
     const int want_adj = std::max<int>((int)smem_adj, configured_adj[dv]);

@@ -44,6 +44,9 @@ Scalars scalars(pa_plan* p, int n) {
   return s;
 }
 
+// graphs a plan keeps (one per distinct reconstruction argument set)
+constexpr size_t kMaxGraphs = 64;
+
 void drop_graphs(pa_plan* p) {
   for (auto& kv : p->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -452,6 +455,12 @@ pa_status pa_reconstruct(pa_plan* plan, pa_method method, int n_iter, const void
                                      o.power_iters, o.power_v0_dev, o.kernel_timing,
                                      o.l1_weight, o.tv_weight, o.tv_eps, o.restart);
     auto it = plan->graphs.find(key);
+    if (it == plan->graphs.end() && plan->graphs.size() >= kMaxGraphs) {
+      // a bounded cache: past kMaxGraphs argument sets, start again (after the
+      // device has finished with the old graphs)
+      PA_CUDA(cudaDeviceSynchronize());
+      drop_graphs(plan);
+    }
     if (it == plan->graphs.end()) {
       pa_plan::GraphEntry entry;
       t.entry = &entry;

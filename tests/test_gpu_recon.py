@@ -357,3 +357,21 @@ def test_cgls_bits_do_not_depend_on_thread_layouts(torch_cuda):
     for x, h in outs[1:]:
         assert torch.equal(x, outs[0][0])
         np.testing.assert_array_equal(h, outs[0][1])
+
+
+def test_graph_cache_is_bounded(torch_cuda, disks):
+    """Each distinct argument set is captured once; past 64 of them the plan
+    starts its cache again and every result stays the same."""
+    torch = torch_cuda
+    prob, geo, y, v0, lam = disks
+    yd = _dev(torch, y)
+    with _plan(prob) as plan:
+        ref = plan.reconstruct(yd, "cgls", 2)
+        keep = []
+        for i in range(70):
+            x = torch.zeros(prob.n_pixels, device="cuda")
+            keep.append(x)  # distinct buffers: distinct graphs
+            plan.reconstruct(yd, "cgls", 2, out=x)
+        torch.cuda.synchronize()
+        for x in keep:
+            assert torch.equal(x, ref)
