@@ -611,8 +611,9 @@ cudaError_t launch_pack(const float* r, float2* packed, int S, int K, int Kp, in
 //
 // One cluster of C CTAs per 1024-pixel tile; CTA rank r loops over its share of
 // the sensors.  A producer warp stages, per pipeline stage, the reference
-// entries of kAdjSB sensors and each sensor's window of L packed trace samples
-// (one cp.async.bulk per sensor, completion tracked by an mbarrier); NW = 8 (or
+// entries of its sensors (8 per stage in 2D, 16 in 3D) and each sensor's
+// window of L packed trace samples (one cp.async.bulk per sensor, completion
+// tracked by an mbarrier); NW = 8 (or
 // 4) compute warps evaluate 4 (or 8) pixels per thread per sensor from shared
 // memory, as packed pixel pairs.  The C partial images are summed through
 // distributed shared memory in rank order, then the epilogue (store /
@@ -680,21 +681,26 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
                                                  int s_begin, int s_end, unsigned char* smem) {
   constexpr int PPT = kTilePixels / (32 * NW);
   constexpr int NPAIR = PPT / 2;
+  // pipeline shape (sensors per stage x stages, the same shared memory): 8 x 4
+  // in 2D, 16 x 2 in 3D (at 128^3 A^T 1.227 against 1.260 ms; the same in 2D)
+  constexpr int SB = DIM == 3 ? 2 * kAdjSB : kAdjSB;
+  constexpr int NST = kAdjStages * kAdjSB / SB;
+  static_assert(SB <= 32 && NST >= 2, "one producer lane per sensor, double buffering at least");
   static_assert(PPT % 2 == 0, "pixels are processed in pairs");
   const int L = P.L;
   float2* s_trace = reinterpret_cast<float2*>(smem);
-  TileRef2* s_ref = reinterpret_cast<TileRef2*>(smem + kAdjStages * kAdjSB * L * sizeof(float2));
-  float* s_acc = reinterpret_cast<float*>(s_ref + kAdjStages * kAdjSB);
+  TileRef2* s_ref = reinterpret_cast<TileRef2*>(smem + NST * SB * L * sizeof(float2));
+  float* s_acc = reinterpret_cast<float*>(s_ref + NST * SB);
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_acc + kTilePixels);
-  uint64_t* s_empty = s_full + kAdjStages;
+  uint64_t* s_empty = s_full + NST;
   __shared__ int s_abort;
   __shared__ int s_issued;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n_stages = s_end > s_begin ? (s_end - s_begin + kAdjSB - 1) / kAdjSB : 0;
+  const int n_stages = s_end > s_begin ? (s_end - s_begin + SB - 1) / SB : 0;
 
   if (tid == 0) {
-    for (int i = 0; i < kAdjStages; ++i) {
+    for (int i = 0; i < NST; ++i) {
       mbar_init(&s_full[i], 1);
       mbar_init(&s_empty[i], NW);
     }
@@ -708,10 +714,10 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
     // ----------------------------- producer warp -----------------------------
     int j = 0;
     for (; j < n_stages; ++j) {
-      const int slot = j % kAdjStages;
-      if (j >= kAdjStages) {
+      const int slot = j % NST;
+      if (j >= NST) {
         int ok = 1;
-        if (lane == 0) ok = mbar_wait_bounded(&s_empty[slot], ((j / kAdjStages) - 1) & 1);
+        if (lane == 0) ok = mbar_wait_bounded(&s_empty[slot], ((j / NST) - 1) & 1);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) {
@@ -721,10 +727,10 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
           break;
         }
       }
-      const int s = s_begin + j * kAdjSB + lane;
+      const int s = s_begin + j * SB + lane;
       uint32_t bytes = 0;
       const float2* src = nullptr;
-      if (lane < kAdjSB) {
+      if (lane < SB) {
         TileRef r;
         r.klo = kSkip;
         if (s < s_end) {
@@ -744,16 +750,16 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
           }
         }
         if (r.klo != kSkip) {
-          s_ref[slot * kAdjSB + lane] = expand_ref(r);
+          s_ref[slot * SB + lane] = expand_ref(r);
         } else {
-          s_ref[slot * kAdjSB + lane].klo = kSkip;
+          s_ref[slot * SB + lane].klo = kSkip;
         }
       }
       const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
       __syncwarp();
       if (lane == 0) mbar_arrive_expect_tx(&s_full[slot], total);
       __syncwarp();
-      if (bytes) bulk_g2s(s_trace + (slot * kAdjSB + lane) * L, src, bytes, &s_full[slot]);
+      if (bytes) bulk_g2s(s_trace + (slot * SB + lane) * L, src, bytes, &s_full[slot]);
     }
     if (lane == 0) s_issued = j;
   } else if (warp < NW) {
@@ -782,8 +788,8 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
     const Chk chk{L, P.err};
     const uint32_t trace_u32 = smem_u32(s_trace);
     for (int j = 0; j < n_stages; ++j) {
-      const int slot = j % kAdjStages;
-      const bool ok = mbar_wait_bounded(&s_full[slot], (j / kAdjStages) & 1);
+      const int slot = j % NST;
+      const bool ok = mbar_wait_bounded(&s_full[slot], (j / NST) & 1);
       if (__any_sync(0xffffffffu, !ok)) {
         if (lane == 0) {
           atomicOr(P.err, ERR_WAIT_TIMEOUT);
@@ -792,10 +798,10 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
         break;
       }
       if (*(volatile int*)&s_abort) break;
-      const TileRef2* refs = s_ref + slot * kAdjSB;
-      uint32_t base = magic_base(trace_u32 + (uint32_t)(slot * kAdjSB * L + L / 2) * 8u, 3);
+      const TileRef2* refs = s_ref + slot * SB;
+      uint32_t base = magic_base(trace_u32 + (uint32_t)(slot * SB * L + L / 2) * 8u, 3);
 #pragma unroll 1
-      for (int sb = 0; sb < kAdjSB; ++sb, base += 8u * (uint32_t)L) {
+      for (int sb = 0; sb < SB; ++sb, base += 8u * (uint32_t)L) {
         const TileRef2 r = refs[sb];
         if (r.klo == kSkip) continue;
         if (r.klo & kNear) {
@@ -825,8 +831,8 @@ __device__ __forceinline__ float* adj_accumulate(const AdjParams& P, const float
     // drain copies that may still be in flight before the CTA's shared memory
     // is released (bounded)
     const int issued = s_issued;
-    for (int jj = max(0, issued - kAdjStages); jj < issued; ++jj)
-      mbar_wait_bounded(&s_full[jj % kAdjStages], (jj / kAdjStages) & 1);
+    for (int jj = max(0, issued - NST); jj < issued; ++jj)
+      mbar_wait_bounded(&s_full[jj % NST], (jj / NST) & 1);
   }
 
   __syncthreads();
