@@ -151,3 +151,26 @@ def test_sharded_cgls_planar_128_full_size(torch_cuda):
     err = rel_l2(x_s.cpu().numpy(), x_u.cpu().numpy())
     assert err <= RECON_TOL, err
     np.testing.assert_allclose(h_s, h_u, rtol=RECON_TOL)
+
+
+def test_sharded_cgls_with_f16_traces(torch_cuda, ring):
+    """Shards whose plans take FP16 measured traces (the time-series storage):
+    the sharded run equals the unsharded FP16 reconstruction up to the order
+    of sums, 5 iterations."""
+    torch = torch_cuda
+    from paper_2404_10928_gb300 import shard
+    from paper_2404_10928_gb300.api import Plan
+    prob, geo, y = ring
+    y16 = torch.tensor(y.reshape(prob.n_sensors, -1), dtype=torch.float16, device="cuda")
+    with Plan.from_problem(prob, y_dtype="f16") as full:
+        x_u, h_u = full.reconstruct(y16, "cgls", 5, history=True)
+    ranges = shard.sensor_ranges(prob.n_sensors, 3)
+    plans = shard.shard_plans(prob, ranges, y_dtype="f16")
+    try:
+        x_s, h_s = shard.sharded_cgls(plans, [y16[b:e].contiguous() for b, e in ranges], 5,
+                                      history=True)
+    finally:
+        for p in plans:
+            p.close()
+    assert rel_l2(x_s.cpu().numpy(), x_u.cpu().numpy()) <= 1e-5
+    np.testing.assert_allclose(h_s, h_u, rtol=1e-5)
