@@ -286,6 +286,22 @@ def read_traffic(kernel: str):
     return None
 
 
+def read_per_pair(kernel: str):
+    """(thread instructions, shared-memory wavefronts) per pixel-sensor pair of
+    `kernel` from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "ncu_per_pair.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and not line.startswith("#"):
+            try:
+                return float(parts[1]), float(parts[2])
+            except ValueError:
+                return None
+    return None
+
+
 def _events_time(torch, fn, reps: int) -> float:
     """Median seconds of fn() measured with CUDA events on the current stream."""
     times = []
@@ -739,6 +755,22 @@ def run_gpu(args):
                     f"{sm_max:.0f} MHz (MEASURED_PEAKS.json has no FP32 figure)")
         sfu_peak = props.multi_processor_count * SFU_PER_SM_CLK * sm_max * 1e6  # results/s
 
+        def ceilings(kernel, ms):
+            """The gather's pairs/s against the issue ceiling (4 warp instructions =
+            128 thread instructions per SM per clock) and the shared-memory one
+            (one wavefront per SM per clock), with its profiled per-pair counts."""
+            pp = read_per_pair(kernel)
+            if pp is None:
+                return None
+            ipp, wpp = pp
+            got = prob.pairs / (ms * 1e-3) / (props.multi_processor_count * sm_max * 1e6)
+            return {"pairs_per_sm_clock": got,
+                    "issue": {"instr_per_pair": ipp, "ceiling": 128.0 / ipp,
+                              "frac": got * ipp / 128.0},
+                    "shared": {"wavefronts_per_pair": wpp, "ceiling": 1.0 / wpp,
+                               "frac": got * wpp},
+                    "source": "profiles/ncu_per_pair.txt (ncu counters of the CGLS form)"}
+
         def sfu(ms):  # the SFU (XU pipe) roofline of a gather: two MUFU results per pair
             got = prob.pairs * MUFU_PER_PAIR / (ms * 1e-3)
             return {"achieved": got, "peak": sfu_peak, "unit": "MUFU results/s",
@@ -758,13 +790,14 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": read_traffic(kname), "peak_source": peak_src,
-                         "flops_per_launch": flops, "sfu": sfu(adj_ms if dom_is_adj else fwd_ms)},
+                         "flops_per_launch": flops, "sfu": sfu(adj_ms if dom_is_adj else fwd_ms),
+                         "ceilings": ceilings(kname, adj_ms if dom_is_adj else fwd_ms)},
             "roofline_adjoint": {"bound": "alu", "kernel": "k_adjoint<2>", "achieved": adj_tf,
                                  "peak": peak_tflops, "unit": "TFLOP/s",
                                  "frac": adj_tf / peak_tflops,
                                  "traffic": read_traffic("k_adjoint<2>"),
                                  "peak_source": peak_src, "flops_per_launch": flops,
-                                 "sfu": sfu(adj_ms)},
+                                 "sfu": sfu(adj_ms), "ceilings": ceilings("k_adjoint<2>", adj_ms)},
             "kernels": {"adjoint_ms_per_launch": adj_ms, "forward_ms_per_application": fwd_ms,
                         "adjoint_pairs_per_s": prob.pairs / (adj_ms * 1e-3),
                         "forward_pairs_per_s": prob.pairs / (fwd_ms * 1e-3),

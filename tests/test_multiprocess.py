@@ -50,6 +50,12 @@ def test_two_rank_job_clock_and_rate(tmp_path):
 def test_single_process_helpers():
     assert bench.max_over_ranks(None, None, 1.5) == 1.5
     assert bench.whole_job_rate(10.0, 1, 2.0) == 5.0
+    # the committed ncu summaries the benchmark line reads
+    for k in ("k_adjoint<2>", "k_fwd_tile<2>+k_fwd_combine"):
+        assert bench.read_traffic(k) > 0
+        ipp, wpp = bench.read_per_pair(k)
+        assert 9 <= ipp <= 64 and 0 < wpp < 1
+    assert bench.read_per_pair("no-such-kernel") is None
 
 
 def _run_reference(rank, world, tmp_path):
