@@ -59,7 +59,7 @@ typedef enum {
   PA_ERR_OOM = 4,           /* device allocation failed */
   PA_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
   PA_ERR_DEVICE_CHECK = 6,  /* an internal device-side consistency check failed */
-  PA_ERR_UNSUPPORTED = 7    /* valid request this build does not handle */
+  PA_ERR_UNSUPPORTED = 7    /* a valid request outside the library's limits */
 } pa_status;
 
 typedef enum { PA_LANDWEBER = 0, PA_CGLS = 1, PA_FISTA = 2, PA_PCGLS = 3 } pa_method;
