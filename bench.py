@@ -835,13 +835,30 @@ def run_profile_case(kind: str) -> int:
     one persistent batched launch of 4 projected Landweber iterations, twice.
     "dc": on the 64^3 planar plan, the speed-of-sound derivative and the
     smoothed TV with its gradient, three times each.  "cgls": the benchmark step
-    itself (256x256 ring, 50 CGLS iterations) three times.  Prints nothing."""
+    itself (256x256 ring, 50 CGLS iterations) three times.  "cgls3d": the 128^3
+    planar workload's 30-iteration CGLS twice.  Prints nothing."""
     import torch
 
     from paper_2404_10928_gb300 import phantoms as ph
     from paper_2404_10928_gb300.api import Batch, Plan
 
     torch.cuda.set_device(0)
+    if kind == "cgls3d":
+        # the 128^3 planar workload's step: its autotuned decomposition (2-CTA
+        # adjoint clusters of 8 warps, forward items of 128 sensors on 128
+        # threads), y = A x_true, two 30-iteration CGLS reconstructions
+        prob = ph.planar_vessel_tree()
+        with Plan.from_problem(prob, adj_cluster=2, fwd_sensors_per_cta=128, fwd_threads=128,
+                               adj_warps=8) as plan:
+            x_true = torch.tensor(prob.x_true, dtype=torch.float32, device="cuda")
+            y = plan.forward(x_true)
+            x = torch.zeros(prob.n_pixels, dtype=torch.float32, device="cuda")
+            for _ in range(2):
+                x.zero_()
+                plan.reconstruct(y, "cgls", 30, out=x)
+            torch.cuda.synchronize()
+            plan.sync_status()
+        return 0
     if kind == "cgls":
         # the benchmark step: the 256^2 ring frame, the autotuned decomposition
         # (8-CTA adjoint clusters of 4 compute warps, 24 sensors and 128 threads
@@ -946,7 +963,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and differentiable workloads")
-    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch", "dc", "cgls"],
+    ap.add_argument("--profile-case", choices=["2d", "3d", "dense", "freq", "batch", "dc", "cgls",
+                                                "cgls3d"],
                     help="only run the small gather workload used for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
