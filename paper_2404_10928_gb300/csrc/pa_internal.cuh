@@ -338,6 +338,8 @@ cudaError_t launch_affine_sum(const double* a, int n, const double* b, int m, do
 cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
+// parts[0] = the sum of parts[0..n) (in place, one CTA)
+cudaError_t launch_fold_partials(float2* parts, int n, cudaStream_t st);
 // parts[0] = the double-float form (hi, lo) of *v
 cudaError_t launch_df_of(const double* v, float2* parts, cudaStream_t st);
 cudaError_t launch_tv(int dim, const float* x, int nx, int ny, int nz, float eps, float* grad,

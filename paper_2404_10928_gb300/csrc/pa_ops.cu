@@ -1670,6 +1670,18 @@ __global__ void k_clamp(float* x, int N) {
     x[i] = fmaxf(x[i], 0.0f);
 }
 
+// parts[0] = the sum of parts[0..n) (one CTA, the fixed order of
+// sum_partials), so that the many CTAs that need the total read one partial
+__global__ void __launch_bounds__(256) k_fold_partials(float2* parts, int n) {
+  __shared__ DF s_red[8];
+  const DF t = sum_partials(parts, n, s_red);
+  if (threadIdx.x == 0) parts[0] = make_float2(t.hi, t.lo);
+}
+
+cudaError_t launch_fold_partials(float2* parts, int n, cudaStream_t st) {
+  return launch_k(k_fold_partials, dim3(1), dim3(256), 0, st, 0, parts, n);
+}
+
 __global__ void k_set_scalar(double* dst, double v) {
   *dst = v;
 }

@@ -179,6 +179,19 @@ pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg,
   return PA_OK;
 }
 
+// s = A^T r with the partials of ||s||^2 in parts_s (one per tile).  With many
+// tiles every CTA of the two kernels that need the total would sum them all
+// (at 128^3: 16 K forward CTAs x 2048 partials), so one CTA folds them into
+// parts_s[0] first; s_parts_count() is the count the consumers then sum.
+constexpr int kFoldAbove = 256;
+int s_parts_count(const pa_plan* p) { return p->ntiles > kFoldAbove ? 1 : p->ntiles; }
+
+pa_status adj_norm(pa_plan* p, float* out, Timing& t, cudaStream_t st) {
+  PA_TRY(adj(p, out, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+  if (p->ntiles > kFoldAbove) PA_CUDA(launch_fold_partials(p->d_parts_s, p->ntiles, st));
+  return PA_OK;
+}
+
 int vec_blocks_r(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
 // v <- A^T A v / ||A^T A v||, n_pow times, from v0 (NULL = ones).  Afterwards
@@ -239,13 +252,13 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
   // (OP_STORE), the next kernel that needs the total sums them itself, and the
   // residual history is summed once after the loop (launch_hist).
   const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
-  const int n_adj = p->ntiles;  // the adjoint stores one partial per tile (per cluster)
+  const int n_adj = s_parts_count(p);  // partials of ||s||^2 (adj_norm)
   const int n_xr = cgls_r_blocks(p->S, p->K);
   float2* hist_row = p->d_parts_h;
   // r = y - A x0; s = A^T r; p = s (||r||^2 -> history row 0, ||s||^2 -> parts_s)
   PA_TRY(fwd(p, x, r_in, FWD_RESID, y, stored(hist_row), t, st));
   PA_CUDA(launch_pack(r_in, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+  PA_TRY(adj_norm(p, p_cur, t, st));
   for (int it = 0; it < n_iter; ++it) {
     // p = s + beta p with beta = ||s||^2 / gamma (fused into the gather from the
     // second iteration on); q = A p (||q||^2 -> parts_q)
@@ -276,7 +289,7 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
     PA_CUDA(launch_cgls_xr(x, p_cur, r_in, r_out, p->d_q, p->d_packed, ca, N, p->S, p->K, p->Kp,
                            p->pad, stored(hist_row + (size_t)(it + 1) * p->n_partials), st));
     // s = A^T r (||s||^2 -> parts_s)
-    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+    PA_TRY(adj_norm(p, p->d_sv, t, st));
     std::swap(r_in, r_out);
     std::swap(p_cur, p_prev);
   }
@@ -296,11 +309,11 @@ pa_status enqueue_pcgls(pa_plan* p, int n_iter, const void* y, float* x, const p
   float* p_cur = p->d_pv;
   float* p_prev = p->d_pb;
   const int n_comb = forward_combine_blocks(p->S, p->K, p->comb_spt);
-  const int n_adj = p->ntiles;
+  const int n_adj = s_parts_count(p);
   if (o.nonneg) PA_CUDA(launch_clamp(x, N, st));
   PA_TRY(fwd(p, x, r, FWD_RESID, y, stored(p->d_parts_h), t, st));
   PA_CUDA(launch_pack(r, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-  PA_TRY(adj(p, p_cur, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+  PA_TRY(adj_norm(p, p_cur, t, st));
   for (int it = 0; it < n_iter; ++it) {
     if (it == 0) {
       PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
@@ -329,7 +342,7 @@ pa_status enqueue_pcgls(pa_plan* p, int n_iter, const void* y, float* x, const p
     PA_TRY(fwd(p, x, r, FWD_RESID, y, stored(p->d_parts_h + (size_t)(it + 1) * p->n_partials), t,
                st));
     PA_CUDA(launch_pack(r, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
-    PA_TRY(adj(p, p->d_sv, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
+    PA_TRY(adj_norm(p, p->d_sv, t, st));
     std::swap(p_cur, p_prev);
   }
   PA_CUDA(launch_hist(p->d_parts_h, p->n_partials, n_comb, n_comb, n_iter + 1, sc.hist, st));
@@ -662,8 +675,10 @@ pa_status pa_shard_cgls_direction(pa_plan* plan, int it, const float* s_dev,
   const int64_t N = (int64_t)plan->grid.nx * plan->grid.ny * plan->grid.nz;
   const Scalars sc = scalars(plan, plan->shard_n);
   // partials of gamma_it = ||s_it||^2 from the summed image (identical on every shard)
-  const int n_s = vec_blocks_r(N);
-  PA_CUDA(launch_norm(s_dev, N, stored(plan->d_parts_s), n_s, st));
+  const int n_blk = vec_blocks_r(N);
+  PA_CUDA(launch_norm(s_dev, N, stored(plan->d_parts_s), n_blk, st));
+  if (n_blk > kFoldAbove) PA_CUDA(launch_fold_partials(plan->d_parts_s, n_blk, st));
+  const int n_s = n_blk > kFoldAbove ? 1 : n_blk;
   // q = A p_it; ||q||^2 over this plan's sensors -> *delta_part_dev (+= with accumulate)
   Reduce rq = make_reduce(plan, OP_SUM, delta_part_dev, nullptr, nullptr);
   rq.accumulate = accumulate ? 1 : 0;
@@ -706,7 +721,7 @@ pa_status pa_shard_cgls_update(pa_plan* plan, int it, const double* delta_dev, f
   ca.q_parts = plan->d_parts_q;
   ca.n_q_parts = 1;
   ca.s_parts = plan->d_parts_s;
-  ca.n_s_parts = vec_blocks_r(N);
+  ca.n_s_parts = vec_blocks_r(N) > kFoldAbove ? 1 : vec_blocks_r(N);  // as the direction step
   ca.alpha = sc.alpha + it;
   ca.gamma = sc.gamma + it;
   ca.delta = sc.delta + it;
