@@ -338,6 +338,10 @@ cudaError_t launch_affine_sum(const double* a, int n, const double* b, int m, do
 cudaError_t launch_fista_tau(double* tau, const double* inv_lam, double c_tv, cudaStream_t st);
 cudaError_t launch_fill(float* dst, float value, int64_t n, cudaStream_t st);
 cudaError_t launch_norm(const float* v, int64_t n, const Reduce& red, int nblk, cudaStream_t st);
+// p_new = s + beta p_old, beta = ||s||^2 / gamma_old from n_s_parts partials
+cudaError_t launch_cgls_dir(float* p_new, const float* s, const float* p_old, int64_t n,
+                            const float2* s_parts, int n_s_parts, const double* gamma_old,
+                            double* beta, double* gamma_new, int beta_zero, cudaStream_t st);
 // parts[0] = the sum of parts[0..n) (in place, one CTA)
 cudaError_t launch_fold_partials(float2* parts, int n, cudaStream_t st);
 // parts[0] = the double-float form (hi, lo) of *v

@@ -1670,6 +1670,48 @@ __global__ void k_clamp(float* x, int N) {
     x[i] = fmaxf(x[i], 0.0f);
 }
 
+// The CGLS direction p_new = s + beta p_old with beta = ||s||^2 / gamma_old
+// (0 on a restart), as one vector step: the arithmetic of the forward gather's
+// fused direction prologue (so the same bits), for grids whose many sensor
+// chunks per tile would each form the tile's p again.  Block 0 records beta
+// and gamma_new = ||s||^2.
+__global__ void __launch_bounds__(kVecThreads) k_cgls_dir(float* p_new, const float* s,
+                                                         const float* p_old, int64_t n,
+                                                         const float2* s_parts, int n_s_parts,
+                                                         const double* gamma_old, double* beta,
+                                                         double* gamma_new, int beta_zero) {
+  __shared__ float s_beta, s_beta_lo;
+  if (threadIdx.x < 32) {
+    const double g_old = __ldcg(gamma_old);
+    const DF t = warp_sum_partials(s_parts, n_s_parts);
+    if (threadIdx.x == 0) {
+      const DF go = df_from_double(g_old);
+      const DF b = (go.hi > 0.0f && !beta_zero) ? df_div(t, go) : df_zero();
+      s_beta = b.hi;
+      s_beta_lo = b.lo;
+      if (blockIdx.x == 0) {
+        const double g_new = df_to_double(t);
+        *beta = (g_old > 0.0 && !beta_zero) ? g_new / g_old : 0.0;
+        *gamma_new = g_new;
+      }
+    }
+  }
+  __syncthreads();
+  const DF bt{s_beta, s_beta_lo};
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kVecThreads)
+    p_new[i] = df_axpy(bt, p_old[i], s[i]);
+}
+
+cudaError_t launch_cgls_dir(float* p_new, const float* s, const float* p_old, int64_t n,
+                            const float2* s_parts, int n_s_parts, const double* gamma_old,
+                            double* beta, double* gamma_new, int beta_zero, cudaStream_t st) {
+  const int blocks =
+      (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecThreads - 1) / kVecThreads, 152 * 8));
+  return launch_k(k_cgls_dir, dim3(blocks), dim3(kVecThreads), 0, st, 0, p_new, s, p_old, n,
+                  s_parts, n_s_parts, gamma_old, beta, gamma_new, beta_zero);
+}
+
 // parts[0] = the sum of parts[0..n) (one CTA, the fixed order of
 // sum_partials), so that the many CTAs that need the total read one partial
 __global__ void __launch_bounds__(256) k_fold_partials(float2* parts, int n) {

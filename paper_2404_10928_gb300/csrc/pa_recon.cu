@@ -186,6 +186,12 @@ pa_status adj(pa_plan* p, float* out, int mode, const double* omega, int nonneg,
 constexpr int kFoldAbove = 256;
 int s_parts_count(const pa_plan* p) { return p->ntiles > kFoldAbove ? 1 : p->ntiles; }
 
+// The CGLS direction p = s + beta p_old: fused into the forward gather's
+// prologue, or, on grids this large, formed once by a vector step before it
+// (every sensor chunk of a tile would form the tile's p again: at 128^3 eight
+// times, ~6% of the gather)
+bool direction_apart(const pa_plan* p) { return p->ntiles > kFoldAbove; }
+
 pa_status adj_norm(pa_plan* p, float* out, Timing& t, cudaStream_t st) {
   PA_TRY(adj(p, out, ADJ_NORM, nullptr, 0, stored(p->d_parts_s), t, st));
   if (p->ntiles > kFoldAbove) PA_CUDA(launch_fold_partials(p->d_parts_s, p->ntiles, st));
@@ -264,6 +270,10 @@ pa_status enqueue_cgls(pa_plan* p, int n_iter, const void* y, float* x, const pa
     // second iteration on); q = A p (||q||^2 -> parts_q)
     if (it == 0) {
       PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
+    } else if (direction_apart(p)) {
+      PA_CUDA(launch_cgls_dir(p_cur, p->d_sv, p_prev, N, p->d_parts_s, n_adj, sc.gamma + it - 1,
+                              sc.beta + it - 1, sc.gamma + it, 0, st));
+      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
     } else {
       DirUpdate du;
       du.s = p->d_sv;
@@ -315,7 +325,12 @@ pa_status enqueue_pcgls(pa_plan* p, int n_iter, const void* y, float* x, const p
   PA_CUDA(launch_pack(r, p->d_packed, p->S, p->K, p->Kp, p->pad, st));
   PA_TRY(adj_norm(p, p_cur, t, st));
   for (int it = 0; it < n_iter; ++it) {
+    const int restart = o.restart > 0 && it % o.restart == 0;
     if (it == 0) {
+      PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
+    } else if (direction_apart(p)) {
+      PA_CUDA(launch_cgls_dir(p_cur, p->d_sv, p_prev, N, p->d_parts_s, n_adj, sc.gamma + it - 1,
+                              sc.beta + it - 1, sc.gamma + it, restart, st));
       PA_TRY(fwd(p, p_cur, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st));
     } else {
       DirUpdate du;
@@ -327,7 +342,7 @@ pa_status enqueue_pcgls(pa_plan* p, int n_iter, const void* y, float* x, const p
       du.gamma_old = sc.gamma + it - 1;
       du.beta = sc.beta + it - 1;
       du.gamma_new = sc.gamma + it;
-      du.restart = o.restart > 0 && it % o.restart == 0;
+      du.restart = restart;
       PA_TRY(fwd(p, nullptr, p->d_q, FWD_NORM, nullptr, stored(p->d_parts_q), t, st, du));
     }
     CglsAlpha ca;
@@ -686,7 +701,11 @@ pa_status pa_shard_cgls_direction(pa_plan* plan, int it, const float* s_dev,
     PA_CUDA(cudaMemcpyAsync(shard_p(plan, 0), s_dev, (size_t)N * sizeof(float),
                             cudaMemcpyDeviceToDevice, st));
     PA_TRY(fwd(plan, shard_p(plan, 0), plan->d_q, FWD_NORM, nullptr, rq, none, st));
-  } else {  // p_it = s_it + (gamma_it / gamma_{it-1}) p_{it-1}, fused into the gather
+  } else if (direction_apart(plan)) {  // p_it = s_it + (gamma_it / gamma_{it-1}) p_{it-1}
+    PA_CUDA(launch_cgls_dir(shard_p(plan, it), s_dev, shard_p(plan, it - 1), N, plan->d_parts_s,
+                            n_s, sc.gamma + it - 1, sc.beta + it - 1, sc.gamma + it, 0, st));
+    PA_TRY(fwd(plan, shard_p(plan, it), plan->d_q, FWD_NORM, nullptr, rq, none, st));
+  } else {  // the same, fused into the gather
     DirUpdate du;
     du.s = s_dev;
     du.p_old = shard_p(plan, it - 1);
