@@ -272,6 +272,10 @@ pa_status run_batch(pa_batch* b, int method, const std::vector<BatchFrame>& fram
     if (omega) PA_CUDA(cudaMemcpy(b->d_omega, omega, n * sizeof(double), cudaMemcpyHostToDevice));
     PA_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_state, 0, 8 * sizeof(unsigned), b->cap);
+    // the frames' last-CTA reduction counters start at zero on every launch: a
+    // launch whose barriers gave up may have left one mid-count
+    for (int f = 0; f < n && e == cudaSuccess; ++f)
+      e = cudaMemsetAsync(b->plans[f]->d_counter, 0, sizeof(unsigned), b->cap);
     if (e == cudaSuccess)
       e = method == PA_CGLS
               ? launch_batch_cgls(b->dim, b->d_frames, n, b->d_pre, n_iter, b->d_state, b->d_err,
